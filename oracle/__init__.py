@@ -1,0 +1,327 @@
+"""FP64 CPU oracle of the spin/polarization-resolved SF-QED particle step
+(Wan et al., arXiv:2306.11288).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py``.  The product library never imports,
+links or calls anything here, and this package shares no code with it.
+
+The C source (``qed_oracle.c``) is compiled with gcc into ``oracle/_build`` on first
+use; ``build()`` forces that.  The Python side only marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qed_oracle.c")
+_HDR = os.path.join(_HERE, "qed_oracle.h")
+_OUT = os.path.join(_HERE, "_build", "libqed_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+F_NCS, F_NBW, F_VB, F_SPIN, F_NO_RECOIL, F_DROP_PHOTONS = 1, 2, 4, 8, 16, 32
+FIELD_NONE, FIELD_UNIFORM, FIELD_PLANE, FIELD_GAUSS, FIELD_GRID2D = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain gcc, -ffp-contract=off) and return the .so path."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    fresh = os.path.exists(_OUT) and os.path.getmtime(_OUT) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not fresh:
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class Particles(C.Structure):
+    _fields_ = [(n, C.POINTER(C.c_double)) for n in
+                ("x", "y", "z", "px", "py", "pz", "s1", "s2", "s3", "theta", "w")] + [
+        ("id", C.POINTER(C.c_uint64)), ("n", C.c_uint64), ("cap", C.c_uint64)]
+
+
+class Fields(C.Structure):
+    _fields_ = [("kind", C.c_int), ("circular", C.c_int), ("a0", C.c_double),
+                ("phi0", C.c_double), ("len", C.c_double), ("w0", C.c_double),
+                ("zf", C.c_double), ("E", C.c_double * 3), ("B", C.c_double * 3),
+                ("gEx", C.POINTER(C.c_float)), ("gEy", C.POINTER(C.c_float)),
+                ("gEz", C.POINTER(C.c_float)), ("gBx", C.POINTER(C.c_float)),
+                ("gBy", C.POINTER(C.c_float)), ("gBz", C.POINTER(C.c_float)),
+                ("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_ncs", C.c_uint64 * 2), ("n_nbw", C.c_uint64), ("n_range", C.c_uint64),
+                ("n_drop", C.c_uint64), ("n_near", C.c_uint64)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            d, pd, u64 = C.c_double, C.POINTER(C.c_double), C.c_uint64
+            L.or_ctx_create.restype = C.c_void_p
+            L.or_ctx_destroy.argtypes = [C.c_void_p]
+            L.or_set_next_id.argtypes = [C.c_void_p, u64]
+            L.or_get_next_id.argtypes = [C.c_void_p]
+            L.or_get_next_id.restype = u64
+            L.or_near_log.argtypes = [C.c_void_p, C.POINTER(u64), C.POINTER(C.c_uint32), pd, u64]
+            L.or_step.argtypes = [C.c_void_p, C.POINTER(Particles), C.POINTER(Particles),
+                                  C.POINTER(Particles), C.POINTER(Fields), d, d, u64,
+                                  C.c_uint32, C.c_uint32, C.POINTER(Stats)]
+            L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+            L.or_uniforms.argtypes = [u64, u64, C.c_uint32, C.c_uint32, pd]
+            L.or_besselk_scaled.argtypes = [d, pd]
+            L.or_ktable.argtypes = [C.c_void_p, d, pd]
+            L.or_ncs_rates.argtypes = [C.c_void_p, d, pd]
+            L.or_ncs_invcdf.argtypes = [C.c_void_p, C.c_int, d, d]
+            L.or_ncs_invcdf.restype = d
+            L.or_nbw_rates.argtypes = [C.c_void_p, d, pd]
+            L.or_nbw_invcdf.argtypes = [C.c_void_p, C.c_int, d, d]
+            L.or_nbw_invcdf.restype = d
+            L.or_vb_m.argtypes = [C.c_void_p, d, pd]
+            L.or_scorer_gi_prime.argtypes = [d]
+            L.or_scorer_gi_prime.restype = d
+            L.or_field.argtypes = [C.POINTER(Fields), d, d, d, d, pd, pd]
+            L.or_ncs_F.argtypes = [C.c_void_p, d, d, pd, pd, pd, pd, pd]
+            L.or_nbw_G.argtypes = [C.c_void_p, d, d, d, pd, pd, pd, pd, pd, pd]
+            L.or_table.argtypes = [C.c_void_p, C.c_int, C.POINTER(u64)]
+            L.or_table.restype = pd
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _vec(v):
+    return np.ascontiguousarray(v, dtype=np.float64)
+
+
+class ParticleArrays:
+    """Owned numpy SoA for one species; ``photon`` adds the basis angle."""
+
+    NAMES = ("x", "y", "z", "px", "py", "pz", "s1", "s2", "s3", "theta", "w")
+
+    def __init__(self, cap: int, photon: bool = False):
+        self.cap = int(cap)
+        self.photon = photon
+        self.arr = {k: np.zeros(max(self.cap, 1)) for k in self.NAMES}
+        self.id = np.zeros(max(self.cap, 1), dtype=np.uint64)
+        self.n = 0
+        self._s = Particles()
+        for k in self.NAMES:
+            setattr(self._s, k, _dp(self.arr[k]) if (photon or k != "theta") else None)
+        self._s.id = self.id.ctypes.data_as(C.POINTER(C.c_uint64))
+        self._s.cap = self.cap
+
+    def load(self, d: dict):
+        n = len(d["id"])
+        if n > self.cap:
+            raise ValueError("more particles than capacity")
+        for k in self.NAMES:
+            if k in d:
+                self.arr[k][:n] = d[k]
+        self.id[:n] = d["id"]
+        self.n = n
+        return self
+
+    def view(self) -> dict:
+        out = {k: self.arr[k][: self.n].copy() for k in self.NAMES if self.photon or k != "theta"}
+        out["id"] = self.id[: self.n].copy()
+        return out
+
+    def struct(self):
+        self._s.n = self.n
+        return C.byref(self._s)
+
+    def sync(self):
+        self.n = int(self._s.n)
+
+
+def make_fields(kind=FIELD_NONE, circular=0, a0=0.0, phi0=0.0, length=1.0, w0=1.0, zf=0.0,
+                E=(0, 0, 0), B=(0, 0, 0), grid=None):
+    f = Fields()
+    f.kind, f.circular, f.a0, f.phi0, f.len, f.w0, f.zf = kind, circular, a0, phi0, length, w0, zf
+    f.E[:] = list(E)
+    f.B[:] = list(B)
+    f._keep = None
+    if grid is not None:
+        comps = [np.ascontiguousarray(grid[k], dtype=np.float32) for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")]
+        f._keep = comps
+        for name, a in zip(("gEx", "gEy", "gEz", "gBx", "gBy", "gBz"), comps):
+            setattr(f, name, a.ctypes.data_as(C.POINTER(C.c_float)))
+        f.ny, f.nx = comps[0].shape
+        f.dx, f.dy, f.x0, f.y0 = grid["dx"], grid["dy"], grid.get("x0", 0.0), grid.get("y0", 0.0)
+    return f
+
+
+class Oracle:
+    """Owns one oracle context (tables + id counter)."""
+
+    def __init__(self):
+        self.L = lib()
+        self.ctx = self.L.or_ctx_create()
+        if not self.ctx:
+            raise MemoryError("or_ctx_create failed")
+
+    def __del__(self):
+        try:
+            self.L.or_ctx_destroy(self.ctx)
+        except Exception:
+            pass
+
+    # --- simulation ---------------------------------------------------------------
+    def set_next_id(self, i: int):
+        self.L.or_set_next_id(self.ctx, int(i))
+
+    def next_id(self) -> int:
+        return int(self.L.or_get_next_id(self.ctx))
+
+    def step(self, e, pos, ph, fields, t, dt, seed, step, flags):
+        st = Stats()
+        self.L.or_step(self.ctx, e.struct(), pos.struct(), ph.struct(), C.byref(fields),
+                       float(t), float(dt), int(seed), int(step), int(flags), C.byref(st))
+        e.sync(); pos.sync(); ph.sync()
+        return {"n_ncs_e": st.n_ncs[0], "n_ncs_p": st.n_ncs[1], "n_nbw": st.n_nbw,
+                "n_range": st.n_range, "n_drop": st.n_drop, "n_near": st.n_near}
+
+    def near_log(self, cap=65536):
+        ids = np.zeros(cap, dtype=np.uint64)
+        steps = np.zeros(cap, dtype=np.uint32)
+        m = np.zeros(cap)
+        self.L.or_near_log(self.ctx, ids.ctypes.data_as(C.POINTER(C.c_uint64)),
+                           steps.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(m), cap)
+        k = int((m > 0).sum())
+        return ids[:k], steps[:k], m[:k]
+
+    # --- pieces -------------------------------------------------------------------
+    def ktable(self, x):
+        o = np.zeros(3)
+        self.L.or_ktable(self.ctx, float(x), _dp(o))
+        return o
+
+    def ncs_rates(self, chi):
+        o = np.zeros(2)
+        self.L.or_ncs_rates(self.ctx, float(chi), _dp(o))
+        return o
+
+    def ncs_invcdf(self, comp, chi, t):
+        return self.L.or_ncs_invcdf(self.ctx, int(comp), float(chi), float(t))
+
+    def nbw_rates(self, chig):
+        o = np.zeros(2)
+        self.L.or_nbw_rates(self.ctx, float(chig), _dp(o))
+        return o
+
+    def nbw_invcdf(self, comp, chig, t):
+        return self.L.or_nbw_invcdf(self.ctx, int(comp), float(chig), float(t))
+
+    def vb_m(self, chig):
+        o = np.zeros(2)
+        self.L.or_vb_m(self.ctx, float(chig), _dp(o))
+        return o
+
+    def ncs_F(self, u, chi, n, a, Si, Sf):
+        o = np.zeros(4)
+        n, a, Si, Sf = map(_vec, (n, a, Si, Sf))
+        self.L.or_ncs_F(self.ctx, float(u), float(chi), _dp(n), _dp(a), _dp(Si), _dp(Sf), _dp(o))
+        return o
+
+    def nbw_G(self, delta, omega, chig, ap, bp, vp, Sp, Sm):
+        o = np.zeros(4)
+        ap, bp, vp, Sp, Sm = map(_vec, (ap, bp, vp, Sp, Sm))
+        self.L.or_nbw_G(self.ctx, float(delta), float(omega), float(chig), _dp(ap), _dp(bp),
+                        _dp(vp), _dp(Sp), _dp(Sm), _dp(o))
+        return o
+
+    def table(self, which):
+        n = C.c_uint64()
+        p = self.L.or_table(self.ctx, int(which), C.byref(n))
+        return np.ctypeslib.as_array(p, shape=(n.value,)).copy()
+
+
+def philox(ctr, key):
+    c = (C.c_uint32 * 4)(*ctr)
+    k = (C.c_uint32 * 2)(*key)
+    o = (C.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return list(o)
+
+
+def uniforms(seed, pid, step, ctr):
+    o = np.zeros(2)
+    lib().or_uniforms(int(seed), int(pid), int(step), int(ctr), _dp(o))
+    return o
+
+
+def besselk_scaled(x):
+    o = np.zeros(3)
+    lib().or_besselk_scaled(float(x), _dp(o))
+    return o
+
+
+def scorer_gi_prime(y):
+    return lib().or_scorer_gi_prime(float(y))
+
+
+def field(f, x, y, z, t):
+    E, B = np.zeros(3), np.zeros(3)
+    lib().or_field(C.byref(f), float(x), float(y), float(z), float(t), _dp(E), _dp(B))
+    return E, B
+
+
+_KIND = {"none": FIELD_NONE, "uniform": FIELD_UNIFORM, "plane": FIELD_PLANE,
+         "gauss": FIELD_GAUSS, "grid2d": FIELD_GRID2D}
+
+
+def fields_from_spec(spec: dict, grid=None):
+    """Field descriptor dict (as produced by ``workloads``) -> oracle Fields."""
+    return make_fields(kind=_KIND[spec["kind"]], circular=int(spec.get("circular", 0)),
+                       a0=float(spec.get("a0", 0.0)), phi0=float(spec.get("phi0", 0.0)),
+                       length=float(spec.get("len", 1.0)), w0=float(spec.get("w0", 1.0)),
+                       zf=float(spec.get("zf", 0.0)), E=spec.get("E", (0, 0, 0)),
+                       B=spec.get("B", (0, 0, 0)), grid=grid)
+
+
+class Sim:
+    """One oracle simulation: e-, e+, photon arrays plus the id counter."""
+
+    def __init__(self, orc: Oracle, wl: dict, cap_e=None, cap_p=None, cap_ph=None):
+        self.o = orc
+        ne, npos, nph = len(wl["e"]["id"]), len(wl["pos"]["id"]), len(wl["ph"]["id"])
+        self.e = ParticleArrays(cap_e if cap_e is not None else max(4 * (ne + nph), 16)).load(wl["e"])
+        self.pos = ParticleArrays(cap_p if cap_p is not None else max(4 * (npos + nph), 16)).load(wl["pos"])
+        self.ph = ParticleArrays(cap_ph if cap_ph is not None else max(8 * (ne + npos + nph), 16),
+                                 photon=True).load(wl["ph"])
+        self.fields = fields_from_spec(wl["field"], wl.get("grid"))
+        self.dt = float(wl["dt"])
+        self.t = float(wl.get("t0", 0.0))
+        self.seed = int(wl["seed"])
+        self.step_no = int(wl.get("step0", 0))
+        orc.set_next_id(int(wl["next_id"]))
+
+    def run(self, nsteps, flags):
+        tot = {}
+        for _ in range(nsteps):
+            s = self.o.step(self.e, self.pos, self.ph, self.fields, self.t, self.dt, self.seed,
+                            self.step_no, flags)
+            for k, v in s.items():
+                tot[k] = tot.get(k, 0) + v
+            self.t += self.dt
+            self.step_no += 1
+        return tot
+
+    def state(self):
+        return {"e": self.e.view(), "pos": self.pos.view(), "ph": self.ph.view(),
+                "next_id": self.o.next_id()}

@@ -1,0 +1,110 @@
+/*
+ * qed_oracle.h -- plain, slow, FP64 CPU oracle of the spin/polarization-resolved
+ * strong-field QED particle step of Wan et al., "Simulations of spin/polarization-
+ * resolved laser-plasma interactions in the nonlinear QED regime" (arXiv:2306.11288).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or call
+ * this code: only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline /
+ * reference leg use it.  It shares no code with the CUDA library.
+ *
+ * Units (paper Sec. I, normalisation paragraph): t in 1/omega0, x in 1/k0,
+ * p in m c, E and B in m c omega0 / e, energies in m c^2.
+ *
+ * Parity status per function is stated in oracle/qed_oracle.c's header comment.
+ */
+#ifndef QED_ORACLE_H
+#define QED_ORACLE_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* --- process flags (same meaning as the library's QED_F_* flags) ----------- */
+#define OR_F_NCS        1u   /* nonlinear Compton (Sec. III C)                 */
+#define OR_F_NBW        2u   /* nonlinear Breit-Wheeler (Sec. III D)            */
+#define OR_F_VB         4u   /* vacuum birefringence (Sec. III F)               */
+#define OR_F_SPIN       8u   /* T-BMT precession (Sec. III B, Eq. bmteqn)       */
+#define OR_F_NO_RECOIL 16u   /* test mode: emission leaves p unchanged, no photon */
+#define OR_F_DROP_PHOTONS 32u /* emitted photons are not stored (recoil kept)  */
+
+/* --- particle arrays (structure of arrays, caller-owned) -------------------- */
+typedef struct {
+  double *x, *y, *z;       /* position                                          */
+  double *px, *py, *pz;    /* lepton momentum, or photon k = omega * n          */
+  double *s1, *s2, *s3;    /* lepton spin unit vector, or photon Stokes xi1..3  */
+  double *theta;           /* photons: basis angle (NULL for leptons)           */
+  double *w;               /* macro weight                                      */
+  uint64_t *id;            /* global id                                         */
+  uint64_t n;              /* live count (updated by or_step)                   */
+  uint64_t cap;            /* capacity                                          */
+} or_particles;
+
+/* --- external field descriptor ---------------------------------------------- */
+enum { OR_FIELD_NONE = 0, OR_FIELD_UNIFORM = 1, OR_FIELD_PLANE = 2,
+       OR_FIELD_GAUSS = 3, OR_FIELD_GRID2D = 4 };
+typedef struct {
+  int kind;
+  int circular;            /* 0: linear (E along x), 1: circular              */
+  double a0;               /* peak amplitude per component                     */
+  double phi0, len;        /* sin^2 envelope over phi = t + z in [phi0, phi0+len] */
+  double w0;               /* Gaussian waist (normalised, k0 w0)               */
+  double zf;               /* focal plane z                                    */
+  double E[3], B[3];       /* uniform fields                                   */
+  /* 2D3V Yee grid (x,y), fields constant along z */
+  const float *gEx, *gEy, *gEz, *gBx, *gBy, *gBz;
+  int nx, ny;
+  double dx, dy, x0, y0;
+} or_fields;
+
+typedef struct {
+  uint64_t n_ncs[2];       /* emissions by e-, e+                             */
+  uint64_t n_nbw;          /* pair creations                                   */
+  uint64_t n_range;        /* chi clamped at a table's upper edge              */
+  uint64_t n_drop;         /* births dropped for lack of capacity              */
+  uint64_t n_near;         /* decisions with |r-P| < 1e-6 P (logged)           */
+} or_stats;
+
+typedef struct or_ctx or_ctx;
+
+/* tables of Sec. III C-F; built once (seconds) */
+or_ctx *or_ctx_create(void);
+void or_ctx_destroy(or_ctx *c);
+void or_set_next_id(or_ctx *c, uint64_t id);
+uint64_t or_get_next_id(const or_ctx *c);
+/* near-tie log: (id, step, margin) of decisions within 1e-6 relative */
+void or_near_log(or_ctx *c, uint64_t *ids, uint32_t *steps, double *margins, uint64_t cap);
+
+int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph,
+            const or_fields *f, double t, double dt, uint64_t seed, uint32_t step,
+            uint32_t flags, or_stats *st);
+
+/* --- pieces exposed for the oracle's own pins ------------------------------- */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void or_uniforms(uint64_t seed, uint64_t id, uint32_t step, uint32_t ctr, double u[2]);
+void or_besselk_scaled(double x, double out[3]);   /* e^x{K13, K23, IntK13}(x) */
+void or_ktable(const or_ctx *c, double x, double out[3]);
+void or_ncs_rates(const or_ctx *c, double chi, double out[2]);      /* A, B     */
+double or_ncs_invcdf(const or_ctx *c, int comp, double chi, double t); /* ln u */
+void or_nbw_rates(const or_ctx *c, double chig, double out[2]);     /* T0, T3   */
+double or_nbw_invcdf(const or_ctx *c, int comp, double chig, double t); /* ln d */
+void or_vb_m(const or_ctx *c, double chig, double out[2]);          /* M_par, M_perp */
+double or_scorer_gi_prime(double y);
+void or_field(const or_fields *f, double x, double y, double z, double t,
+              double E[3], double B[3]);
+/* F0..F3 of Eqs. F0-F3 at (u, chi) for spins Si, Sf in frame (n, a) */
+void or_ncs_F(const or_ctx *c, double u, double chi, const double n[3],
+              const double a[3], const double Si[3], const double Sf[3], double F[4]);
+/* G0..G3 of Eqs. G0-G3 (common W0/2 dropped, K's scaled by e^rho) */
+void or_nbw_G(const or_ctx *c, double delta, double omega, double chig,
+              const double ap[3], const double bp[3], const double vp[3],
+              const double Sp[3], const double Sm[3], double G[4]);
+/* raw table access for pins: which = 0 K, 1 ncs rate, 2 ncs inv, 3 nbw rate,
+   4 nbw inv, 5 vb */
+const double *or_table(const or_ctx *c, int which, uint64_t *len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
