@@ -258,16 +258,23 @@ static double or_bary(const double fv[8], double xi) {
   return num / den;
 }
 
-/* integral over [-1, xe] of the polynomial through (GL8X, fv), by GL8 */
-static double or_bary_int(const double fv[8], double xe) {
+/* A panel's density is represented through the logarithms of its node values (the
+ * density falls by many e-folds across a panel in the tails; its logarithm is smooth). */
+static void or_logs(const double *f8, double lf[8]) {
+  for (int k = 0; k < 8; ++k) lf[k] = f8[k] > 0.0 ? log(f8[k]) : -745.0;
+}
+static double or_dens(const double lf[8], double xi) { return exp(or_bary(lf, xi)); }
+
+/* integral over [-1, xe] of exp(log-polynomial), by GL8 on the sub-interval */
+static double or_dens_int(const double lf[8], double xe) {
   double half = 0.5 * (xe + 1.0), mid = 0.5 * (xe - 1.0), s = 0;
-  for (int k = 0; k < 8; ++k) s += GL8W[k] * or_bary(fv, mid + half * GL8X[k]);
+  for (int k = 0; k < 8; ++k) s += GL8W[k] * or_dens(lf, mid + half * GL8X[k]);
   return s * half;
 }
 
 /* Invert a panel-wise cumulative integral.  Panels p = 0..np-1 on [v0 + p H, v0+(p+1)H],
  * node values fv[p*8+k].  cum[p] = integral below panel p's left edge (cum[0] = tail),
- * target measured from below.  Returns v. */
+ * target measured from below.  Returns v; *fout = density at v. */
 static double or_invert_lower(const double *fv, const double *cum, int np, double v0, double H, double target,
                               double *fout) {
   if (target <= cum[0]) { /* analytic lower tail, integral ~ c e^{v/3}: F(v) = F(v0) e^{(v-v0)/3} */
@@ -280,20 +287,22 @@ static double or_invert_lower(const double *fv, const double *cum, int np, doubl
     if (cum[m] <= target) lo = m; else hi = m;
   }
   int p = lo;
-  const double *f8 = fv + (size_t)p * 8;
-  double need = target - cum[p];
-  double total = cum[p + 1] - cum[p];
+  double lf[8];
+  or_logs(fv + (size_t)p * 8, lf);
+  double need = (target - cum[p]) / (0.5 * H);
+  double total = (cum[p + 1] - cum[p]) / (0.5 * H);
   double a = -1.0, b = 1.0, xi = -1.0 + 2.0 * need / total;
-  for (int it = 0; it < 60; ++it) {
-    double g = or_bary_int(f8, xi) * (H * 0.5) - need;
-    double fx = or_bary(f8, xi) * (H * 0.5);
+  if (!(xi > a && xi < b)) xi = 0.0;
+  for (int it = 0; it < 80; ++it) {
+    double g = or_dens_int(lf, xi) - need;
+    double fx = or_dens(lf, xi);
     if (g > 0) b = xi; else a = xi;
     double nx = (fx > 0) ? xi - g / fx : 0.5 * (a + b);
     if (!(nx > a && nx < b)) nx = 0.5 * (a + b);
     if (fabs(nx - xi) < 1e-15) { xi = nx; break; }
     xi = nx;
   }
-  *fout = or_bary(f8, xi);
+  *fout = or_dens(lf, xi);
   return v0 + (p + 0.5 * (xi + 1.0)) * H;
 }
 
@@ -306,22 +315,23 @@ static double or_invert_upper(const double *fv, const double *cumu, int np, doub
     if (cumu[m] > target) lo = m; else hi = m;
   }
   int p = lo;
-  const double *f8 = fv + (size_t)p * 8;
-  double total = cumu[p] - cumu[p + 1];
-  double need = cumu[p] - target;  /* integral from panel left edge to v */
-  double a = -1.0, b = 1.0, xi = -1.0 + 2.0 * need / total;
-  for (int it = 0; it < 60; ++it) {
-    /* integral from v to panel right edge must equal target - cumu[p+1] */
-    double above = (total - or_bary_int(f8, xi) * (H * 0.5));
-    double g = (target - cumu[p + 1]) - above;   /* increases with xi */
-    double fx = or_bary(f8, xi) * (H * 0.5);
+  double lf[8];
+  or_logs(fv + (size_t)p * 8, lf);
+  double above = (target - cumu[p + 1]) / (0.5 * H);   /* mass to leave above v in this panel */
+  double a = -1.0, b = 1.0, xi = 0.0;
+  /* integral from xi to +1 decreases with xi; solve it = above */
+  for (int it = 0; it < 80; ++it) {
+    double half = 0.5 * (1.0 - xi), mid = 0.5 * (1.0 + xi), s = 0;
+    for (int k = 0; k < 8; ++k) s += GL8W[k] * or_dens(lf, mid + half * GL8X[k]);
+    double g = above - s * half;   /* increases with xi */
+    double fx = or_dens(lf, xi);
     if (g > 0) b = xi; else a = xi;
     double nx = (fx > 0) ? xi - g / fx : 0.5 * (a + b);
     if (!(nx > a && nx < b)) nx = 0.5 * (a + b);
     if (fabs(nx - xi) < 1e-15) { xi = nx; break; }
     xi = nx;
   }
-  *fout = or_bary(f8, xi);
+  *fout = or_dens(lf, xi);
   return v0 + (p + 0.5 * (xi + 1.0)) * H;
 }
 
@@ -386,6 +396,7 @@ static void or_build_ncs(or_ctx *c) {
   double *fv = (double *)malloc(sizeof(double) * nn);
   double *cum = (double *)malloc(sizeof(double) * (NCS_NP + 1));
   double *cumu = (double *)malloc(sizeof(double) * (NCS_NP + 1));
+  double *pint = (double *)malloc(sizeof(double) * NCS_NP);
   const double hx = (R_HI - R_LO) / (NCX - 1);
   const double ht = (CT_HI - CT_LO) / (NCT - 1);
   for (int comp = 0; comp < 2; ++comp) {
@@ -403,10 +414,12 @@ static void or_build_ncs(or_ctx *c) {
       for (int p = 0; p < NCS_NP; ++p) {
         double s = 0;
         for (int k = 0; k < 8; ++k) s += GL8W[k] * fv[p * 8 + k];
-        cum[p + 1] = cum[p] + s * NCS_H * 0.5;
+        pint[p] = s * NCS_H * 0.5;
+        cum[p + 1] = cum[p] + pint[p];
       }
+      /* mass above each panel edge, summed from the top (no differences of large sums) */
       cumu[NCS_NP] = 0;
-      for (int p = NCS_NP - 1; p >= 0; --p) cumu[p] = cumu[p + 1] + (cum[p + 1] - cum[p]);
+      for (int p = NCS_NP - 1; p >= 0; --p) cumu[p] = cumu[p + 1] + pint[p];
       double tot = cum[NCS_NP];
       double lnscale = log(1.5 * chi);
       for (int j = 0; j < NCT; ++j) {
@@ -420,7 +433,7 @@ static void or_build_ncs(or_ctx *c) {
       }
     }
   }
-  free(fv); free(cum); free(cumu); free(up); free(ks);
+  free(fv); free(cum); free(cumu); free(pint); free(up); free(ks);
 }
 
 /* ======================================================================= *

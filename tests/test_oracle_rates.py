@@ -261,3 +261,49 @@ def test_ncs_power_vs_paper_q_fits(orc, chi):
     fit2 = (1 + 8.93 * chi + 2.41 * chi * chi) ** (-2 / 3)
     assert q == pytest.approx(fit1, rel=0.03)
     assert q == pytest.approx(fit2, rel=0.04)
+
+
+def _ncs_ccdf(chi, comp, U):
+    """Mass above u of component comp, integrated from u upwards (no 1 - CDF)."""
+    c = 2 / (3 * chi)
+    sg = -1.0 if comp == 0 else 1.0
+    kw = dict(epsabs=0, epsrel=1e-12, limit=500)
+    def dens(u):
+        x = c * u
+        return ((2 + 2 * u + u * u) * special.kv(2 / 3, x) - (1 + u) * _intk13(x) + sg * u * special.kv(1 / 3, x)) / (1 + u) ** 3
+    brk = [U, U * 1.2, U * 1.5, U * 2, U * 4, np.inf]
+    s = sum(integrate.quad(dens, a, b, **kw)[0] for a, b in zip(brk[:-1], brk[1:]))
+    A, B = _ncs_AB(chi)
+    return s / (A + sg * B)
+
+
+@pytest.mark.parametrize("i,comp,j", [(200, 0, 470), (150, 1, 505), (100, 0, 480), (30, 1, 511)])
+def test_ncs_inverse_cdf_far_upper_tail_nodes(orc, i, comp, j):
+    """At table nodes the upper tail (1 - level down to 3e-17) is exact to quadrature."""
+    hx = (math.log(1e3) - math.log(1e-4)) / 255
+    chi = math.exp(math.log(1e-4) + i * hx)
+    t = -38 + j * 76 / 511
+    u = math.exp(orc.ncs_invcdf(comp, chi, t))
+    assert _ncs_ccdf(chi, comp, u) == pytest.approx(1 / (1 + math.exp(t)), rel=1e-9)
+
+
+@pytest.mark.parametrize("chi,comp,t", [(0.8, 0, 30.0), (0.05, 1, 35.0), (2.0, 0, 37.5)])
+def test_ncs_inverse_cdf_far_upper_tail_offgrid(orc, chi, comp, t):
+    u = math.exp(orc.ncs_invcdf(comp, chi, t))
+    assert _ncs_ccdf(chi, comp, u) == pytest.approx(1 / (1 + math.exp(t)), rel=1e-6)
+
+
+@pytest.mark.parametrize("chig,comp,t", [(0.0105, 0, -36.0), (0.3, 1, -33.0), (150.0, 0, -37.0)])
+def test_nbw_inverse_cdf_deep_tail(orc, chig, comp, t):
+    d = math.exp(orc.nbw_invcdf(comp, chig, t))
+    sg = -1.0 if comp == 0 else 1.0
+    r0 = 8 / (3 * chig)
+    def dens(x):
+        rho = 2 / (3 * chig * x * (1 - x))
+        k23 = special.kve(2 / 3, rho) * math.exp(-(rho - r0))
+        ik = _intk13(rho) * math.exp(r0)
+        return ik + (x / (1 - x) + (1 - x) / x) * k23 + sg * k23
+    kw = dict(epsabs=0, epsrel=1e-11, limit=400)
+    num = integrate.quad(dens, 0, d, **kw)[0]
+    den = sum(integrate.quad(dens, a, b, **kw)[0] for a, b in ((0, 0.4), (0.4, 0.5)))
+    assert num / den == pytest.approx(math.exp(t), rel=1e-5)
