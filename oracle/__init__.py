@@ -301,7 +301,7 @@ class Sim:
         self.o = orc
         ne, npos, nph = len(wl["e"]["id"]), len(wl["pos"]["id"]), len(wl["ph"]["id"])
         self.e = ParticleArrays(cap_e if cap_e is not None else max(4 * (ne + nph), 16)).load(wl["e"])
-        self.pos = ParticleArrays(cap_p if cap_p is not None else max(4 * (npos + nph), 16)).load(wl["pos"])
+        self.pos = ParticleArrays(cap_p if cap_p is not None else max(4 * (ne + npos + nph), 16)).load(wl["pos"])
         self.ph = ParticleArrays(cap_ph if cap_ph is not None else max(8 * (ne + npos + nph), 16),
                                  photon=True).load(wl["ph"])
         self.fields = fields_from_spec(wl["field"], wl.get("grid"))

@@ -232,12 +232,11 @@ static void or_gauleg(int n, double *x, double *w) {
     w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * pp * pp);
   }
 }
-static double GL8X[8], GL8W[8], GL64X[64], GL64W[64];
+static double GL8X[8], GL8W[8];
 static double GL8B[8];  /* barycentric weights of the GL8 nodes */
 
 static void or_gl8_bary(void) {
   or_gauleg(8, GL8X, GL8W);
-  or_gauleg(64, GL64X, GL64W);
   for (int j = 0; j < 8; ++j) {
     double p = 1.0;
     for (int k = 0; k < 8; ++k)
@@ -540,17 +539,25 @@ double or_scorer_gi_prime(double y) {
   return acc * h / OR_PI;
 }
 
+/* The upsilon integral: the integrand changes shape in a layer of width ~1/chi_g next to
+ * upsilon = 1 (where x grows from O(1) to infinity), so the interval is split into [0, 1/2]
+ * and panels [1 - 2^-k, 1 - 2^-(k+1)], k = 1..30, each with 8-point Gauss; the remainder
+ * next to 1 contributes below 1e-18. */
 static void or_vb_exact(double chig, double out[2]) {
   double mp = 0, mq = 0;
-  for (int k = 0; k < 64; ++k) {
-    double xg = GL64X[k], wg = GL64W[k];
-    double v = 0.5 * (xg + 1.0), wv = 0.5 * wg;   /* map [-1,1] -> [0,1] */
-    double omv = 1.0 - v * v;
-    double x = 4.0 / (omv * chig);
-    double y = pow(x, 2.0 / 3.0);
-    double g = OR_PI * y * y * or_scorer_gi_prime(y);   /* = pi x^{4/3} Gi'(x^{2/3}) */
-    mp += wv * omv * 0.5 * (1.0 + v * v / 3.0) * g;
-    mq += wv * omv * (1.0 - v * v / 3.0) * g;
+  for (int k = 0; k <= 30; ++k) {
+    double a = (k == 0) ? 0.0 : 1.0 - ldexp(1.0, -k);
+    double b = 1.0 - ldexp(1.0, -(k + 1));
+    double hm = 0.5 * (b - a), c = 0.5 * (b + a);
+    for (int j = 0; j < 8; ++j) {
+      double v = c + hm * GL8X[j], wv = hm * GL8W[j];
+      double omv = 1.0 - v * v;
+      double x = 4.0 / (omv * chig);
+      double y = pow(x, 2.0 / 3.0);
+      double g = OR_PI * y * y * or_scorer_gi_prime(y);   /* = pi x^{4/3} Gi'(x^{2/3}) */
+      mp += wv * omv * 0.5 * (1.0 + v * v / 3.0) * g;
+      mq += wv * omv * (1.0 - v * v / 3.0) * g;
+    }
   }
   out[0] = -11.25 * mp; out[1] = -11.25 * mq;
 }

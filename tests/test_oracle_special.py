@@ -139,3 +139,29 @@ def test_paper_printed_constants():
     alpha = 7.2973525693e-3
     v, tol = rows["rr_ratio_coeff"]
     assert (2 / 3) * alpha * 2 * xil == pytest.approx(v, rel=tol)
+
+
+def test_vb_large_chi_vs_direct_mpmath(orc):
+    """At large chi_gamma the upsilon integrand has a boundary layer next to 1; an
+    independent mpmath quadrature with graded break points pins the table there."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 20
+    chig = 300.0
+
+    def integrand(v, par):
+        om = 1 - v * v
+        if om <= 0:
+            return mp.mpf(0)
+        x = 4 / (om * chig)
+        y = x ** (mp.mpf(2) / 3)
+        g = mp.pi * x ** (mp.mpf(4) / 3) * mp.diff(mp.scorergi, y)
+        w = (1 + v * v / 3) / 2 if par else (1 - v * v / 3)
+        return om * w * g
+
+    pts = [mp.mpf(0), mp.mpf("0.5"), mp.mpf("0.9"), mp.mpf("0.99"), mp.mpf("0.999"), mp.mpf("0.9999"),
+           mp.mpf("0.99999"), mp.mpf(1)]
+    mpar = float(-mp.mpf(45) / 4 * mp.quad(lambda v: integrand(v, True), pts))
+    mperp = float(-mp.mpf(45) / 4 * mp.quad(lambda v: integrand(v, False), pts))
+    m = orc.vb_m(chig)
+    assert m[0] == pytest.approx(mpar, rel=1e-6)
+    assert m[1] == pytest.approx(mperp, rel=1e-6)

@@ -87,9 +87,10 @@ def c2(n=1_000_000, seed=2, gamma0=2.0e4, spread=0.05, a0=100.0, w0_um=3.0, cycl
 # Config 3: 2D3V Yee grid snapshot of an LP pulse reflected off a dense slab
 # ---------------------------------------------------------------------------------
 def c3_grid(nx=4096, ny=2048, a0=150.0, ncrit=100.0, seed=3):
-    """FP32 Yee arrays (cells of lambda/32) holding an LP pulse (E along y) moving along
-    +x plus its reflection (pi phase) off a slab at x_s = 3/4 of the box with plasma
-    frequency sqrt(ncrit) omega0; inside the slab the field decays as exp(-(x-x_s) w_p).
+    """FP32 Yee arrays (cells of lambda/32) holding an LP pulse (E along y, 8 cycles) moving
+    along +x whose centre has reached a slab at x_s = 3/4 of the box (plasma frequency
+    sqrt(ncrit) omega0): in front of the slab the incident field plus its reflection (pi
+    phase, the mirror image of the part beyond x_s); inside, decay as exp(-(x-x_s) w_p).
     A single frozen snapshot; Ez = Bx = By = 0 (2D TE-like, z squeezed)."""
     dx = TWO_PI / 32.0
     dy = dx
@@ -99,8 +100,8 @@ def c3_grid(nx=4096, ny=2048, a0=150.0, ncrit=100.0, seed=3):
     wy = 0.25 * ny * dy             # transverse Gaussian width
     yc = 0.5 * ny * dy
 
-    def profile(xp):  # incident at time 0: centre a distance 0.5 L before the slab
-        ph = xp - (xs - 0.5 * L)
+    def profile(xp):  # incident pulse centred on the slab surface: half already reflected
+        ph = xp - xs
         env = np.where(np.abs(ph) < 0.5 * L, np.cos(math.pi * ph / L) ** 2, 0.0)
         return env
 
