@@ -1,0 +1,230 @@
+/*
+ * qed.h -- C ABI of the GB300 (sm_103a) spin/polarization-resolved strong-field QED
+ * particle step: the per-macroparticle hot path of the particle-in-cell method of
+ * Wan et al., "Simulations of spin/polarization-resolved laser-plasma interactions
+ * in the nonlinear QED regime" (arXiv:2306.11288).
+ *
+ * Units (paper Sec. I, last paragraph): time in 1/omega0, length in 1/k0 (the laser
+ * wavelength is 2 pi), momentum in m c, energy in m c^2, E and B in m c omega0 / e.
+ * The laser wavelength is 1 um, so xi_L = hbar omega0 / m c^2 = 2.42631023867e-6.
+ *
+ * Conventions shared by every call:
+ *   - Every pointer called "device" must point to memory of the current CUDA device;
+ *     "host" pointers are ordinary (preferably pinned) host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls marked "async" only enqueue work; calls marked "syncs" block on `stream`.
+ *   - Every call returns a qed_status.  Arguments are validated on the host before any
+ *     work is enqueued; on a non-OK return nothing has been enqueued and
+ *     qed_last_error() holds a message (thread-local).  Nothing throws across the ABI.
+ *   - Device-side failures (capacity overflow, a bounded wait that gave up, a table
+ *     range clamp) never trap: kernels set bits in a device status word that
+ *     qed_read_status() returns.
+ *   - The library never frees caller memory.
+ */
+#ifndef QED_H
+#define QED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QED_OK = 0,
+  QED_ERR_INVALID_ARG = 1,     /* host-side validation failed                        */
+  QED_ERR_CUDA = 2,            /* a CUDA runtime call failed (message says which)    */
+  QED_ERR_CAPACITY = 3,        /* births exceeded a particle array's capacity         */
+  QED_ERR_NOT_INITIALIZED = 4, /* NULL or destroyed context                          */
+  QED_ERR_TIMEOUT = 5,         /* a bounded device wait gave up                       */
+  QED_WARN_TABLE_RANGE = 6     /* chi above a table's range was clamped              */
+} qed_status;
+
+/* bits of the device status word (qed_read_status) */
+#define QED_STATUS_CAPACITY 1u
+#define QED_STATUS_TIMEOUT 2u
+#define QED_STATUS_TABLE_RANGE 4u
+
+typedef enum { QED_ELECTRON = 0, QED_POSITRON = 1, QED_PHOTON = 2 } qed_species;
+
+/* Storage precision of a particle set.
+ * QED_PREC_F64:   every array is double.
+ * QED_PREC_MIXED: positions x, y, z are double; momenta, spins/Stokes, basis angle and
+ *                 weights are float; arithmetic is FP32 except the FP64 islands (phase
+ *                 and position accumulation, chi under cancellation, the u -> 1 branch). */
+typedef enum { QED_PREC_F64 = 0, QED_PREC_MIXED = 1 } qed_precision;
+
+/* process flags of qed_step (paper Sec. IV orders them: Lorentz & T-BMT => VB => NBW => NCS) */
+#define QED_F_NCS 1u           /* spin/polarization-resolved nonlinear Compton (Sec. III C)   */
+#define QED_F_NBW 2u           /* polarization/spin-resolved nonlinear Breit-Wheeler (III D)  */
+#define QED_F_VB 4u            /* vacuum birefringence rotation of photon Stokes (III F)      */
+#define QED_F_SPIN 8u          /* T-BMT spin precession (Sec. III B, Eq. bmteqn)             */
+#define QED_F_NO_RECOIL 16u    /* test mode: emission changes the spin only, no photon born   */
+#define QED_F_DROP_PHOTONS 32u /* emitted photons are not stored (recoil is applied)          */
+
+/* Structure-of-arrays view of one species, caller-owned device memory.  Element i of
+ * every array describes particle i.  Element types follow qed_precision (above):
+ *   x, y, z   : double always
+ *   px,py,pz  : lepton momentum p (m c) or photon wave vector k = omega n (m c)
+ *   s1,s2,s3  : lepton spin unit vector S (Sec. III B), or photon Stokes parameters
+ *               xi1..xi3 (Sec. III C, Stokes parameters paragraph)
+ *   theta     : photons only: basis angle; P1 = cos(theta) e1 + sin(theta) e2 with
+ *               e1 = unit(y_hat x n) (unit(n x x_hat) within 1e-10 rad of +-y), e2 = n x e1,
+ *               and P2 = n x P1.  The Stokes parameters refer to (P1, P2, n).  NULL for leptons.
+ *   w         : macro-particle weight (copied to newborns)
+ *   id        : uint64 global id (newborns get ids from the context's counter)
+ * Arrays must hold `capacity` elements; the first `n` are live. */
+typedef struct {
+  void *x, *y, *z;
+  void *px, *py, *pz;
+  void *s1, *s2, *s3;
+  void *theta;
+  void *w;
+  uint64_t *id;
+} qed_soa;
+
+/* External field (paper Sec. II D: force deposition onto particles).
+ * kind QED_FIELD_UNIFORM : constant E, B.
+ * kind QED_FIELD_PLANE   : plane wave moving along -z, phase phi = t + z, sin^2 envelope
+ *                          g = a0 sin^2(pi (phi-phi0)/len) on [phi0, phi0+len] (0 outside);
+ *                          E = g (cos phi, circular ? sin phi : 0, 0), B = (-z_hat) x E.
+ * kind QED_FIELD_GAUSS   : first-order paraxial Gaussian moving along -z, focus z = zf,
+ *                          waist w0, Rayleigh length w0^2/2; same envelope in phi; carrier
+ *                          phase phi - r^2 zeta/(2(zeta^2+zR^2)) + atan(zeta/zR), zeta = zf - z;
+ *                          amplitude w0/w(zeta) exp(-r^2/w^2); longitudinal parts neglected.
+ * kind QED_FIELD_GRID2D  : 2D3V Yee grid (z squeezed; paper Sec. II B figure "yeegrid"),
+ *                          float arrays [ny][nx] in device memory with Ex(i+1/2,j),
+ *                          Ey(i,j+1/2), Ez(i,j), Bx(i,j+1/2), By(i+1/2,j), Bz(i+1/2,j+1/2);
+ *                          cell (i, j) at (x0 + i dx, y0 + j dy); gathered with the TSC
+ *                          shape of Sec. II E (nodes outside the grid contribute zero). */
+typedef enum { QED_FIELD_NONE = 0, QED_FIELD_UNIFORM = 1, QED_FIELD_PLANE = 2,
+               QED_FIELD_GAUSS = 3, QED_FIELD_GRID2D = 4 } qed_field_kind;
+
+typedef struct {
+  int kind;
+  int circular;
+  double a0, phi0, len, w0, zf;
+  double E[3], B[3];
+  const float *gEx, *gEy, *gEz, *gBx, *gBy, *gBz;
+  int nx, ny;
+  double dx, dy, x0, y0;
+} qed_fields;
+
+/* Per-step event counters accumulated on the device (add-only). */
+typedef struct {
+  uint64_t n_ncs[2];     /* photon emissions by e-, e+                         */
+  uint64_t n_nbw;        /* pairs created                                      */
+  uint64_t n_range;      /* chi clamped at a table's upper edge                */
+  uint64_t n_drop;       /* births dropped for lack of capacity                */
+  uint64_t n_steps;      /* steps accumulated                                  */
+} qed_step_stats;
+
+typedef struct qed_ctx qed_ctx;             /* tables, id counter, scratch, status   */
+typedef struct qed_particles qed_particles; /* non-owning SoA view + device count      */
+
+/* Build the QED lookup tables on the current device (FP64 quadrature on the GPU) and
+ * return a context.  Tables: scaled K_1/3, K_2/3, IntK_1/3 (Eqs. F0-F3, G0-G3); the
+ * u-integrated spin-resolved NCS rate of Eq. Wspin2; inverse CDFs of the photon energy
+ * fraction for spin projections +-1; the spin-summed NBW rate (Eq. BW summed over both
+ * spins) and inverse CDFs of the positron energy fraction for xi3' = +-1; the VB
+ * functions M_par, M_perp of Sec. III F.  Syncs `stream`.  *out receives a context
+ * that the caller releases with qed_destroy.  Errors: QED_ERR_INVALID_ARG (out NULL),
+ * QED_ERR_CUDA. */
+qed_status qed_init_tables(qed_ctx **out, void *stream);
+
+/* Release a context and its device memory (tables, scratch).  Syncs the device. */
+qed_status qed_destroy(qed_ctx *ctx);
+
+/* Wrap caller-owned device arrays as one species (paper Sec. IV: ParticleList).
+ * `buffers` pointers are copied; the arrays must outlive the returned object.  All
+ * particle sets stepped together must share one precision.  `n` <= `capacity`.
+ * Allocates a device count word (and grows the context's scratch to the capacity).
+ * Syncs `stream`.  Errors: QED_ERR_INVALID_ARG (NULL array, n > capacity, photon
+ * without theta), QED_ERR_CUDA. */
+qed_status particles_create(qed_ctx *ctx, qed_species species, const qed_soa *buffers,
+                            uint64_t n, uint64_t capacity, qed_precision prec, void *stream,
+                            qed_particles **out);
+
+/* Live count (device word) into *n.  Syncs `stream`. */
+qed_status particles_count(const qed_particles *p, uint64_t *n, void *stream);
+
+/* Overwrite the live count (e.g. after refilling the arrays).  Async. */
+qed_status particles_set_count(qed_particles *p, uint64_t n, void *stream);
+
+/* Release the wrapper and its count word (not the caller's arrays).  Syncs the device. */
+qed_status particles_destroy(qed_particles *p);
+
+/* Id counter of newborn particles (ids of primaries are the caller's).  set: async;
+ * get: syncs `stream`. */
+qed_status qed_set_next_id(qed_ctx *ctx, uint64_t next_id, void *stream);
+qed_status qed_get_next_id(qed_ctx *ctx, uint64_t *next_id, void *stream);
+
+/* One time step of every live particle (async, graph-capturable: no host sync, no
+ * allocation).  Order (paper Sec. IV and the leapfrog of Sec. II F):
+ *   photons: gather E, B at x^n, t; rotate Stokes into the local pair frame (Eq.
+ *     rotation); VB phase (Eq. rotation2) if QED_F_VB; NBW decision and pair sampling
+ *     (Sec. III D) if QED_F_NBW; survivors move x += dt n; decayed photons are removed
+ *     (stable); pairs are born at the photon's x^n.
+ *   leptons (e- then e+): Boris push (Eqs. boris1-6), T-BMT rotation (Eqs. bmt-boris1-4)
+ *     if QED_F_SPIN, x^{n+1} = x^n + dt p^{n+1/2}/gamma; chi_e; NCS decision from the
+ *     spin-resolved total rate (Eq. Wspin2 integrated over u); no-emission spin update
+ *     and collapse, or emission: photon energy, recoil, spin collapse along the SQA of
+ *     Eq. F0, photon pure state from Eqs. F1-F3; photons are born at x^{n+1}.
+ *   newborns are appended after the survivors and are first advanced at the next step.
+ * Ids of newborns: next_id + ... in the order NBW pairs (photon order; e- then e+), then
+ * NCS photons (e- order, then e+ order).  Random numbers: Philox4x32-10 with key = seed
+ * and counter = (id_lo, id_hi, step, stream index).
+ * e, pos, ph may be NULL (an absent species); all given sets share one precision.
+ * dev_stats (device memory, optional) accumulates counters.
+ * Errors: QED_ERR_INVALID_ARG (dt <= 0 or not finite, precision mismatch, unknown
+ * field kind, NULL grid arrays, NBW without lepton arrays), QED_ERR_NOT_INITIALIZED,
+ * QED_ERR_CUDA (launch failure). */
+qed_status qed_step(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed_particles *ph,
+                    const qed_fields *f, double t, double dt, uint64_t seed, uint32_t step,
+                    uint32_t flags, qed_step_stats *dev_stats, void *stream);
+
+/* End-to-end form of qed_step for callers whose particles live in host memory: copies
+ * the live part of each given host SoA (same layout and precision as the device set,
+ * counts n_host[3] for e-, e+, photons) into the device sets, runs one qed_step, and
+ * copies the device sets back (capacity elements are available in the host arrays;
+ * n_host is updated with the new counts).  host_soa[k] may be NULL for an absent
+ * species.  Syncs `stream`. */
+qed_status qed_step_host(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed_particles *ph,
+                         const qed_soa *host_e, const qed_soa *host_pos, const qed_soa *host_ph,
+                         uint64_t n_host[3], const qed_fields *f, double t, double dt,
+                         uint64_t seed, uint32_t step, uint32_t flags, void *stream);
+
+/* Device status word (QED_STATUS_* bits) accumulated since the last clear; syncs
+ * `stream`.  clear != 0 resets it. */
+qed_status qed_read_status(qed_ctx *ctx, uint32_t *status, int clear, void *stream);
+
+/* Diagnostics: per-kernel timing.  While enabled, qed_step records CUDA events around
+ * its two kernels (photon kernel, lepton kernel) on `stream` and waits for them, adding
+ * the elapsed milliseconds to two accumulators (so every step syncs its stream).
+ * qed_get_timing returns and clears them with the number of steps timed.  Off by default. */
+qed_status qed_set_timing(qed_ctx *ctx, int enable);
+qed_status qed_get_timing(qed_ctx *ctx, double ms[2], uint64_t *steps);
+
+/* Diagnostics: copy one FP64 lookup table of the context to host memory (syncs).
+ * which: 0 scaled K13, K23, IntK13 values then their d/dln x, [2][3][1024] on ln x in
+ *          [ln 1e-3, ln 1e5];
+ *        1 NCS A(chi)/chi then B(chi)/chi, [2][512] on ln chi in [ln 1e-4, ln 1e3];
+ *        2 NCS inverse CDF: ln u then d(ln u)/dt, [2][2 spin projections +1,-1][256 chi]
+ *          [512 t], t = logit(level) in [-38, 38];
+ *        3 NBW T0 then T3, each times exp(8/(3 chi_g)), [2][256] on ln chi_g in
+ *          [ln 1e-2, ln 1e3];
+ *        4 NBW half inverse CDF: ln delta then d(ln delta)/dt, [2][2 xi3' = +1,-1][256 chi_g]
+ *          [256 t], t = ln(level of the half distribution) in [-38, 0];
+ *        5 VB M_par then M_perp, [2][1024] on ln chi_g in [ln 1e-3, ln 1e3].
+ * *len receives the element count; host may be NULL to query it; otherwise cap must be
+ * >= the count.  Errors: QED_ERR_INVALID_ARG (bad which, cap too small). */
+qed_status qed_copy_table(qed_ctx *ctx, int which, double *host, uint64_t cap, uint64_t *len, void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *qed_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,334 @@
+"""Thin Python binding of the GB300 SF-QED step library (include/qed.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA kernels of
+``libqed_gb300.so``.  PyTorch provides device memory and streams.  If the shared
+library has not been built, importing the binding's functions raises -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqed_gb300.so")
+
+QED_OK, QED_ERR_INVALID_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY = 0, 1, 2, 3
+QED_ERR_NOT_INITIALIZED, QED_ERR_TIMEOUT, QED_WARN_TABLE_RANGE = 4, 5, 6
+QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
+QED_PREC_F64, QED_PREC_MIXED = 0, 1
+QED_F_NCS, QED_F_NBW, QED_F_VB, QED_F_SPIN, QED_F_NO_RECOIL, QED_F_DROP_PHOTONS = 1, 2, 4, 8, 16, 32
+QED_STATUS_CAPACITY, QED_STATUS_TIMEOUT, QED_STATUS_TABLE_RANGE = 1, 2, 4
+FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
+
+ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particles_count",
+                 "particles_set_count", "particles_destroy", "qed_set_next_id", "qed_get_next_id",
+                 "qed_step", "qed_step_host", "qed_read_status", "qed_copy_table", "qed_set_timing", "qed_get_timing",
+                 "qed_last_error")
+
+
+class qed_soa(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("x", "y", "z", "px", "py", "pz", "s1", "s2", "s3", "theta", "w")] + [
+        ("id", C.c_void_p)]
+
+
+class qed_fields(C.Structure):
+    _fields_ = [("kind", C.c_int), ("circular", C.c_int), ("a0", C.c_double), ("phi0", C.c_double),
+                ("len", C.c_double), ("w0", C.c_double), ("zf", C.c_double), ("E", C.c_double * 3),
+                ("B", C.c_double * 3), ("gEx", C.c_void_p), ("gEy", C.c_void_p), ("gEz", C.c_void_p),
+                ("gBx", C.c_void_p), ("gBy", C.c_void_p), ("gBz", C.c_void_p), ("nx", C.c_int),
+                ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double), ("x0", C.c_double),
+                ("y0", C.c_double)]
+
+
+class qed_step_stats(C.Structure):
+    _fields_ = [("n_ncs", C.c_uint64 * 2), ("n_nbw", C.c_uint64), ("n_range", C.c_uint64),
+                ("n_drop", C.c_uint64), ("n_steps", C.c_uint64)]
+
+
+class QedError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib():
+    """Load libqed_gb300.so (built by ``build()``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise QedError(f"{LIB_PATH} is missing: run paper_2306_11288_gb300.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, u64, u32, d = C.c_void_p, C.c_uint64, C.c_uint32, C.c_double
+        L.qed_init_tables.argtypes = [C.POINTER(vp), vp]
+        L.qed_destroy.argtypes = [vp]
+        L.particles_create.argtypes = [vp, C.c_int, C.POINTER(qed_soa), u64, u64, C.c_int, vp, C.POINTER(vp)]
+        L.particles_count.argtypes = [vp, C.POINTER(u64), vp]
+        L.particles_set_count.argtypes = [vp, u64, vp]
+        L.particles_destroy.argtypes = [vp]
+        L.qed_set_next_id.argtypes = [vp, u64, vp]
+        L.qed_get_next_id.argtypes = [vp, C.POINTER(u64), vp]
+        L.qed_step.argtypes = [vp, vp, vp, vp, C.POINTER(qed_fields), d, d, u64, u32, u32, vp, vp]
+        L.qed_step_host.argtypes = [vp, vp, vp, vp, C.POINTER(qed_soa), C.POINTER(qed_soa),
+                                    C.POINTER(qed_soa), C.POINTER(u64), C.POINTER(qed_fields), d, d, u64,
+                                    u32, u32, vp]
+        L.qed_read_status.argtypes = [vp, C.POINTER(u32), C.c_int, vp]
+        L.qed_copy_table.argtypes = [vp, C.c_int, C.POINTER(C.c_double), u64, C.POINTER(u64), vp]
+        L.qed_set_timing.argtypes = [vp, C.c_int]
+        L.qed_get_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(u64)]
+        L.qed_last_error.restype = C.c_char_p
+        for name in ABI_FUNCTIONS:
+            if name != "qed_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def _check(rc: int, what: str):
+    if rc != QED_OK:
+        msg = lib().qed_last_error().decode(errors="replace")
+        raise QedError(f"{what} failed with status {rc}: {msg}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream)
+
+
+# ---- the C-ABI calls, same names -------------------------------------------------------
+def qed_init_tables(stream=None):
+    h = C.c_void_p()
+    _check(lib().qed_init_tables(C.byref(h), _stream(stream)), "qed_init_tables")
+    return h
+
+
+def qed_destroy(ctx):
+    _check(lib().qed_destroy(ctx), "qed_destroy")
+
+
+def particles_create(ctx, species, soa: qed_soa, n, cap, prec, stream=None):
+    h = C.c_void_p()
+    _check(lib().particles_create(ctx, int(species), C.byref(soa), int(n), int(cap), int(prec),
+                                  _stream(stream), C.byref(h)), "particles_create")
+    return h
+
+
+def particles_count(p, stream=None) -> int:
+    v = C.c_uint64()
+    _check(lib().particles_count(p, C.byref(v), _stream(stream)), "particles_count")
+    return int(v.value)
+
+
+def particles_set_count(p, n, stream=None):
+    _check(lib().particles_set_count(p, int(n), _stream(stream)), "particles_set_count")
+
+
+def particles_destroy(p):
+    _check(lib().particles_destroy(p), "particles_destroy")
+
+
+def qed_set_next_id(ctx, i, stream=None):
+    _check(lib().qed_set_next_id(ctx, int(i), _stream(stream)), "qed_set_next_id")
+
+
+def qed_get_next_id(ctx, stream=None) -> int:
+    v = C.c_uint64()
+    _check(lib().qed_get_next_id(ctx, C.byref(v), _stream(stream)), "qed_get_next_id")
+    return int(v.value)
+
+
+def qed_step(ctx, e, pos, ph, fields: qed_fields, t, dt, seed, step, flags, dev_stats=None, stream=None):
+    _check(lib().qed_step(ctx, e, pos, ph, C.byref(fields), float(t), float(dt), int(seed), int(step),
+                          int(flags), dev_stats, _stream(stream)), "qed_step")
+
+
+def qed_step_host(ctx, e, pos, ph, host_e, host_pos, host_ph, n_host, fields, t, dt, seed, step, flags,
+                  stream=None):
+    arr = (C.c_uint64 * 3)(*[int(v) for v in n_host])
+    _check(lib().qed_step_host(ctx, e, pos, ph, C.byref(host_e) if host_e else None,
+                               C.byref(host_pos) if host_pos else None, C.byref(host_ph) if host_ph else None,
+                               arr, C.byref(fields), float(t), float(dt), int(seed), int(step), int(flags),
+                               _stream(stream)), "qed_step_host")
+    return [int(v) for v in arr]
+
+
+def qed_read_status(ctx, clear=False, stream=None) -> int:
+    v = C.c_uint32()
+    _check(lib().qed_read_status(ctx, C.byref(v), int(bool(clear)), _stream(stream)), "qed_read_status")
+    return int(v.value)
+
+
+def qed_copy_table(ctx, which, stream=None) -> np.ndarray:
+    n = C.c_uint64()
+    _check(lib().qed_copy_table(ctx, int(which), None, 0, C.byref(n), _stream(stream)), "qed_copy_table")
+    out = np.zeros(n.value)
+    _check(lib().qed_copy_table(ctx, int(which), out.ctypes.data_as(C.POINTER(C.c_double)), n.value,
+                                C.byref(n), _stream(stream)), "qed_copy_table")
+    return out
+
+
+def qed_set_timing(ctx, enable: bool):
+    _check(lib().qed_set_timing(ctx, int(bool(enable))), "qed_set_timing")
+
+
+def qed_get_timing(ctx):
+    ms = (C.c_double * 2)()
+    n = C.c_uint64()
+    _check(lib().qed_get_timing(ctx, ms, C.byref(n)), "qed_get_timing")
+    return [ms[0], ms[1]], int(n.value)
+
+
+def qed_last_error() -> str:
+    return lib().qed_last_error().decode(errors="replace")
+
+
+# ---- memory plumbing (torch tensors as storage) ----------------------------------------------
+_NAMES = ("x", "y", "z", "px", "py", "pz", "s1", "s2", "s3", "theta", "w")
+
+
+class Species:
+    """Device SoA (torch tensors) for one species, wrapped as a qed_particles handle."""
+
+    def __init__(self, ctx, species, cap, prec=QED_PREC_F64, device="cuda", pin_host=False):
+        import torch
+        self.torch = torch
+        self.ctx, self.species, self.cap, self.prec = ctx, species, int(cap), prec
+        rt = torch.float64 if prec == QED_PREC_F64 else torch.float32
+        self.t = {}
+        for k in _NAMES:
+            if k == "theta" and species != QED_PHOTON:
+                continue
+            dt = torch.float64 if k in ("x", "y", "z") else rt
+            self.t[k] = torch.zeros(max(self.cap, 1), dtype=dt, device=device)
+        self.t["id"] = torch.zeros(max(self.cap, 1), dtype=torch.int64, device=device)
+        self.soa = qed_soa()
+        for k, v in self.t.items():
+            setattr(self.soa, k, v.data_ptr())
+        self.handle = particles_create(ctx, species, self.soa, 0, self.cap, prec)
+        self._closed = False
+
+    def load(self, d: dict, stream=None):
+        n = len(d["id"])
+        if n > self.cap:
+            raise ValueError("more particles than capacity")
+        for k, v in self.t.items():
+            if k == "id":
+                src = np.asarray(d["id"], dtype=np.uint64).view(np.int64)
+            elif k in d:
+                src = np.asarray(d[k], dtype=np.float64)
+            else:
+                continue
+            if n:
+                v[:n].copy_(self.torch.from_numpy(np.ascontiguousarray(src)).to(v.dtype))
+        self.torch.cuda.synchronize()
+        particles_set_count(self.handle, n, stream)
+        return self
+
+    def count(self, stream=None) -> int:
+        return particles_count(self.handle, stream)
+
+    def to_dict(self) -> dict:
+        n = self.count()
+        out = {}
+        for k, v in self.t.items():
+            a = v[:n].cpu().numpy()
+            out[k] = a.view(np.uint64) if k == "id" else a.astype(np.float64)
+        return out
+
+    def close(self):
+        if not self._closed:
+            self._closed = True
+            particles_destroy(self.handle)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fields_from_spec(spec: dict, grid=None) -> qed_fields:
+    """Field descriptor dict -> qed_fields; grid components must be CUDA float32 tensors."""
+    f = qed_fields()
+    f.kind = FIELD_KIND[spec["kind"]]
+    f.circular = int(spec.get("circular", 0))
+    f.a0 = float(spec.get("a0", 0.0))
+    f.phi0 = float(spec.get("phi0", 0.0))
+    f.len = float(spec.get("len", 1.0))
+    f.w0 = float(spec.get("w0", 1.0))
+    f.zf = float(spec.get("zf", 0.0))
+    f.E[:] = [float(v) for v in spec.get("E", (0, 0, 0))]
+    f.B[:] = [float(v) for v in spec.get("B", (0, 0, 0))]
+    if grid is not None:
+        for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz"):
+            setattr(f, "g" + k, grid[k].data_ptr())
+        f.ny, f.nx = grid["Ey"].shape
+        f.dx, f.dy = float(grid["dx"]), float(grid["dy"])
+        f.x0, f.y0 = float(grid.get("x0", 0.0)), float(grid.get("y0", 0.0))
+    return f
+
+
+class Simulation:
+    """One context + e-, e+, photon sets stepping together (device resident)."""
+
+    def __init__(self, wl: dict, prec=QED_PREC_F64, cap_e=None, cap_p=None, cap_ph=None, ctx=None):
+        import torch
+        self.torch = torch
+        self.ctx = ctx if ctx is not None else qed_init_tables()
+        self.own_ctx = ctx is None
+        ne, npos, nph = len(wl["e"]["id"]), len(wl["pos"]["id"]), len(wl["ph"]["id"])
+        self.e = Species(self.ctx, QED_ELECTRON, cap_e if cap_e is not None else max(4 * (ne + nph), 16), prec).load(wl["e"])
+        self.pos = Species(self.ctx, QED_POSITRON, cap_p if cap_p is not None else max(4 * (ne + npos + nph), 16), prec).load(wl["pos"])
+        self.ph = Species(self.ctx, QED_PHOTON, cap_ph if cap_ph is not None else max(8 * (ne + npos + nph), 16), prec).load(wl["ph"])
+        self.grid = None
+        if wl["field"]["kind"] == "grid2d":
+            g = wl["grid"]
+            self.grid = {k: torch.as_tensor(np.ascontiguousarray(g[k]), dtype=torch.float32, device="cuda")
+                         for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")}
+            self.grid.update({k: g[k] for k in ("dx", "dy") if k in g})
+            self.grid.update({k: g.get(k, 0.0) for k in ("x0", "y0")})
+        self.fields = fields_from_spec(wl["field"], self.grid)
+        self.dt = float(wl["dt"])
+        self.t = float(wl.get("t0", 0.0))
+        self.seed = int(wl["seed"])
+        self.step_no = int(wl.get("step0", 0))
+        self.stats = torch.zeros(6, dtype=torch.int64, device="cuda")
+        qed_set_next_id(self.ctx, int(wl["next_id"]))
+        qed_read_status(self.ctx, clear=True)
+
+    def run(self, nsteps, flags, stream=None):
+        for _ in range(nsteps):
+            qed_step(self.ctx, self.e.handle, self.pos.handle, self.ph.handle, self.fields, self.t, self.dt,
+                     self.seed, self.step_no, flags, self.stats.data_ptr(), stream)
+            self.t += self.dt
+            self.step_no += 1
+
+    def state(self) -> dict:
+        self.torch.cuda.synchronize()
+        return {"e": self.e.to_dict(), "pos": self.pos.to_dict(), "ph": self.ph.to_dict(),
+                "next_id": qed_get_next_id(self.ctx)}
+
+    def counters(self) -> dict:
+        s = self.stats.cpu().numpy()
+        return {"n_ncs_e": int(s[0]), "n_ncs_p": int(s[1]), "n_nbw": int(s[2]), "n_range": int(s[3]),
+                "n_drop": int(s[4]), "n_steps": int(s[5])}
+
+    def status(self, clear=False) -> int:
+        return qed_read_status(self.ctx, clear)
+
+    def close(self):
+        for s in (self.e, self.pos, self.ph):
+            s.close()
+        if self.own_ctx:
+            qed_destroy(self.ctx)

@@ -1,0 +1,380 @@
+// qed_api.cu -- the C ABI declared in include/qed.h: argument validation, context and
+// particle-set bookkeeping, and the host-buffer (end-to-end) form of the step.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "qed_common.cuh"
+#include "qed_internal.h"
+
+namespace qedk {
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+}  // namespace qedk
+
+using namespace qedk;
+
+#define FAIL(code, ...)       \
+  do {                        \
+    set_error(__VA_ARGS__);   \
+    return code;              \
+  } while (0)
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) FAIL(QED_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" const char* qed_last_error(void) { return g_err; }
+
+extern "C" qed_status qed_init_tables(qed_ctx** out, void* stream) {
+  if (!out) FAIL(QED_ERR_INVALID_ARG, "qed_init_tables: out is NULL");
+  *out = nullptr;
+  g_err[0] = 0;
+  qed_ctx* c = (qed_ctx*)calloc(1, sizeof(qed_ctx));
+  if (!c) FAIL(QED_ERR_INVALID_ARG, "qed_init_tables: host allocation failed");
+  CK(cudaGetDevice(&c->device));
+  cudaError_t e = cudaMalloc(&c->tab64, sizeof(double) * kTableLen);
+  if (e == cudaSuccess) e = cudaMalloc(&c->tab32, sizeof(float) * kTableLen);
+  if (e == cudaSuccess) e = cudaMalloc(&c->st, sizeof(DevState));
+  if (e != cudaSuccess) {
+    cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st); free(c);
+    FAIL(QED_ERR_CUDA, "qed_init_tables: cudaMalloc: %s", cudaGetErrorString(e));
+  }
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  h.epoch = 1;
+  e = cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, S(stream));
+  if (e != cudaSuccess) {
+    cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st); free(c);
+    FAIL(QED_ERR_CUDA, "qed_init_tables: %s", cudaGetErrorString(e));
+  }
+  qed_status r = build_tables(c->tab64, c->tab32, S(stream));
+  if (r == QED_OK) r = step_grid_sizes(QED_PREC_F64, &c->nblk[0][0], &c->nblk[0][1]);
+  if (r == QED_OK) r = step_grid_sizes(QED_PREC_MIXED, &c->nblk[1][0], &c->nblk[1][1]);
+  if (r != QED_OK) {
+    cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st); free(c);
+    return r;
+  }
+  c->alive = 1;
+  *out = c;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_destroy(qed_ctx* c) {
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_destroy: invalid context");
+  cudaDeviceSynchronize();
+  cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st);
+  cudaFree(c->look[0]); cudaFree(c->look[1]);
+  for (int k = 0; k < 3; ++k)
+    if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+  c->alive = 0;
+  free(c);
+  return QED_OK;
+}
+
+static qed_status grow_look(qed_ctx* c, int which, unsigned long long need, cudaStream_t s) {
+  if (need <= c->look_cap[which]) return QED_OK;
+  unsigned long long* p = nullptr;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMalloc(&p, sizeof(unsigned long long) * need));
+  CK(cudaMemsetAsync(p, 0, sizeof(unsigned long long) * need, s));
+  CK(cudaStreamSynchronize(s));
+  cudaFree(c->look[which]);
+  c->look[which] = p;
+  c->look_cap[which] = need;
+  return QED_OK;
+}
+
+static unsigned long long tiles_of(unsigned long long n) { return (n + kTile - 1) / kTile; }
+
+extern "C" qed_status particles_create(qed_ctx* c, qed_species sp, const qed_soa* b, uint64_t n, uint64_t cap,
+                                       qed_precision prec, void* stream, qed_particles** out) {
+  if (!out) FAIL(QED_ERR_INVALID_ARG, "particles_create: out is NULL");
+  *out = nullptr;
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "particles_create: invalid context");
+  if (!b) FAIL(QED_ERR_INVALID_ARG, "particles_create: buffers is NULL");
+  if (sp < QED_ELECTRON || sp > QED_PHOTON) FAIL(QED_ERR_INVALID_ARG, "particles_create: bad species %d", (int)sp);
+  if (prec != QED_PREC_F64 && prec != QED_PREC_MIXED) FAIL(QED_ERR_INVALID_ARG, "particles_create: bad precision");
+  if (n > cap) FAIL(QED_ERR_INVALID_ARG, "particles_create: n (%llu) > capacity (%llu)",
+                    (unsigned long long)n, (unsigned long long)cap);
+  if (cap > (1ull << 37)) FAIL(QED_ERR_INVALID_ARG, "particles_create: capacity above 2^37");
+  if (cap > 0) {
+    const void* req[] = {b->x, b->y, b->z, b->px, b->py, b->pz, b->s1, b->s2, b->s3, b->w, b->id};
+    for (const void* p : req)
+      if (!p) FAIL(QED_ERR_INVALID_ARG, "particles_create: a required array is NULL");
+    if (sp == QED_PHOTON && !b->theta) FAIL(QED_ERR_INVALID_ARG, "particles_create: photons need theta");
+  }
+  cudaStream_t s = S(stream);
+  // look-back words: photons alone; e- and e+ share the lepton tile space
+  qed_status r = grow_look(c, sp == QED_PHOTON ? 0 : 1, 2 * tiles_of(cap) + 2, s);
+  if (r != QED_OK) return r;
+  qed_particles* p = (qed_particles*)calloc(1, sizeof(qed_particles));
+  p->ctx = c;
+  p->species = sp;
+  p->prec = prec;
+  p->soa = *b;
+  p->cap = cap;
+  unsigned long long nn = n;
+  CK(cudaMemcpyAsync(&c->st->n_live[sp], &nn, sizeof(nn), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  *out = p;
+  return QED_OK;
+}
+
+extern "C" qed_status particles_count(const qed_particles* p, uint64_t* n, void* stream) {
+  if (!p || !n) FAIL(QED_ERR_INVALID_ARG, "particles_count: NULL argument");
+  if (!p->ctx || !p->ctx->alive) FAIL(QED_ERR_NOT_INITIALIZED, "particles_count: context destroyed");
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, &p->ctx->st->n_live[p->species], sizeof(v), cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  *n = v;
+  return QED_OK;
+}
+
+extern "C" qed_status particles_set_count(qed_particles* p, uint64_t n, void* stream) {
+  if (!p) FAIL(QED_ERR_INVALID_ARG, "particles_set_count: NULL");
+  if (n > p->cap) FAIL(QED_ERR_INVALID_ARG, "particles_set_count: n > capacity");
+  static thread_local unsigned long long hv;
+  hv = n;
+  CK(cudaMemcpyAsync(&p->ctx->st->n_live[p->species], &hv, sizeof(hv), cudaMemcpyHostToDevice, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  return QED_OK;
+}
+
+extern "C" qed_status particles_destroy(qed_particles* p) {
+  if (!p) FAIL(QED_ERR_INVALID_ARG, "particles_destroy: NULL");
+  free(p);
+  return QED_OK;
+}
+
+extern "C" qed_status qed_set_next_id(qed_ctx* c, uint64_t id, void* stream) {
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_set_next_id: invalid context");
+  static thread_local unsigned long long hv;
+  hv = id;
+  CK(cudaMemcpyAsync(&c->st->next_id, &hv, sizeof(hv), cudaMemcpyHostToDevice, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  return QED_OK;
+}
+
+extern "C" qed_status qed_get_next_id(qed_ctx* c, uint64_t* id, void* stream) {
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_get_next_id: invalid context");
+  if (!id) FAIL(QED_ERR_INVALID_ARG, "qed_get_next_id: NULL");
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, &c->st->next_id, sizeof(v), cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  *id = v;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_read_status(qed_ctx* c, uint32_t* status, int clear, void* stream) {
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_read_status: invalid context");
+  if (!status) FAIL(QED_ERR_INVALID_ARG, "qed_read_status: NULL");
+  unsigned int v = 0;
+  CK(cudaMemcpyAsync(&v, &c->st->status, sizeof(v), cudaMemcpyDeviceToHost, S(stream)));
+  if (clear) CK(cudaMemsetAsync(&c->st->status, 0, sizeof(unsigned int), S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  *status = v;
+  return QED_OK;
+}
+
+static qed_status fill_species(SpeciesArgs& a, const qed_particles* p) {
+  memset(&a, 0, sizeof(a));
+  if (!p) return QED_OK;
+  a.x = (double*)p->soa.x; a.y = (double*)p->soa.y; a.z = (double*)p->soa.z;
+  a.px = p->soa.px; a.py = p->soa.py; a.pz = p->soa.pz;
+  a.s1 = p->soa.s1; a.s2 = p->soa.s2; a.s3 = p->soa.s3;
+  a.theta = p->soa.theta; a.w = p->soa.w; a.id = p->soa.id;
+  a.cap = p->cap;
+  a.present = p->cap > 0 ? 1 : 0;
+  return QED_OK;
+}
+
+static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
+                                const qed_fields* f, double dt, uint32_t flags, qed_precision* prec) {
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_step: invalid context");
+  if (!f) FAIL(QED_ERR_INVALID_ARG, "qed_step: fields is NULL");
+  if (!(dt > 0.0) || !std::isfinite(dt)) FAIL(QED_ERR_INVALID_ARG, "qed_step: dt must be positive and finite");
+  if (flags & ~63u) FAIL(QED_ERR_INVALID_ARG, "qed_step: unknown flag bits 0x%x", flags & ~63u);
+  const qed_particles* all[3] = {e, pos, ph};
+  const qed_species want[3] = {QED_ELECTRON, QED_POSITRON, QED_PHOTON};
+  int have = -1;
+  for (int k = 0; k < 3; ++k) {
+    if (!all[k]) continue;
+    if (all[k]->ctx != c) FAIL(QED_ERR_INVALID_ARG, "qed_step: particle set from another context");
+    if (all[k]->species != want[k]) FAIL(QED_ERR_INVALID_ARG, "qed_step: argument %d has the wrong species", k);
+    if (have >= 0 && (int)all[k]->prec != have) FAIL(QED_ERR_INVALID_ARG, "qed_step: mixed precisions");
+    have = (int)all[k]->prec;
+  }
+  *prec = have < 0 ? QED_PREC_F64 : (qed_precision)have;
+  if ((flags & QED_F_NBW) && (!e || !pos)) FAIL(QED_ERR_INVALID_ARG, "qed_step: NBW needs e- and e+ sets");
+  switch (f->kind) {
+    case QED_FIELD_NONE:
+    case QED_FIELD_UNIFORM:
+      break;
+    case QED_FIELD_PLANE:
+      if (!(f->len > 0.0)) FAIL(QED_ERR_INVALID_ARG, "qed_step: envelope length must be positive");
+      break;
+    case QED_FIELD_GAUSS:
+      if (!(f->len > 0.0) || !(f->w0 > 0.0)) FAIL(QED_ERR_INVALID_ARG, "qed_step: len and w0 must be positive");
+      break;
+    case QED_FIELD_GRID2D:
+      if (!f->gEx || !f->gEy || !f->gEz || !f->gBx || !f->gBy || !f->gBz)
+        FAIL(QED_ERR_INVALID_ARG, "qed_step: grid arrays must be non-NULL");
+      if (f->nx < 1 || f->ny < 1 || !(f->dx > 0) || !(f->dy > 0))
+        FAIL(QED_ERR_INVALID_ARG, "qed_step: bad grid geometry");
+      break;
+    default:
+      FAIL(QED_ERR_INVALID_ARG, "qed_step: unknown field kind %d", f->kind);
+  }
+  const unsigned long long tp = ph ? tiles_of(ph->cap) : 0;
+  const unsigned long long tl = (e ? tiles_of(e->cap) : 0) + (pos ? tiles_of(pos->cap) : 0);
+  if (tp > c->look_cap[0] || tl > c->look_cap[1])
+    FAIL(QED_ERR_INVALID_ARG, "qed_step: particle sets larger than the context's scan space");
+  return QED_OK;
+}
+
+extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
+                               const qed_fields* f, double t, double dt, uint64_t seed, uint32_t step,
+                               uint32_t flags, qed_step_stats* dev_stats, void* stream) {
+  qed_precision prec;
+  qed_status r = validate_step(c, e, pos, ph, f, dt, flags, &prec);
+  if (r != QED_OK) return r;
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  fill_species(a.sp[0], e);
+  fill_species(a.sp[1], pos);
+  fill_species(a.sp[2], ph);
+  a.f = *f;
+  a.t = t;
+  a.dt = dt;
+  a.seed = seed;
+  a.step = step;
+  a.flags = flags;
+  a.tables = prec == QED_PREC_F64 ? (const void*)c->tab64 : (const void*)c->tab32;
+  a.st = c->st;
+  a.look[0] = c->look[0];
+  a.look[1] = c->look[1];
+  a.look_cap[0] = c->look_cap[0];
+  a.look_cap[1] = c->look_cap[1];
+  a.user_stats = dev_stats;
+  const int pi = prec == QED_PREC_F64 ? 0 : 1;
+  r = launch_step(a, prec, c->nblk[pi][0], c->nblk[pi][1], S(stream), c->timing ? c->tev : nullptr);
+  if (r != QED_OK || !c->timing) return r;
+  CK(cudaEventSynchronize(c->tev[2]));
+  float m0 = 0, m1 = 0;
+  CK(cudaEventElapsedTime(&m0, c->tev[0], c->tev[1]));
+  CK(cudaEventElapsedTime(&m1, c->tev[1], c->tev[2]));
+  c->tms[0] += m0;
+  c->tms[1] += m1;
+  c->tsteps += 1;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_set_timing(qed_ctx* c, int enable) {
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_set_timing: invalid context");
+  if (enable && !c->tev[0]) {
+    for (int k = 0; k < 3; ++k) CK(cudaEventCreate(&c->tev[k]));
+  }
+  c->timing = enable ? 1 : 0;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_get_timing(qed_ctx* c, double ms[2], uint64_t* steps) {
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_get_timing: invalid context");
+  if (!ms || !steps) FAIL(QED_ERR_INVALID_ARG, "qed_get_timing: NULL output");
+  ms[0] = c->tms[0];
+  ms[1] = c->tms[1];
+  *steps = c->tsteps;
+  c->tms[0] = c->tms[1] = 0.0;
+  c->tsteps = 0;
+  return QED_OK;
+}
+
+static size_t elem(qed_precision p) { return p == QED_PREC_F64 ? 8 : 4; }
+
+static qed_status copy_soa(const qed_soa* dst, const qed_soa* src, unsigned long long n, qed_precision prec,
+                           bool photon, cudaMemcpyKind kind, cudaStream_t s) {
+  if (n == 0) return QED_OK;
+  const size_t r = elem(prec);
+  void* const d8[3] = {dst->x, dst->y, dst->z};
+  void* const s8[3] = {src->x, src->y, src->z};
+  for (int k = 0; k < 3; ++k) CK(cudaMemcpyAsync(d8[k], s8[k], 8 * n, kind, s));
+  void* const dr[7] = {dst->px, dst->py, dst->pz, dst->s1, dst->s2, dst->s3, dst->w};
+  void* const sr[7] = {src->px, src->py, src->pz, src->s1, src->s2, src->s3, src->w};
+  for (int k = 0; k < 7; ++k) CK(cudaMemcpyAsync(dr[k], sr[k], r * n, kind, s));
+  if (photon) CK(cudaMemcpyAsync(dst->theta, src->theta, r * n, kind, s));
+  CK(cudaMemcpyAsync(dst->id, src->id, 8 * n, kind, s));
+  return QED_OK;
+}
+
+extern "C" qed_status qed_step_host(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
+                                    const qed_soa* he, const qed_soa* hp, const qed_soa* hg, uint64_t n_host[3],
+                                    const qed_fields* f, double t, double dt, uint64_t seed, uint32_t step,
+                                    uint32_t flags, void* stream) {
+  qed_precision prec;
+  qed_status r = validate_step(c, e, pos, ph, f, dt, flags, &prec);
+  if (r != QED_OK) return r;
+  if (!n_host) FAIL(QED_ERR_INVALID_ARG, "qed_step_host: n_host is NULL");
+  qed_particles* dev[3] = {e, pos, ph};
+  const qed_soa* host[3] = {he, hp, hg};
+  cudaStream_t s = S(stream);
+  for (int k = 0; k < 3; ++k) {
+    if (!dev[k]) continue;
+    if (!host[k]) FAIL(QED_ERR_INVALID_ARG, "qed_step_host: host set %d missing", k);
+    if (n_host[k] > dev[k]->cap) FAIL(QED_ERR_INVALID_ARG, "qed_step_host: n_host[%d] > capacity", k);
+  }
+  static thread_local unsigned long long counts[3];
+  for (int k = 0; k < 3; ++k) {
+    if (!dev[k]) continue;
+    r = copy_soa(&dev[k]->soa, host[k], n_host[k], prec, k == 2, cudaMemcpyHostToDevice, s);
+    if (r != QED_OK) return r;
+    counts[k] = n_host[k];
+    CK(cudaMemcpyAsync(&c->st->n_live[k], &counts[k], sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+  }
+  r = qed_step(c, e, pos, ph, f, t, dt, seed, step, flags, nullptr, stream);
+  if (r != QED_OK) return r;
+  CK(cudaMemcpyAsync(counts, c->st->n_live, sizeof(counts), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < 3; ++k) {
+    if (!dev[k]) continue;
+    r = copy_soa(host[k], &dev[k]->soa, counts[k], prec, k == 2, cudaMemcpyDeviceToHost, s);
+    if (r != QED_OK) return r;
+    n_host[k] = counts[k];
+  }
+  CK(cudaStreamSynchronize(s));
+  return QED_OK;
+}
+
+extern "C" qed_status qed_copy_table(qed_ctx* c, int which, double* host, uint64_t cap, uint64_t* len, void* stream) {
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_copy_table: invalid context");
+  if (!len) FAIL(QED_ERR_INVALID_ARG, "qed_copy_table: len is NULL");
+  size_t off, n;
+  switch (which) {
+    case 0: off = kOffKV; n = 6 * (size_t)kNK; break;
+    case 1: off = kOffRA; n = 2 * (size_t)kNR; break;
+    case 2: off = kOffCY; n = 4 * (size_t)kNCX * kNCT; break;
+    case 3: off = kOffT0; n = 2 * (size_t)kNBX; break;
+    case 4: off = kOffBY; n = 4 * (size_t)kNBX * kNBT; break;
+    case 5: off = kOffMP; n = 2 * (size_t)kNV; break;
+    default: FAIL(QED_ERR_INVALID_ARG, "qed_copy_table: which must be 0..5");
+  }
+  *len = n;
+  if (!host) return QED_OK;
+  if (cap < n) FAIL(QED_ERR_INVALID_ARG, "qed_copy_table: cap %llu < %llu", (unsigned long long)cap,
+                    (unsigned long long)n);
+  CK(cudaMemcpyAsync(host, c->tab64 + off, n * sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  return QED_OK;
+}

@@ -1,0 +1,209 @@
+// qed_common.cuh -- device-side building blocks of the GB300 SF-QED step:
+// physical constants, table geometry, Philox4x32-10, small vector algebra and the
+// table interpolation rules.  Written for sm_103a; precision-generic (R = double for
+// the FP64 path, float for the mixed path).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/qed.h"
+
+namespace qedk {
+
+// ---- constants (CODATA 2018; lambda = 1 um) -----------------------------------
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kAlpha = 7.2973525693e-3;
+constexpr double kXiL = 2.42631023867e-6;     // hbar omega0 / (m c^2)
+constexpr double kAe = 1.15965218128e-3;      // g/2 - 1
+constexpr double kChiMin = 1e-4, kChiMax = 1e3;
+constexpr double kChigMin = 1e-2, kChigMax = 1e3;
+constexpr double kVbMin = 1e-3, kVbMax = 1e3;
+
+// ---- table geometry (uniform grids in ln of the argument) -----------------------
+constexpr int kNK = 1024;     // scaled K13, K23, IntK13 on ln x in [ln 1e-3, ln 1e5]
+constexpr double kKLo = -6.907755278982137, kKHi = 11.512925464970229;
+constexpr int kNR = 512;      // NCS rates A/chi, B/chi on ln chi in [ln 1e-4, ln 1e3]
+constexpr double kRLo = -9.210340371976182, kRHi = 6.907755278982137;
+constexpr int kNCX = 256, kNCT = 512;   // NCS inverse CDF: ln chi x logit level in [-38, 38]
+constexpr double kCTLo = -38.0, kCTHi = 38.0;
+constexpr int kNBX = 256, kNBT = 256;   // NBW rates / half inverse CDF: ln chi_g x ln level
+constexpr double kBLo = -4.605170185988091, kBHi = 6.907755278982137;
+constexpr double kBTLo = -38.0, kBTHi = 0.0;
+constexpr int kNV = 1024;     // VB M_par, M_perp on ln chi_g in [ln 1e-3, ln 1e3]
+constexpr double kVLo = -6.907755278982137, kVHi = 6.907755278982137;
+
+// element offsets inside one table block (same layout in double and float copies)
+constexpr size_t kOffKV = 0;                                   // [3][kNK] values
+constexpr size_t kOffKD = kOffKV + 3 * kNK;                    // [3][kNK] d/dlnx
+constexpr size_t kOffRA = kOffKD + 3 * kNK;                    // [kNR]
+constexpr size_t kOffRB = kOffRA + kNR;
+constexpr size_t kOffT0 = kOffRB + kNR;                        // [kNBX]
+constexpr size_t kOffT3 = kOffT0 + kNBX;
+constexpr size_t kOffMP = kOffT3 + kNBX;                       // [kNV]
+constexpr size_t kOffMQ = kOffMP + kNV;
+constexpr size_t kOffCY = kOffMQ + kNV;                        // [2][kNCX][kNCT]
+constexpr size_t kOffCD = kOffCY + 2 * (size_t)kNCX * kNCT;
+constexpr size_t kOffBY = kOffCD + 2 * (size_t)kNCX * kNCT;    // [2][kNBX][kNBT]
+constexpr size_t kOffBD = kOffBY + 2 * (size_t)kNBX * kNBT;
+constexpr size_t kTableLen = kOffBD + 2 * (size_t)kNBX * kNBT;
+// the 1-D rate tables are contiguous [kOffRA, kOffCY): staged to shared memory
+constexpr size_t kSmemRateLen = kOffCY - kOffRA;
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) ------------------------------------------
+struct U4 { uint32_t a, b, c, d; };
+
+__device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                       uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// two 53-bit uniforms in [0,1): counter (id_lo, id_hi, step, ctr), key = seed
+struct Uni2 { double u0, u1; };
+__device__ __forceinline__ Uni2 uniforms(uint64_t seed, uint64_t id, uint32_t step, uint32_t ctr) {
+  U4 o = philox10((uint32_t)id, (uint32_t)(id >> 32), step, ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double s = 1.1102230246251565404e-16;  // 2^-53
+  Uni2 r;
+  r.u0 = (double)((((uint64_t)(o.a >> 5)) << 26) | (uint64_t)(o.b >> 6)) * s;
+  r.u1 = (double)((((uint64_t)(o.c >> 5)) << 26) | (uint64_t)(o.d >> 6)) * s;
+  return r;
+}
+
+// ---- vectors --------------------------------------------------------------------
+template <typename R> struct V3 { R x, y, z; };
+template <typename R> __device__ __forceinline__ V3<R> mk(R a, R b, R c) { return V3<R>{a, b, c}; }
+template <typename R> __device__ __forceinline__ R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename R> __device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b) {
+  return V3<R>{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename R> __device__ __forceinline__ V3<R> operator+(V3<R> a, V3<R> b) { return V3<R>{a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename R> __device__ __forceinline__ V3<R> operator-(V3<R> a, V3<R> b) { return V3<R>{a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename R> __device__ __forceinline__ V3<R> operator*(R s, V3<R> a) { return V3<R>{s * a.x, s * a.y, s * a.z}; }
+template <typename R> __device__ __forceinline__ R norm(V3<R> a) { return sqrt(dot(a, a)); }
+
+// ---- math wrappers that pick the precision ---------------------------------------------
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double m_atan(double x) { return atan(x); }
+__device__ __forceinline__ float m_atan(float x) { return atanf(x); }
+__device__ __forceinline__ void m_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void m_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ double m_floor(double x) { return floor(x); }
+__device__ __forceinline__ float m_floor(float x) { return floorf(x); }
+
+// ---- interpolation rules (shared specification with the test oracle) -----------------
+// 4-point Lagrange on a uniform grid, X in grid units, clamped; nodes i-1..i+2 with
+// i = clamp(floor(X), 1, n-3).
+template <typename R>
+__device__ __forceinline__ R lagrange4(const R* y, int n, R X) {
+  X = X < R(0) ? R(0) : (X > R(n - 1) ? R(n - 1) : X);
+  int i = (int)m_floor(X);
+  i = i < 1 ? 1 : (i > n - 3 ? n - 3 : i);
+  const R f = X - R(i);
+  const R fm1 = f - R(1), fm2 = f - R(2), fp1 = f + R(1);
+  const R wm = -f * fm1 * fm2 * R(1.0 / 6.0);
+  const R w0 = fp1 * fm1 * fm2 * R(0.5);
+  const R w1 = -fp1 * f * fm2 * R(0.5);
+  const R w2 = fp1 * f * fm1 * R(1.0 / 6.0);
+  return wm * y[i - 1] + w0 * y[i] + w1 * y[i + 1] + w2 * y[i + 2];
+}
+
+// cubic Hermite between nodes i, i+1 with derivatives (per unit of the grid variable)
+template <typename R>
+__device__ __forceinline__ R hermite(const R* y, const R* d, int n, R T, R h) {
+  T = T < R(0) ? R(0) : (T > R(n - 1) ? R(n - 1) : T);
+  int i = (int)m_floor(T);
+  i = i < 0 ? 0 : (i > n - 2 ? n - 2 : i);
+  const R f = T - R(i), f2 = f * f, f3 = f2 * f;
+  return (R(2) * f3 - R(3) * f2 + R(1)) * __ldg(y + i) + (f3 - R(2) * f2 + f) * h * __ldg(d + i) +
+         (R(3) * f2 - R(2) * f3) * __ldg(y + i + 1) + (f3 - f2) * h * __ldg(d + i + 1);
+}
+
+// 2-D: Lagrange across rows (ln chi), Hermite along the level variable
+template <typename R>
+__device__ __forceinline__ R table2d(const R* Y, const R* D, int nx, int nt, R X, R T, R ht) {
+  X = X < R(0) ? R(0) : (X > R(nx - 1) ? R(nx - 1) : X);
+  int i = (int)m_floor(X);
+  i = i < 1 ? 1 : (i > nx - 3 ? nx - 3 : i);
+  const R f = X - R(i);
+  const R fm1 = f - R(1), fm2 = f - R(2), fp1 = f + R(1);
+  const R w[4] = {-f * fm1 * fm2 * R(1.0 / 6.0), fp1 * fm1 * fm2 * R(0.5), -fp1 * f * fm2 * R(0.5),
+                  fp1 * f * fm1 * R(1.0 / 6.0)};
+  R acc = R(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const size_t row = (size_t)(i - 1 + k) * nt;
+    acc += w[k] * hermite(Y + row, D + row, nt, T, ht);
+  }
+  return acc;
+}
+
+// scaled K functions e^x {K13, K23, IntK13}(x): table in [1e-3, 1e5], the two-term
+// power series of I_{+-nu} below, the leading asymptote sqrt(pi/2x) above.
+template <typename R>
+__device__ __forceinline__ void kfun(const R* tab, R x, R& k13, R& k23, R& ik) {
+  if (x < R(1e-3)) {
+    const R g13 = R(2.678938534707747633), g23 = R(1.354117939426400417);
+    const R g43 = g13 / R(3), g53 = R(2) * g23 / R(3), g73 = R(4) * g43 / R(3), g83 = R(5) * g53 / R(3);
+    const R c = R(kPi / 1.7320508075688772935);  // pi / (2 sin(pi/3))
+    const R h = R(0.5) * x, h2 = h * h;
+    const R hp13 = m_pow(h, R(1.0 / 3.0)), hm13 = R(1) / hp13;
+    const R hp23 = hp13 * hp13, hm23 = hm13 * hm13;
+    const R e = m_exp(x);
+    k13 = e * c * (hm13 * (R(1) / g23 + h2 / g53) - hp13 * (R(1) / g43 + h2 / g73));
+    k23 = e * c * (hm23 * (R(1) / g13 + h2 / g43) - hp23 * (R(1) / g53 + h2 / g83));
+    // int_0^x K13 = c [3 h^{2/3}/G(2/3) + (3/4) h^{8/3}/G(5/3) - (3/2) h^{4/3}/G(4/3) - (3/5) h^{10/3}/G(7/3)]
+    const R h43 = hp23 * hp23;
+    const R in = c * (R(3) * hp23 / g23 + R(0.75) * hp23 * h2 / g53 - R(1.5) * h43 / g43 - R(0.6) * h43 * h2 / g73);
+    ik = e * (R(1.8137993642342178505) - in);   // pi/sqrt(3)
+    return;
+  }
+  if (x > R(1e5)) {
+    const R v = sqrt(R(kPi) / (R(2) * x));
+    k13 = k23 = ik = v;
+    return;
+  }
+  const R h = R((kKHi - kKLo) / (kNK - 1));
+  R X = (m_log(x) - R(kKLo)) / h;
+  int i = (int)m_floor(X);
+  i = i < 0 ? 0 : (i > kNK - 2 ? kNK - 2 : i);
+  const R f = X - R(i), f2 = f * f, f3 = f2 * f;
+  const R h00 = R(2) * f3 - R(3) * f2 + R(1), h10 = (f3 - R(2) * f2 + f) * h, h01 = R(3) * f2 - R(2) * f3,
+          h11 = (f3 - f2) * h;
+  const R* v = tab + kOffKV;
+  const R* d = tab + kOffKD;
+  k13 = h00 * __ldg(v + i) + h10 * __ldg(d + i) + h01 * __ldg(v + i + 1) + h11 * __ldg(d + i + 1);
+  k23 = h00 * __ldg(v + kNK + i) + h10 * __ldg(d + kNK + i) + h01 * __ldg(v + kNK + i + 1) + h11 * __ldg(d + kNK + i + 1);
+  ik = h00 * __ldg(v + 2 * kNK + i) + h10 * __ldg(d + 2 * kNK + i) + h01 * __ldg(v + 2 * kNK + i + 1) +
+       h11 * __ldg(d + 2 * kNK + i + 1);
+}
+
+// ---- device status -----------------------------------------------------------------
+struct DevState {
+  unsigned long long n_live[3];      // e-, e+, photon live counts (authoritative)
+  unsigned long long next_id;
+  unsigned long long n_surv;         // this step: photons surviving NBW
+  unsigned long long n_nbw;          // this step: pairs created
+  unsigned long long n_ncs_tot;      // this step: NCS photons to append
+  unsigned long long n_old[3];       // counts at the start of this step
+  unsigned long long ev[6];          // this step: ncs_e, ncs_p, nbw, range, drop, spare
+  unsigned int ticket[2];            // tile tickets: photon kernel, lepton kernel
+  unsigned int done[2];              // finished-block counters
+  unsigned int epoch;                // look-back tag, bumped every step
+  unsigned int status;               // QED_STATUS_* bits (sticky)
+};
+
+}  // namespace qedk
