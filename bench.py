@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""QED particle-steps/s of the spin/polarization-resolved SF-QED step on one GB300.
+
+Workload (config 2): 1e6 electrons, gamma ~ N(2e4, 5%), transverse and longitudinal rms
+1 um, spins uniform on the sphere, head-on with a circularly polarised paraxial Gaussian
+pulse (a0 = 100, w0 = 3 um, 10-cycle sin^2 envelope); NCS + NBW + VB + T-BMT with photon
+and pair compaction every step; dt = T0/200.  The beam starts 150 steps before its centre
+meets the pulse centre at the focus; those 150 steps run untimed (they populate photons
+and pairs), then W warm-up steps, then K timed steps.  A "step" is one qed_step over all
+live e-, e+ and photons; the metric counts every live particle of every step.
+
+Timing: CUDA events on the library's stream around each step, L2 flushed (256 MB write)
+before every timed step; per-kernel durations from the library's timing hook; clocks
+sampled with nvidia-smi during the timed loop.  The mixed path (headline) and the plain
+FP64 path run the same workload.  e2e: the host-buffer entry point (qed_step_host) with
+pinned host arrays, copies included.  cpu_baseline / --impl reference: the FP64 oracle
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QED particle-steps/s: mixed vs FP64 GPU at matched spectra; HBM % of peak"
+PRE_STEPS = 150
+T_SHIFT = 8.5 * math.pi
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def c2_workload(n, seed):
+    import workloads
+    wl = workloads.c2(n=n, seed=seed)
+    wl["e"]["z"] = wl["e"]["z"] + T_SHIFT
+    wl["t0"] = T_SHIFT
+    wl["step0"] = int(round(T_SHIFT / wl["dt"]))
+    return wl
+
+
+# algorithmic bytes per particle-step (state that must be read and written)
+BYTES = {
+    "mixed": {"lep": 104, "ph": 104, "ncs_birth": 68, "nbw_birth": 120},
+    "f64": {"lep": 152, "ph": 152, "ncs_birth": 104, "nbw_birth": 176},
+}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed loop runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.out = os.path.join("/tmp", f"qed_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.out, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.out):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 8:
+                    rows.append(f)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu_path(q, torch, wl, prec, steps, warmup, flush, flags):
+    """Pre-run, warm up, then time `steps` steps.  Returns totals and per-kernel data."""
+    n = len(wl["e"]["id"])
+    sim = q.Simulation(wl, prec=prec, cap_e=n + 4_000_000, cap_p=4_000_000, cap_ph=40 * n)
+    stream = torch.cuda.current_stream()
+    sim.run(PRE_STEPS, flags)
+    sim.run(warmup, flags)
+    torch.cuda.synchronize()
+    q.qed_set_timing(sim.ctx, True)
+    q.qed_get_timing(sim.ctx)
+    tot_particles = 0
+    tot_ms = 0.0
+    lep_units = ph_units = ncs_births = nbw_births = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats_before = sim.stats.clone()
+    kern_ms = [0.0, 0.0]
+    for _ in range(steps):
+        ne, npos, nph = sim.e.count(), sim.pos.count(), sim.ph.count()
+        tot_particles += ne + npos + nph
+        lep_units += ne + npos
+        ph_units += nph
+        flush.zero_()
+        s0 = sim.stats.clone()
+        ev0.record(stream)
+        q.qed_step(sim.ctx, sim.e.handle, sim.pos.handle, sim.ph.handle, sim.fields, sim.t, sim.dt,
+                   sim.seed, sim.step_no, flags, sim.stats.data_ptr())
+        ev1.record(stream)
+        ev1.synchronize()
+        tot_ms += ev0.elapsed_time(ev1)
+        d = (sim.stats - s0).cpu().numpy()
+        ncs_births += int(d[0] + d[1])
+        nbw_births += int(d[2])
+        sim.t += sim.dt
+        sim.step_no += 1
+    kms, ksteps = q.qed_get_timing(sim.ctx)
+    q.qed_set_timing(sim.ctx, False)
+    status = sim.status()
+    info = {"particles": tot_particles, "ms": tot_ms, "lep_units": lep_units, "ph_units": ph_units,
+            "ncs_births": ncs_births, "nbw_births": nbw_births, "kernel_ms": kms, "kernel_steps": ksteps,
+            "status": status, "final_counts": (sim.e.count(), sim.pos.count(), sim.ph.count())}
+    return sim, info
+
+
+def run_e2e(q, torch, sim, prec, steps, flags):
+    """Host-resident particles: every step copies the live state in and out (pinned)."""
+    import ctypes as C
+    rt = torch.float64 if prec == q.QED_PREC_F64 else torch.float32
+    hosts, keep = [], []
+    for sp in (sim.e, sim.pos, sim.ph):
+        soa = q.qed_soa()
+        d = {}
+        for k, v in sp.t.items():
+            h = torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+            h.copy_(v)
+            d[k] = h
+            setattr(soa, k, h.data_ptr())
+        hosts.append(soa)
+        keep.append(d)
+    counts = [sim.e.count(), sim.pos.count(), sim.ph.count()]
+    esz = 8 if prec == q.QED_PREC_F64 else 4
+    per = {0: 24 + 7 * esz + 8, 1: 24 + 7 * esz + 8, 2: 24 + 8 * esz + 8}
+    tot_p = h2d = d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        tot_p += sum(counts)
+        h2d += sum(per[k] * counts[k] for k in range(3))
+        counts = q.qed_step_host(sim.ctx, sim.e.handle, sim.pos.handle, sim.ph.handle, hosts[0], hosts[1],
+                                 hosts[2], counts, sim.fields, sim.t, sim.dt, sim.seed, sim.step_no, flags)
+        d2h += sum(per[k] * counts[k] for k in range(3))
+        sim.t += sim.dt
+        sim.step_no += 1
+    el = time.perf_counter() - t0
+    return {"value": tot_p / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // steps,
+            "d2h_bytes_per_step": d2h // steps, "steps": steps}
+
+
+def oracle_sample(n_e, steps_timed, warmup=0, seed=2):
+    """The oracle on a bounded sample of the same workload (single host thread)."""
+    import oracle
+    o = oracle.Oracle()
+    wl = c2_workload(n_e, seed)
+    s = oracle.Sim(o, wl)
+    flags = oracle.F_NCS | oracle.F_NBW | oracle.F_VB | oracle.F_SPIN
+    s.run(PRE_STEPS + warmup, flags)
+    tot = 0
+    t0 = time.perf_counter()
+    for _ in range(steps_timed):
+        tot += s.e.n + s.pos.n + s.ph.n
+        s.run(1, flags)
+    el = time.perf_counter() - t0
+    return tot / el, tot, el
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-sample", type=int, default=20_000)
+    ap.add_argument("--no-f64", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        ncores = 1
+        v, tot, el = oracle_sample(args.cpu_sample, args.steps, args.warmup)
+        line = {"metric": METRIC, "value": v, "unit": "particle-steps/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": "c2_focused_cp_a100_g2e4", "electrons": args.cpu_sample,
+                           "pre_steps": PRE_STEPS, "processes": "NCS+NBW+VB+T-BMT"},
+                "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": ncores, "kind": "oracle",
+                                 "sample": f"{args.cpu_sample} electrons of the same beam recipe, "
+                                           f"{args.steps} steps after {PRE_STEPS + args.warmup} untimed"},
+                "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    import paper_2306_11288_gb300 as q
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        q.build()
+    if dist is not None:
+        dist.barrier()
+    flags = q.QED_F_NCS | q.QED_F_NBW | q.QED_F_VB | q.QED_F_SPIN
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    wl = c2_workload(args.n, seed=2 + rank)
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        sim, info = run_gpu_path(q, torch, wl, q.QED_PREC_MIXED, args.steps, args.warmup, flush, flags)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    f64 = None
+    if not args.no_f64:
+        sim64, f64 = run_gpu_path(q, torch, c2_workload(args.n, seed=2 + rank), q.QED_PREC_F64, args.steps,
+                                  args.warmup, flush, flags)
+        sim64.close()
+    e2e = run_e2e(q, torch, sim, q.QED_PREC_MIXED, args.e2e_steps, flags)
+
+    ms, parts = info["ms"], info["particles"]
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        p = torch.tensor([parts], device="cuda", dtype=torch.float64)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        ms, parts = float(t.item()), float(p.item())
+    if rank != 0:
+        sim.close()
+        dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = _peaks()
+    b = BYTES["mixed"]
+    k_ph_ms, k_lep_ms = info["kernel_ms"]
+    lep_bytes = info["lep_units"] * b["lep"] + info["ncs_births"] * b["ncs_birth"]
+    ph_bytes = info["ph_units"] * b["ph"] + info["nbw_births"] * b["nbw_birth"]
+    dom = "k_photon" if k_ph_ms >= k_lep_ms else "k_lepton"
+    dom_bytes, dom_ms = (ph_bytes, k_ph_ms) if dom == "k_photon" else (lep_bytes, k_lep_ms)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    value = parts / (ms * 1e-3)
+    cpu_v, cpu_tot, cpu_el = oracle_sample(max(args.cpu_sample, 1), 20, 0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-islands",
+        "data": "synthetic",
+        "config": {"workload": "c2_focused_cp_a100_g2e4", "electrons_per_gpu": args.n,
+                   "processes": "NCS+NBW+VB+T-BMT, compaction every step", "pre_steps": PRE_STEPS,
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy)", "traffic": None,
+                     "bytes_per_launch": dom_bytes / max(info["kernel_steps"], 1),
+                     "avg_launch_ms": dom_ms / max(info["kernel_steps"], 1)},
+        "kernels": {"k_photon_ms": k_ph_ms, "k_lepton_ms": k_lep_ms,
+                    "k_photon_GBs": ph_bytes / (k_ph_ms * 1e-3) / 1e9 if k_ph_ms else None,
+                    "k_lepton_GBs": lep_bytes / (k_lep_ms * 1e-3) / 1e9 if k_lep_ms else None},
+        "cpu_baseline": {"value": cpu_v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.cpu_sample} electrons of the same beam recipe, 20 steps after "
+                                   f"{PRE_STEPS} untimed"},
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+        "counts_after": {"e": info["final_counts"][0], "pos": info["final_counts"][1],
+                         "ph": info["final_counts"][2]},
+        "status": info["status"],
+    }
+    if f64 is not None:
+        v64 = f64["particles"] / (f64["ms"] * 1e-3)
+        line["f64"] = {"value": v64, "ms_per_step": f64["ms"] / args.steps, "speedup_mixed": value / v64,
+                       "k_photon_ms": f64["kernel_ms"][0], "k_lepton_ms": f64["kernel_ms"][1]}
+    print(json.dumps(line))
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

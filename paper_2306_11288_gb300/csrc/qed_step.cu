@@ -31,34 +31,52 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 constexpr int kValBits = 38;
 constexpr unsigned long long kValMask = (1ull << kValBits) - 1;
 
-__device__ unsigned long long lookback(unsigned long long* words, unsigned int tile, unsigned long long agg,
-                                       unsigned int epoch, unsigned int* status) {
+// Warp-parallel look-back, run by all 32 lanes of one warp: publishes this tile's
+// aggregate, then inspects 32 predecessors per probe (lane k looks at tile - 1 - k), adds
+// the aggregates up to the nearest inclusive prefix, and publishes its own inclusive prefix.
+// A predecessor that has not published yet is polled with a bounded number of retries.
+__device__ unsigned long long lookback_warp(unsigned long long* words, unsigned int tile, unsigned long long agg,
+                                            unsigned int epoch, unsigned int* status) {
+  const unsigned int lane = threadIdx.x & 31;
   const unsigned long long ep = (unsigned long long)(epoch & 0xFFFFFFu);
   const unsigned long long tag = ep << 40;
   if (tile == 0) {
-    st_release(words, tag | (2ull << kValBits) | agg);
+    if (lane == 0) st_release(words, tag | (2ull << kValBits) | agg);
     return 0;
   }
-  st_release(words + tile, tag | (1ull << kValBits) | agg);
+  if (lane == 0) st_release(words + tile, tag | (1ull << kValBits) | agg);
   unsigned long long excl = 0;
-  long long p = (long long)tile - 1;
+  long long base = (long long)tile - 1;
   unsigned int spins = 0;
-  while (p >= 0) {
-    const unsigned long long w = ld_acquire(words + p);
-    const unsigned int flag = (unsigned int)((w >> kValBits) & 3ull);
-    if ((w >> 40) != ep || flag == 0) {
-      if (++spins > (1u << 24)) {   // ~1 s: give up, flag it, keep going (no hang)
-        atomicOr(status, QED_STATUS_TIMEOUT);
+  for (;;) {
+    const long long p = base - (long long)lane;
+    unsigned int flag = 2;
+    unsigned long long v = 0;
+    if (p >= 0) {
+      const unsigned long long w = ld_acquire(words + p);
+      flag = ((w >> 40) == ep) ? (unsigned int)((w >> kValBits) & 3ull) : 0u;
+      v = w & kValMask;
+    }
+    const unsigned int ready = __ballot_sync(0xffffffffu, flag != 0);
+    const unsigned int pmask = __ballot_sync(0xffffffffu, flag == 2);
+    const unsigned int first = pmask ? (unsigned int)(__ffs(pmask) - 1) : 31u;
+    const unsigned int need = first == 31u ? 0xffffffffu : ((2u << first) - 1u);
+    if ((ready & need) != need) {
+      if (++spins > (1u << 22)) {   // about a second: give up, flag it, never hang
+        if (lane == 0) atomicOr(status, QED_STATUS_TIMEOUT);
         break;
       }
-      __nanosleep(64);
+      __nanosleep(32);
       continue;
     }
-    excl += w & kValMask;
-    if (flag == 2) break;
-    --p;
+    unsigned long long mine = (lane <= first) ? v : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    excl += mine;
+    if (pmask) break;
+    base -= 32;
   }
-  st_release(words + tile, tag | (2ull << kValBits) | ((excl + agg) & kValMask));
+  if (lane == 0) st_release(words + tile, tag | (2ull << kValBits) | ((excl + agg) & kValMask));
   return excl;
 }
 
@@ -88,8 +106,9 @@ __device__ __forceinline__ unsigned long long block_rank(bool flag, unsigned int
     }
     const unsigned int total = __shfl_sync(0xffffffffu, c, 31);
     if (lane < nw) sh.warp_off[lane] = c - mine;
+    const unsigned long long pre = lookback_warp(words, tile, total, epoch, status);
     if (lane == 0) {
-      sh.prefix = lookback(words, tile, total, epoch, status);
+      sh.prefix = pre;
       sh.total = total;
     }
   }
@@ -240,8 +259,11 @@ __device__ __forceinline__ void count_event(unsigned long long* ctr, bool flag) 
 // ======================================================================================
 // photon kernel
 // ======================================================================================
+// resident blocks per SM requested from the register allocator
+template <typename R> struct Occ { static constexpr int v = sizeof(R) == 4 ? 3 : 2; };
+
 template <typename R>
-__global__ void __launch_bounds__(kTile) k_photon(StepArgs a) {
+__global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(StepArgs a) {
   __shared__ R s_rates[kSmemRateLen];
   __shared__ ScanShared s_scan;
   __shared__ unsigned int s_tile;
@@ -427,7 +449,7 @@ __global__ void __launch_bounds__(kTile) k_photon(StepArgs a) {
 // lepton kernel
 // ======================================================================================
 template <typename R>
-__global__ void __launch_bounds__(kTile) k_lepton(StepArgs a) {
+__global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(StepArgs a) {
   __shared__ R s_rates[kSmemRateLen];
   __shared__ ScanShared s_scan;
   __shared__ unsigned int s_tile;
