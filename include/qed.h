@@ -138,8 +138,9 @@ qed_status qed_destroy(qed_ctx *ctx);
 
 /* Wrap caller-owned device arrays as one species (paper Sec. IV: ParticleList).
  * `buffers` pointers are copied; the arrays must outlive the returned object.  All
- * particle sets stepped together must share one precision.  `n` <= `capacity`.
- * Allocates a device count word (and grows the context's scratch to the capacity).
+ * particle sets stepped together must share one precision.  `n` <= `capacity` < 2^32.
+ * The live count lives in the context (one set per species per context).  Grows the
+ * context's step scratch (event logs, per-tile counts) to the capacity.
  * Syncs `stream`.  Errors: QED_ERR_INVALID_ARG (NULL array, n > capacity, photon
  * without theta), QED_ERR_CUDA. */
 qed_status particles_create(qed_ctx *ctx, qed_species species, const qed_soa *buffers,
@@ -199,12 +200,13 @@ qed_status qed_step_host(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed
  * `stream`.  clear != 0 resets it. */
 qed_status qed_read_status(qed_ctx *ctx, uint32_t *status, int clear, void *stream);
 
-/* Diagnostics: per-kernel timing.  While enabled, qed_step records CUDA events around
- * its two kernels (photon kernel, lepton kernel) on `stream` and waits for them, adding
- * the elapsed milliseconds to two accumulators (so every step syncs its stream).
- * qed_get_timing returns and clears them with the number of steps timed.  Off by default. */
+/* Diagnostics: per-kernel timing.  While enabled, qed_step records CUDA events on `stream`
+ * around its photon streaming kernel, its lepton streaming kernel and the remaining
+ * event-processing kernels, and waits for them, adding the elapsed milliseconds to three
+ * accumulators (so every step syncs its stream).  qed_get_timing returns and clears them
+ * with the number of steps timed.  Off by default. */
 qed_status qed_set_timing(qed_ctx *ctx, int enable);
-qed_status qed_get_timing(qed_ctx *ctx, double ms[2], uint64_t *steps);
+qed_status qed_get_timing(qed_ctx *ctx, double ms[3], uint64_t *steps);
 
 /* Diagnostics: copy one FP64 lookup table of the context to host memory (syncs).
  * which: 0 scaled K13, K23, IntK13 values then their d/dln x, [2][3][1024] on ln x in

@@ -1109,7 +1109,8 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
  *  One step, in the order of Sec. IV (VB => NBW for photons, then push,    *
  *  T-BMT and NCS for leptons); newborns are appended and first processed   *
  *  at the next step.  Ids: NBW pairs first (photon order, e- then e+),     *
- *  then NCS photons (e- order, then e+ order).                             *
+ *  then NCS photons (e- order, then e+ order).  Decayed photons leave the  *
+ *  array: their slots below the new count are refilled from the tail.      *
  * ======================================================================= */
 int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, const or_fields *f, double t, double dt,
             uint64_t seed, uint32_t step, uint32_t flags, or_stats *st) {
@@ -1117,19 +1118,28 @@ int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, con
   or_lep_birth *be = (or_lep_birth *)malloc(sizeof(or_lep_birth) * (nph + 1));
   or_lep_birth *bp = (or_lep_birth *)malloc(sizeof(or_lep_birth) * (nph + 1));
   or_ph_birth *bg = (or_ph_birth *)malloc(sizeof(or_ph_birth) * (ne + np + 1));
-  uint64_t nnbw = 0, nncs = 0, keep = 0;
-  for (uint64_t i = 0; i < nph; ++i) {
-    int d = or_photon(c, ph, i, f, t, dt, seed, step, flags, &be[nnbw], &bp[nnbw], st);
-    if (d) { nnbw++; continue; }
-    if (keep != i) {
-      ph->x[keep] = ph->x[i]; ph->y[keep] = ph->y[i]; ph->z[keep] = ph->z[i];
-      ph->px[keep] = ph->px[i]; ph->py[keep] = ph->py[i]; ph->pz[keep] = ph->pz[i];
-      ph->s1[keep] = ph->s1[i]; ph->s2[keep] = ph->s2[i]; ph->s3[keep] = ph->s3[i];
-      ph->theta[keep] = ph->theta[i]; ph->w[keep] = ph->w[i]; ph->id[keep] = ph->id[i];
+  uint64_t nnbw = 0, nncs = 0;
+  uint64_t *dec = (uint64_t *)malloc(sizeof(uint64_t) * (nph + 1));
+  for (uint64_t i = 0; i < nph; ++i)
+    if (or_photon(c, ph, i, f, t, dt, seed, step, flags, &be[nnbw], &bp[nnbw], st)) dec[nnbw++] = i;
+  /* removal of decayed photons: with M = n - (decays), the k-th decayed slot below M
+     receives the k-th surviving photon at or above M (both in index order) */
+  if (ph) {
+    uint64_t M = nph - nnbw, H = 0;
+    while (H < nnbw && dec[H] < M) H++;
+    uint64_t q = H, j = M;
+    for (uint64_t k = 0; k < H; ++k) {
+      while (q < nnbw && dec[q] == j) { q++; j++; }
+      uint64_t d = dec[k];
+      ph->x[d] = ph->x[j]; ph->y[d] = ph->y[j]; ph->z[d] = ph->z[j];
+      ph->px[d] = ph->px[j]; ph->py[d] = ph->py[j]; ph->pz[d] = ph->pz[j];
+      ph->s1[d] = ph->s1[j]; ph->s2[d] = ph->s2[j]; ph->s3[d] = ph->s3[j];
+      ph->theta[d] = ph->theta[j]; ph->w[d] = ph->w[j]; ph->id[d] = ph->id[j];
+      j++;
     }
-    keep++;
+    ph->n = M;
   }
-  if (ph) ph->n = keep;
+  free(dec);
   for (uint64_t i = 0; i < ne; ++i)
     if (or_lepton(c, e, i, -1.0, f, t, dt, seed, step, flags, &bg[nncs], st, 0)) nncs++;
   for (uint64_t i = 0; i < np; ++i)

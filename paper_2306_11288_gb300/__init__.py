@@ -183,10 +183,11 @@ def qed_set_timing(ctx, enable: bool):
 
 
 def qed_get_timing(ctx):
-    ms = (C.c_double * 2)()
+    """(milliseconds of [photon pass, lepton pass, event kernels], steps timed)"""
+    ms = (C.c_double * 3)()
     n = C.c_uint64()
     _check(lib().qed_get_timing(ctx, ms, C.byref(n)), "qed_get_timing")
-    return [ms[0], ms[1]], int(n.value)
+    return [ms[0], ms[1], ms[2]], int(n.value)
 
 
 def qed_last_error() -> str:

@@ -61,8 +61,8 @@ extern "C" qed_status qed_init_tables(qed_ctx** out, void* stream) {
     FAIL(QED_ERR_CUDA, "qed_init_tables: %s", cudaGetErrorString(e));
   }
   qed_status r = build_tables(c->tab64, c->tab32, S(stream));
-  if (r == QED_OK) r = step_grid_sizes(QED_PREC_F64, &c->nblk[0][0], &c->nblk[0][1]);
-  if (r == QED_OK) r = step_grid_sizes(QED_PREC_MIXED, &c->nblk[1][0], &c->nblk[1][1]);
+  if (r == QED_OK) r = step_grid_sizes(QED_PREC_F64, c->nblk[0]);
+  if (r == QED_OK) r = step_grid_sizes(QED_PREC_MIXED, c->nblk[1]);
   if (r != QED_OK) {
     cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st); free(c);
     return r;
@@ -76,28 +76,59 @@ extern "C" qed_status qed_destroy(qed_ctx* c) {
   if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_destroy: invalid context");
   cudaDeviceSynchronize();
   cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st);
-  cudaFree(c->look[0]); cudaFree(c->look[1]);
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(c->tile_cnt[k]); cudaFree(c->tile_pre[k]); cudaFree(c->rec[k]);
+  }
+  cudaFree(c->holes);
+  for (int k = 0; k < 4; ++k)
     if (c->tev[k]) cudaEventDestroy(c->tev[k]);
   c->alive = 0;
   free(c);
   return QED_OK;
 }
 
-static qed_status grow_look(qed_ctx* c, int which, unsigned long long need, cudaStream_t s) {
-  if (need <= c->look_cap[which]) return QED_OK;
-  unsigned long long* p = nullptr;
-  CK(cudaStreamSynchronize(s));
-  CK(cudaMalloc(&p, sizeof(unsigned long long) * need));
-  CK(cudaMemsetAsync(p, 0, sizeof(unsigned long long) * need, s));
-  CK(cudaStreamSynchronize(s));
-  cudaFree(c->look[which]);
-  c->look[which] = p;
-  c->look_cap[which] = need;
+static unsigned long long tiles_of(unsigned long long n) { return (n + kTile - 1) / kTile; }
+
+// (Re)sizes the step scratch for the largest capacities seen on this context:
+// per-tile event counts and prefixes, the two event logs (worst case the FP64 record
+// size), and the ranked hole list.  Logs hold up to 1/8 of the photon capacity (decays)
+// and 1/2 of the lepton capacity (emissions) per step; beyond that a step flags
+// QED_STATUS_CAPACITY.
+static qed_status grow_scratch(qed_ctx* c, cudaStream_t s) {
+  const unsigned long long tp = tiles_of(c->cap_seen[2]) + 1;
+  const unsigned long long tl = tiles_of(c->cap_seen[0]) + tiles_of(c->cap_seen[1]) + 1;
+  const unsigned long long rn = c->cap_seen[2] / 8 + 4096;
+  const unsigned long long rl = (c->cap_seen[0] + c->cap_seen[1]) / 2 + 4096;
+  const unsigned long long want_t[2] = {tp, tl}, want_r[2] = {rn, rl};
+  const size_t rbytes[2] = {nbw_rec_bytes(QED_PREC_F64), ncs_rec_bytes(QED_PREC_F64)};
+  bool sync_done = false;
+  for (int k = 0; k < 2; ++k) {
+    if (want_t[k] > c->tile_cap[k]) {
+      if (!sync_done) { CK(cudaStreamSynchronize(s)); sync_done = true; }
+      cudaFree(c->tile_cnt[k]); cudaFree(c->tile_pre[k]);
+      c->tile_cnt[k] = nullptr; c->tile_pre[k] = nullptr; c->tile_cap[k] = 0;
+      CK(cudaMalloc(&c->tile_cnt[k], sizeof(unsigned int) * want_t[k]));
+      CK(cudaMalloc(&c->tile_pre[k], sizeof(unsigned int) * want_t[k]));
+      CK(cudaMemsetAsync(c->tile_cnt[k], 0, sizeof(unsigned int) * want_t[k], s));
+      c->tile_cap[k] = want_t[k];
+    }
+    if (want_r[k] > c->rec_cap[k]) {
+      if (!sync_done) { CK(cudaStreamSynchronize(s)); sync_done = true; }
+      cudaFree(c->rec[k]);
+      c->rec[k] = nullptr; c->rec_cap[k] = 0;
+      CK(cudaMalloc(&c->rec[k], rbytes[k] * want_r[k]));
+      CK(cudaMemsetAsync(c->rec[k], 0, rbytes[k] * want_r[k], s));
+      if (k == 0) {
+        cudaFree(c->holes);
+        c->holes = nullptr;
+        CK(cudaMalloc(&c->holes, sizeof(unsigned int) * want_r[0]));
+      }
+      c->rec_cap[k] = want_r[k];
+    }
+  }
+  if (sync_done) CK(cudaStreamSynchronize(s));
   return QED_OK;
 }
-
-static unsigned long long tiles_of(unsigned long long n) { return (n + kTile - 1) / kTile; }
 
 extern "C" qed_status particles_create(qed_ctx* c, qed_species sp, const qed_soa* b, uint64_t n, uint64_t cap,
                                        qed_precision prec, void* stream, qed_particles** out) {
@@ -109,7 +140,7 @@ extern "C" qed_status particles_create(qed_ctx* c, qed_species sp, const qed_soa
   if (prec != QED_PREC_F64 && prec != QED_PREC_MIXED) FAIL(QED_ERR_INVALID_ARG, "particles_create: bad precision");
   if (n > cap) FAIL(QED_ERR_INVALID_ARG, "particles_create: n (%llu) > capacity (%llu)",
                     (unsigned long long)n, (unsigned long long)cap);
-  if (cap > (1ull << 37)) FAIL(QED_ERR_INVALID_ARG, "particles_create: capacity above 2^37");
+  if (cap >= (1ull << 32)) FAIL(QED_ERR_INVALID_ARG, "particles_create: capacity must be below 2^32");
   if (cap > 0) {
     const void* req[] = {b->x, b->y, b->z, b->px, b->py, b->pz, b->s1, b->s2, b->s3, b->w, b->id};
     for (const void* p : req)
@@ -117,8 +148,8 @@ extern "C" qed_status particles_create(qed_ctx* c, qed_species sp, const qed_soa
     if (sp == QED_PHOTON && !b->theta) FAIL(QED_ERR_INVALID_ARG, "particles_create: photons need theta");
   }
   cudaStream_t s = S(stream);
-  // look-back words: photons alone; e- and e+ share the lepton tile space
-  qed_status r = grow_look(c, sp == QED_PHOTON ? 0 : 1, 2 * tiles_of(cap) + 2, s);
+  if (cap > c->cap_seen[sp]) c->cap_seen[sp] = cap;
+  qed_status r = grow_scratch(c, s);
   if (r != QED_OK) return r;
   qed_particles* p = (qed_particles*)calloc(1, sizeof(qed_particles));
   p->ctx = c;
@@ -240,8 +271,8 @@ static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos
   }
   const unsigned long long tp = ph ? tiles_of(ph->cap) : 0;
   const unsigned long long tl = (e ? tiles_of(e->cap) : 0) + (pos ? tiles_of(pos->cap) : 0);
-  if (tp > c->look_cap[0] || tl > c->look_cap[1])
-    FAIL(QED_ERR_INVALID_ARG, "qed_step: particle sets larger than the context's scan space");
+  if (tp > c->tile_cap[0] || tl > c->tile_cap[1] || !c->rec[0] || !c->rec[1])
+    FAIL(QED_ERR_INVALID_ARG, "qed_step: particle sets larger than the context's scratch");
   return QED_OK;
 }
 
@@ -264,20 +295,32 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
   a.flags = flags;
   a.tables = prec == QED_PREC_F64 ? (const void*)c->tab64 : (const void*)c->tab32;
   a.st = c->st;
-  a.look[0] = c->look[0];
-  a.look[1] = c->look[1];
-  a.look_cap[0] = c->look_cap[0];
-  a.look_cap[1] = c->look_cap[1];
+  const double len = f->len > 0.0 ? f->len : 1.0;
+  a.inv_len = 1.0 / len;
+  const double two_pi = 6.283185307179586477;
+  a.ff.dt = (float)dt;
+  a.ff.inv_len = (float)a.inv_len;
+  a.ff.t_rel = (float)(t - f->phi0);
+  a.ff.t_mod = (float)(t - two_pi * std::floor(t / two_pi));
+  a.ff.a0 = (float)f->a0;
+  a.ff.w0 = (float)f->w0;
+  a.ff.zf = (float)f->zf;
+  a.ff.zr = (float)(0.5 * f->w0 * f->w0);
+  for (int k = 0; k < 2; ++k) {
+    a.tile_cnt[k] = c->tile_cnt[k];
+    a.tile_pre[k] = c->tile_pre[k];
+    a.rec[k] = c->rec[k];
+    a.rec_cap[k] = c->rec_cap[k];
+  }
+  a.holes = c->holes;
   a.user_stats = dev_stats;
   const int pi = prec == QED_PREC_F64 ? 0 : 1;
-  r = launch_step(a, prec, c->nblk[pi][0], c->nblk[pi][1], S(stream), c->timing ? c->tev : nullptr);
+  r = launch_step(a, prec, c->nblk[pi], S(stream), c->timing ? c->tev : nullptr);
   if (r != QED_OK || !c->timing) return r;
-  CK(cudaEventSynchronize(c->tev[2]));
-  float m0 = 0, m1 = 0;
-  CK(cudaEventElapsedTime(&m0, c->tev[0], c->tev[1]));
-  CK(cudaEventElapsedTime(&m1, c->tev[1], c->tev[2]));
-  c->tms[0] += m0;
-  c->tms[1] += m1;
+  CK(cudaEventSynchronize(c->tev[3]));
+  float m[3] = {0, 0, 0};
+  for (int k = 0; k < 3; ++k) CK(cudaEventElapsedTime(&m[k], c->tev[k], c->tev[k + 1]));
+  for (int k = 0; k < 3; ++k) c->tms[k] += m[k];
   c->tsteps += 1;
   return QED_OK;
 }
@@ -285,19 +328,18 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
 extern "C" qed_status qed_set_timing(qed_ctx* c, int enable) {
   if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_set_timing: invalid context");
   if (enable && !c->tev[0]) {
-    for (int k = 0; k < 3; ++k) CK(cudaEventCreate(&c->tev[k]));
+    for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&c->tev[k]));
   }
   c->timing = enable ? 1 : 0;
   return QED_OK;
 }
 
-extern "C" qed_status qed_get_timing(qed_ctx* c, double ms[2], uint64_t* steps) {
+extern "C" qed_status qed_get_timing(qed_ctx* c, double ms[3], uint64_t* steps) {
   if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_get_timing: invalid context");
   if (!ms || !steps) FAIL(QED_ERR_INVALID_ARG, "qed_get_timing: NULL output");
-  ms[0] = c->tms[0];
-  ms[1] = c->tms[1];
+  for (int k = 0; k < 3; ++k) ms[k] = c->tms[k];
   *steps = c->tsteps;
-  c->tms[0] = c->tms[1] = 0.0;
+  c->tms[0] = c->tms[1] = c->tms[2] = 0.0;
   c->tsteps = 0;
   return QED_OK;
 }

@@ -196,13 +196,12 @@ struct DevState {
   unsigned long long n_live[3];      // e-, e+, photon live counts (authoritative)
   unsigned long long next_id;
   unsigned long long n_surv;         // this step: photons surviving NBW
-  unsigned long long n_nbw;          // this step: pairs created
-  unsigned long long n_ncs_tot;      // this step: NCS photons to append
-  unsigned long long n_old[3];       // counts at the start of this step
-  unsigned long long ev[6];          // this step: ncs_e, ncs_p, nbw, range, drop, spare
-  unsigned int ticket[2];            // tile tickets: photon kernel, lepton kernel
-  unsigned int done[2];              // finished-block counters
-  unsigned int epoch;                // look-back tag, bumped every step
+  unsigned long long n_nbw;          // this step: pairs created (ranked decays)
+  unsigned long long n_ncs_tot;      // this step: ranked emissions
+  unsigned long long cursor[2];      // this step: entries written to the NBW / NCS logs
+  unsigned long long ev[6];          // this step: ncs_e, ncs_p, spare, range, drop, spare
+  unsigned int done;                 // finished-block counter of the last kernel
+  unsigned int epoch;                // stamp of this step's log entries
   unsigned int status;               // QED_STATUS_* bits (sticky)
 };
 

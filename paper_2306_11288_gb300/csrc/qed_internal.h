@@ -25,25 +25,37 @@ struct SpeciesArgs {
   int present;
 };
 
+// float copies of per-step constants for the mixed path (no FP64 arithmetic in kernels)
+struct FloatConsts {
+  float dt, inv_len, t_rel, t_mod, a0, w0, zf, zr;
+};
+
 struct StepArgs {
   SpeciesArgs sp[3];                 // e-, e+, photon
   qed_fields f;
   double t, dt;
+  double inv_len;                    // 1 / envelope length
+  FloatConsts ff;
   unsigned long long seed;
   unsigned int step, flags;
   const void* tables;                // double* or float* depending on precision
   DevState* st;
-  unsigned long long* look[2];       // decoupled look-back words: photon, lepton tiles
-  unsigned long long look_cap[2];    // words available
+  unsigned int* tile_cnt[2];         // events per tile: photon tiles, lepton tiles
+  unsigned int* tile_pre[2];         // their exclusive prefixes
+  void* rec[2];                      // event logs: NBW decays, NCS emissions
+  unsigned long long rec_cap[2];
+  unsigned int* holes;               // ranked slots of decayed photons
   qed_step_stats* user_stats;
 };
 
-// launches one step (photon kernel, lepton kernel); prec selects the instantiation.
-// ev (optional): three events recorded before, between and after the kernels.
-qed_status launch_step(const StepArgs& a, qed_precision prec, int nblk_ph, int nblk_lep, cudaStream_t s,
-                       cudaEvent_t* ev);
+// launches one step; prec selects the instantiation; nblk = grid sizes (photon, lepton,
+// events).  ev (optional): four events recorded before the photon pass, between the
+// passes, after the lepton pass and at the end.
+qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, cudaEvent_t* ev);
 // occupancy-derived persistent grid sizes
-qed_status step_grid_sizes(qed_precision prec, int* nblk_ph, int* nblk_lep);
+qed_status step_grid_sizes(qed_precision prec, int* nblk);
+size_t nbw_rec_bytes(qed_precision p);
+size_t ncs_rec_bytes(qed_precision p);
 
 constexpr int kTile = 256;   // particles per tile (= threads per block, one particle each)
 
@@ -54,13 +66,19 @@ struct qed_ctx {
   double* tab64;
   float* tab32;
   qedk::DevState* st;
-  unsigned long long* look[2];
-  unsigned long long look_cap[2];
-  int nblk[2][2];   // [precision][photon, lepton]
+  // step scratch, sized for the largest particle sets created on this context
+  unsigned long long cap_seen[3];     // e-, e+, photon capacities
+  unsigned int* tile_cnt[2];
+  unsigned int* tile_pre[2];
+  unsigned long long tile_cap[2];
+  void* rec[2];
+  unsigned long long rec_cap[2];
+  unsigned int* holes;
+  int nblk[2][3];   // [precision][photon, lepton, events]
   int alive;
   int timing;
-  cudaEvent_t tev[3];
-  double tms[2];
+  cudaEvent_t tev[4];
+  double tms[3];
   unsigned long long tsteps;
 };
 
