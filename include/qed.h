@@ -196,6 +196,26 @@ qed_status qed_step_host(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed
                          uint64_t n_host[3], const qed_fields *f, double t, double dt,
                          uint64_t seed, uint32_t step, uint32_t flags, void *stream);
 
+/* qed_step for callers that cannot allocate device memory when they step -- code that
+ * runs while its stream is captured into a CUDA graph, or an application whose device
+ * memory is all owned by its own allocator.  The paper has no counterpart of this call.
+ * It runs exactly the kernels of qed_step, but keeps their per-step scratch (per-tile event
+ * counts and prefixes, the event logs, the list of decayed photon slots) in one
+ * file-scope device array of the library (about 5.7 MiB, held by every process that
+ * loads the library on every device it uses) instead of the context's buffers, and
+ * calls no cudaMalloc or cudaFree.  Limit: every given particle set must have capacity
+ * <= 65536; larger sets are rejected with QED_ERR_INVALID_ARG (use qed_step).
+ * The first call on a device looks the array's address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture on the device.
+ * Every call shares the array and leaves its contents behind; each call clears the
+ * event logs it needs first.  Calls whose work overlaps on the GPU (other streams,
+ * other threads, other contexts) race on the array: order them on one stream.
+ * The context, its tables and the particle sets are created as for qed_step.
+ * Arguments, order of processes, ids and errors are those of qed_step.  Async. */
+qed_status qed_step_static(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed_particles *ph,
+                           const qed_fields *f, double t, double dt, uint64_t seed, uint32_t step,
+                           uint32_t flags, qed_step_stats *dev_stats, void *stream);
+
 /* Device status word (QED_STATUS_* bits) accumulated since the last clear; syncs
  * `stream`.  clear != 0 resets it. */
 qed_status qed_read_status(qed_ctx *ctx, uint32_t *status, int clear, void *stream);

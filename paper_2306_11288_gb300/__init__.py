@@ -26,8 +26,8 @@ FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
 
 ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particles_count",
                  "particles_set_count", "particles_destroy", "qed_set_next_id", "qed_get_next_id",
-                 "qed_step", "qed_step_host", "qed_read_status", "qed_copy_table", "qed_set_timing", "qed_get_timing",
-                 "qed_last_error")
+                 "qed_step", "qed_step_host", "qed_step_static", "qed_read_status", "qed_copy_table",
+                 "qed_set_timing", "qed_get_timing", "qed_last_error")
 
 
 class qed_soa(C.Structure):
@@ -76,6 +76,7 @@ def lib():
         L.qed_step_host.argtypes = [vp, vp, vp, vp, C.POINTER(qed_soa), C.POINTER(qed_soa),
                                     C.POINTER(qed_soa), C.POINTER(u64), C.POINTER(qed_fields), d, d, u64,
                                     u32, u32, vp]
+        L.qed_step_static.argtypes = [vp, vp, vp, vp, C.POINTER(qed_fields), d, d, u64, u32, u32, vp, vp]
         L.qed_read_status.argtypes = [vp, C.POINTER(u32), C.c_int, vp]
         L.qed_copy_table.argtypes = [vp, C.c_int, C.POINTER(C.c_double), u64, C.POINTER(u64), vp]
         L.qed_set_timing.argtypes = [vp, C.c_int]
@@ -151,6 +152,13 @@ def qed_get_next_id(ctx, stream=None) -> int:
 def qed_step(ctx, e, pos, ph, fields: qed_fields, t, dt, seed, step, flags, dev_stats=None, stream=None):
     _check(lib().qed_step(ctx, e, pos, ph, C.byref(fields), float(t), float(dt), int(seed), int(step),
                           int(flags), dev_stats, _stream(stream)), "qed_step")
+
+
+def qed_step_static(ctx, e, pos, ph, fields: qed_fields, t, dt, seed, step, flags, dev_stats=None, stream=None):
+    """qed_step with its scratch in the library's static device array (no allocation);
+    particle sets of capacity <= 65536 per species."""
+    _check(lib().qed_step_static(ctx, e, pos, ph, C.byref(fields), float(t), float(dt), int(seed), int(step),
+                                 int(flags), dev_stats, _stream(stream)), "qed_step_static")
 
 
 def qed_step_host(ctx, e, pos, ph, host_e, host_pos, host_ph, n_host, fields, t, dt, seed, step, flags,

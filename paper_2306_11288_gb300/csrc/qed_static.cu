@@ -1,0 +1,188 @@
+// qed_static.cu -- qed_step_static: one step for callers that cannot allocate device
+// memory when they step (for example code that runs while a stream is being captured into
+// a CUDA graph, or a host application whose device memory is all owned by its own pool).
+// qed_step keeps its per-step scratch (per-tile event counts and prefixes, the two event
+// logs, the ranked list of decayed photon slots) in buffers that particles_create sizes
+// with cudaMalloc; this entry point keeps that scratch in one file-scope __device__ array
+// instead and allocates nothing.  The price is a fixed limit: at most kStaticMaxCap
+// particles of capacity per species.  The paper has no counterpart of this entry point.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "qed_common.cuh"
+#include "qed_internal.h"
+
+namespace qedk {
+
+constexpr unsigned long long kStaticMaxCap = 65536;   // capacity limit per species
+constexpr unsigned long long kStTilesPh = (kStaticMaxCap + kTile - 1) / kTile + 1;
+constexpr unsigned long long kStTilesLep = 2 * ((kStaticMaxCap + kTile - 1) / kTile) + 1;
+constexpr unsigned long long kStRecNbw = kStaticMaxCap / 8 + 4096;
+constexpr unsigned long long kStRecNcs = (2 * kStaticMaxCap) / 2 + 4096;
+constexpr size_t kAlign = 256;
+constexpr size_t rnd(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+// layout of the array (byte offsets); logs are sized for the FP64 record layout
+constexpr size_t kSoCntPh = 0;
+constexpr size_t kSoPrePh = kSoCntPh + rnd(4 * kStTilesPh);
+constexpr size_t kSoCntLep = kSoPrePh + rnd(4 * kStTilesPh);
+constexpr size_t kSoPreLep = kSoCntLep + rnd(4 * kStTilesLep);
+constexpr size_t kSoHoles = kSoPreLep + rnd(4 * kStTilesLep);
+constexpr size_t kSoLogNbw = kSoHoles + rnd(4 * kStRecNbw);
+constexpr size_t kNbwRecMax = 96, kNcsRecMax = 64;   // bytes per record, bounds checked at run time
+constexpr size_t kSoLogNcs = kSoLogNbw + rnd(kNbwRecMax * kStRecNbw);
+constexpr size_t kStaticBytes = kSoLogNcs + rnd(kNcsRecMax * kStRecNcs);   // about 5.7 MiB
+
+// One array per process and device, shared by every call and every context.
+static __device__ __align__(256) unsigned char g_step_scratch[kStaticBytes];
+
+// Host code cannot use g_step_scratch's name as a device address: the address is looked
+// up once per device (with that device current) and cached.
+static std::mutex g_addr_mu;
+static void* g_addr[256];
+
+static qed_status scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error("qed_step_static: cudaGetDevice: %s", cudaGetErrorString(e));
+    return QED_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= 256) {
+    set_error("qed_step_static: device ordinal %d out of range", dev);
+    return QED_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_addr_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_step_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("qed_step_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      return QED_ERR_CUDA;
+    }
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return QED_OK;
+}
+
+static void species_args(SpeciesArgs& a, const qed_particles* p) {
+  memset(&a, 0, sizeof(a));
+  if (!p) return;
+  a.x = (double*)p->soa.x; a.y = (double*)p->soa.y; a.z = (double*)p->soa.z;
+  a.px = p->soa.px; a.py = p->soa.py; a.pz = p->soa.pz;
+  a.s1 = p->soa.s1; a.s2 = p->soa.s2; a.s3 = p->soa.s3;
+  a.theta = p->soa.theta; a.w = p->soa.w; a.id = p->soa.id;
+  a.cap = p->cap;
+  a.present = p->cap > 0 ? 1 : 0;
+}
+
+}  // namespace qedk
+
+using namespace qedk;
+
+extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
+                                      const qed_fields* f, double t, double dt, uint64_t seed, uint32_t step,
+                                      uint32_t flags, qed_step_stats* dev_stats, void* stream) {
+  if (!c || !c->alive) {
+    set_error("qed_step_static: invalid context");
+    return QED_ERR_NOT_INITIALIZED;
+  }
+  if (!f) {
+    set_error("qed_step_static: fields is NULL");
+    return QED_ERR_INVALID_ARG;
+  }
+  if (!(dt > 0.0) || !std::isfinite(dt)) {
+    set_error("qed_step_static: dt must be positive and finite");
+    return QED_ERR_INVALID_ARG;
+  }
+  if (flags & ~63u) {
+    set_error("qed_step_static: unknown flag bits 0x%x", flags & ~63u);
+    return QED_ERR_INVALID_ARG;
+  }
+  const qed_particles* all[3] = {e, pos, ph};
+  const qed_species want[3] = {QED_ELECTRON, QED_POSITRON, QED_PHOTON};
+  int prec = -1;
+  for (int k = 0; k < 3; ++k) {
+    if (!all[k]) continue;
+    if (all[k]->ctx != c || all[k]->species != want[k]) {
+      set_error("qed_step_static: particle set %d does not belong here", k);
+      return QED_ERR_INVALID_ARG;
+    }
+    if (prec >= 0 && (int)all[k]->prec != prec) {
+      set_error("qed_step_static: mixed precisions");
+      return QED_ERR_INVALID_ARG;
+    }
+    prec = (int)all[k]->prec;
+    if (all[k]->cap > kStaticMaxCap) {
+      set_error("qed_step_static: capacity %llu of particle set %d exceeds the limit of %llu per species "
+                "(use qed_step for larger sets)", (unsigned long long)all[k]->cap, k, kStaticMaxCap);
+      return QED_ERR_INVALID_ARG;
+    }
+  }
+  if ((flags & QED_F_NBW) && (!e || !pos)) {
+    set_error("qed_step_static: NBW needs e- and e+ sets");
+    return QED_ERR_INVALID_ARG;
+  }
+  if (f->kind < QED_FIELD_NONE || f->kind > QED_FIELD_GRID2D ||
+      ((f->kind == QED_FIELD_PLANE || f->kind == QED_FIELD_GAUSS) && !(f->len > 0.0)) ||
+      (f->kind == QED_FIELD_GAUSS && !(f->w0 > 0.0)) ||
+      (f->kind == QED_FIELD_GRID2D && (!f->gEx || !f->gEy || !f->gEz || !f->gBx || !f->gBy || !f->gBz ||
+                                       f->nx < 1 || f->ny < 1 || !(f->dx > 0) || !(f->dy > 0)))) {
+    set_error("qed_step_static: invalid field descriptor");
+    return QED_ERR_INVALID_ARG;
+  }
+  const qed_precision pr = prec < 0 ? QED_PREC_F64 : (qed_precision)prec;
+  if (nbw_rec_bytes(pr) > kNbwRecMax || ncs_rec_bytes(pr) > kNcsRecMax) {
+    set_error("qed_step_static: event record larger than the static layout assumes");
+    return QED_ERR_INVALID_ARG;
+  }
+  void* base = nullptr;
+  qed_status r = scratch_address(&base);
+  if (r != QED_OK) return r;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the logs keep the previous call's entries: clear them so that none can be mistaken
+  // for an entry of this step (the step reads only entries it wrote, this is a safeguard)
+  cudaError_t ce = cudaMemsetAsync(b + kSoLogNbw, 0, kStaticBytes - kSoLogNbw, s);
+  if (ce != cudaSuccess) {
+    set_error("qed_step_static: cudaMemsetAsync: %s", cudaGetErrorString(ce));
+    return QED_ERR_CUDA;
+  }
+  StepArgs a;
+  memset(&a, 0, sizeof(a));
+  species_args(a.sp[0], e);
+  species_args(a.sp[1], pos);
+  species_args(a.sp[2], ph);
+  a.f = *f;
+  a.t = t;
+  a.dt = dt;
+  a.seed = seed;
+  a.step = step;
+  a.flags = flags;
+  a.tables = pr == QED_PREC_F64 ? (const void*)c->tab64 : (const void*)c->tab32;
+  a.st = c->st;
+  const double len = f->len > 0.0 ? f->len : 1.0;
+  a.inv_len = 1.0 / len;
+  const double two_pi = 6.283185307179586477;
+  a.ff.dt = (float)dt;
+  a.ff.inv_len = (float)a.inv_len;
+  a.ff.t_rel = (float)(t - f->phi0);
+  a.ff.t_mod = (float)(t - two_pi * std::floor(t / two_pi));
+  a.ff.a0 = (float)f->a0;
+  a.ff.w0 = (float)f->w0;
+  a.ff.zf = (float)f->zf;
+  a.ff.zr = (float)(0.5 * f->w0 * f->w0);
+  a.tile_cnt[0] = reinterpret_cast<unsigned int*>(b + kSoCntPh);
+  a.tile_pre[0] = reinterpret_cast<unsigned int*>(b + kSoPrePh);
+  a.tile_cnt[1] = reinterpret_cast<unsigned int*>(b + kSoCntLep);
+  a.tile_pre[1] = reinterpret_cast<unsigned int*>(b + kSoPreLep);
+  a.holes = reinterpret_cast<unsigned int*>(b + kSoHoles);
+  a.rec[0] = b + kSoLogNbw;
+  a.rec[1] = b + kSoLogNcs;
+  a.rec_cap[0] = kStRecNbw;
+  a.rec_cap[1] = kStRecNcs;
+  a.user_stats = dev_stats;
+  const int pi = pr == QED_PREC_F64 ? 0 : 1;
+  return launch_step(a, pr, c->nblk[pi], s, nullptr);
+}
