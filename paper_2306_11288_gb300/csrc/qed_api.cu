@@ -306,6 +306,8 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
   a.ff.w0 = (float)f->w0;
   a.ff.zf = (float)f->zf;
   a.ff.zr = (float)(0.5 * f->w0 * f->w0);
+  a.ff.inv_zr = f->w0 > 0.0 ? (float)(2.0 / (f->w0 * f->w0)) : 0.0f;
+  a.ff.inv_w02 = f->w0 > 0.0 ? (float)(1.0 / (f->w0 * f->w0)) : 0.0f;
   for (int k = 0; k < 2; ++k) {
     a.tile_cnt[k] = c->tile_cnt[k];
     a.tile_pre[k] = c->tile_pre[k];

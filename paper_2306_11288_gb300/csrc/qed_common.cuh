@@ -104,6 +104,56 @@ __device__ __forceinline__ void m_sincos(float x, float* s, float* c) { sincosf(
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 
+// ---- fast forms for the FP32 path ------------------------------------------------------
+// The mixed path's tolerance (2e-5 per particle) allows the hardware approximations:
+// reciprocal and reciprocal square root, exp2/log2-based exp and log, sin/cos after an
+// explicit reduction to [-pi, pi], and a polynomial arctangent.  For R = double every
+// helper is the ordinary accurate function, so the FP64 path is unchanged.
+__device__ __forceinline__ float f_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double f_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float f_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double f_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float f_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double f_exp(double x) { return exp(x); }
+__device__ __forceinline__ float f_log(float x) { return __logf(x); }
+__device__ __forceinline__ double f_log(double x) { return log(x); }
+__device__ __forceinline__ void f_sincos(float x, float* s, float* c) {
+  // x - 2 pi k in two parts (6.28125 is exact in float), then the hardware sin/cos
+  const float k = rintf(x * 0.15915494309189535f);
+  const float r = fmaf(-k, 1.9353071795864769e-3f, fmaf(-k, 6.28125f, x));
+  __sincosf(r, s, c);
+}
+__device__ __forceinline__ void f_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+// arctangent on [0,1]: odd polynomial of degree 15 fitted to atan (max error 4e-8)
+__device__ __forceinline__ float atan01(float t) {
+  const float t2 = t * t;
+  float p = -0.004071014306f;
+  p = fmaf(p, t2, 0.02193351733f);
+  p = fmaf(p, t2, -0.05603502029f);
+  p = fmaf(p, t2, 0.09653253829f);
+  p = fmaf(p, t2, -0.1391409575f);
+  p = fmaf(p, t2, 0.1994800309f);
+  p = fmaf(p, t2, -0.3333003743f);
+  p = fmaf(p, t2, 0.9999994061f);
+  return p * t;
+}
+__device__ __forceinline__ float f_atan(float x) {
+  const float a = fabsf(x);
+  const float r = a <= 1.0f ? atan01(a) : 1.5707963267948966f - atan01(__fdividef(1.0f, a));
+  return copysignf(r, x);
+}
+__device__ __forceinline__ double f_atan(double x) { return atan(x); }
+__device__ __forceinline__ float f_atan2(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  if (mx == 0.0f) return 0.0f;
+  float r = atan01(__fdividef(mn, mx));
+  if (ay > ax) r = 1.5707963267948966f - r;
+  if (x < 0.0f) r = 3.141592653589793f - r;
+  return copysignf(r, y);
+}
+__device__ __forceinline__ double f_atan2(double y, double x) { return atan2(y, x); }
+
 // ---- interpolation rules (shared specification with the test oracle) -----------------
 // 4-point Lagrange on a uniform grid, X in grid units, clamped; nodes i-1..i+2 with
 // i = clamp(floor(X), 1, n-3).

@@ -27,7 +27,7 @@ struct SpeciesArgs {
 
 // float copies of per-step constants for the mixed path (no FP64 arithmetic in kernels)
 struct FloatConsts {
-  float dt, inv_len, t_rel, t_mod, a0, w0, zf, zr;
+  float dt, inv_len, t_rel, t_mod, a0, w0, zf, zr, inv_zr, inv_w02;
 };
 
 struct StepArgs {

@@ -173,6 +173,8 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
   a.ff.w0 = (float)f->w0;
   a.ff.zf = (float)f->zf;
   a.ff.zr = (float)(0.5 * f->w0 * f->w0);
+  a.ff.inv_zr = f->w0 > 0.0 ? (float)(2.0 / (f->w0 * f->w0)) : 0.0f;
+  a.ff.inv_w02 = f->w0 > 0.0 ? (float)(1.0 / (f->w0 * f->w0)) : 0.0f;
   a.tile_cnt[0] = reinterpret_cast<unsigned int*>(b + kSoCntPh);
   a.tile_pre[0] = reinterpret_cast<unsigned int*>(b + kSoPrePh);
   a.tile_cnt[1] = reinterpret_cast<unsigned int*>(b + kSoCntLep);

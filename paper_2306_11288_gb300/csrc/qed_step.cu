@@ -100,28 +100,31 @@ __device__ __forceinline__ EB<R> gather(const StepArgs& a, double x, double y, d
     }
     if (s < R(0) || s > R(1)) return r;
     R sn, cs;
-    m_sincos(R(kPi) * s, &sn, &cs);
+    f_sincos(R(kPi) * s, &sn, &cs);
     R g = (sizeof(R) == 8 ? (R)f.a0 : (R)a.ff.a0) * sn * sn;
     if (f.kind == QED_FIELD_GAUSS) {
-      R r2, zr_, w0;
       if (sizeof(R) == 8) {
-        r2 = (R)(x * x + y * y);
-        zr_ = (R)(0.5 * f.w0 * f.w0);
-        w0 = (R)f.w0;
+        const R r2 = (R)(x * x + y * y);
+        const R zr_ = (R)(0.5 * f.w0 * f.w0);
+        const R w0 = (R)f.w0;
+        const R q = zl / zr_;
+        const R w2 = w0 * w0 * (R(1) + q * q);
+        g = g * (w0 / sqrt(w2)) * m_exp(-r2 / w2);
+        ph = ph - R(0.5) * r2 * zl / (zl * zl + zr_ * zr_) + m_atan(q);
       } else {
+        // division-free form: with q = zeta/zR, w0/w = (1+q^2)^{-1/2}
         xr = d2f_bits(x);
         yr = d2f_bits(y);
-        r2 = xr * xr + yr * yr;
-        zr_ = a.ff.zr;
-        w0 = a.ff.w0;
+        const R r2 = xr * xr + yr * yr;
+        const R q = zl * (R)a.ff.inv_zr;
+        const R rs = f_rsqrt(R(1) + q * q);
+        const R inv = rs * rs;
+        g = g * rs * f_exp(-r2 * (R)a.ff.inv_w02 * inv);
+        ph = ph - R(0.5) * r2 * q * (R)a.ff.inv_zr * inv + f_atan(q);
       }
-      const R q = zl / zr_;
-      const R w2 = w0 * w0 * (R(1) + q * q);
-      g = g * (w0 / sqrt(w2)) * m_exp(-r2 / w2);
-      ph = ph - R(0.5) * r2 * zl / (zl * zl + zr_ * zr_) + m_atan(q);
     }
     R sp, cp;
-    m_sincos(ph, &sp, &cp);
+    f_sincos(ph, &sp, &cp);
     r.E.x = g * cp;
     r.E.y = f.circular ? g * sp : R(0);
     r.B.x = r.E.y;
@@ -148,7 +151,7 @@ __device__ __forceinline__ void frame(V3<R> n, V3<R>& e1, V3<R>& e2) {
   R a = n.z, b = R(0), c = -n.x;
   R m2 = a * a + c * c;
   if (m2 < R(1e-20)) { a = R(0); b = n.z; c = -n.y; m2 = b * b + c * c; }
-  const R inv = R(1) / sqrt(m2);
+  const R inv = f_rsqrt(m2);
   e1 = mk<R>(a * inv, b * inv, c * inv);
   e2 = cross(n, e1);
 }
@@ -180,7 +183,7 @@ struct Tabs {
   const R* g;     // full table block in global memory
   const R* s;     // copy of the 1-D rate tables (shared memory in the streaming kernels)
   __device__ __forceinline__ void ncs_rates(R chi, R& A, R& B) const {
-    const R X = (m_log(chi) - R(kRLo)) * R((kNR - 1) / (kRHi - kRLo));
+    const R X = (f_log(chi) - R(kRLo)) * R((kNR - 1) / (kRHi - kRLo));
     A = chi * lagrange4(s, kNR, X);
     B = chi * lagrange4(s + kNR, kNR, X);
   }
@@ -191,8 +194,8 @@ struct Tabs {
     return table2d(g + kOffCY + o, g + kOffCD + o, kNCX, kNCT, X, (t - R(kCTLo)) / ht, ht);
   }
   __device__ __forceinline__ void nbw_rates(R chig, R& T0, R& T3) const {
-    const R X = (m_log(chig) - R(kBLo)) * R((kNBX - 1) / (kBHi - kBLo));
-    const R damp = m_exp(R(-8.0 / 3.0) / chig);
+    const R X = (f_log(chig) - R(kBLo)) * R((kNBX - 1) / (kBHi - kBLo));
+    const R damp = f_exp(R(-8.0 / 3.0) * f_rcp(chig));
     T0 = damp * lagrange4(s + (kOffT0 - kOffRA), kNBX, X);
     T3 = damp * lagrange4(s + (kOffT3 - kOffRA), kNBX, X);
   }
@@ -204,7 +207,7 @@ struct Tabs {
   }
   __device__ __forceinline__ void vb_m(R chig, R& mp, R& mq) const {
     if (chig < R(kVbMin)) { mp = R(4); mq = R(7); return; }
-    const R X = (m_log(chig) - R(kVLo)) * R((kNV - 1) / (kVHi - kVLo));
+    const R X = (f_log(chig) - R(kVLo)) * R((kNV - 1) / (kVHi - kVLo));
     mp = lagrange4(s + (kOffMP - kOffRA), kNV, X);
     mq = lagrange4(s + (kOffMQ - kOffRA), kNV, X);
   }
@@ -323,23 +326,27 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(StepArgs a) {
       id = P.id[i];
     }
     bool decay = false, range = false;
-    const R om = norm(k);
-    const V3<R> nn = (R(1) / om) * k;
+    const R om2 = dot(k, k);
+    const R inv_om = f_rsqrt(om2);
+    const R om = om2 * inv_om;
+    const V3<R> nn = inv_om * k;
     V3<R> P1 = mk<R>(0, 0, 0);
     R chig = 0, rmix = 0;
     if (live && (a.flags & (QED_F_VB | QED_F_NBW))) {
       const EB<R> f = gather<R>(a, x, y, z);
       const R ne = dot(nn, f.E);
       const V3<R> Er = f.E - ne * nn + cross(nn, f.B);
-      const R er = norm(Er);
-      if (er > R(0)) {
+      const R er2 = dot(Er, Er);
+      if (er2 > R(0)) {
+        const R inv_er = f_rsqrt(er2);
+        const R er = er2 * inv_er;
         chig = R(kXiL) * om * er;
-        P1 = (R(1) / er) * Er;
+        P1 = inv_er * Er;
         V3<R> e1, e2;
         frame(nn, e1, e2);
-        const R thn = m_atan2(dot(P1, e2), dot(P1, e1));
+        const R thn = f_atan2(dot(P1, e2), dot(P1, e1));
         R s2, c2;
-        m_sincos(R(2) * (thn - th), &s2, &c2);
+        f_sincos(R(2) * (thn - th), &s2, &c2);
         const R x1 = xi.x * c2 - xi.z * s2, x3 = xi.x * s2 + xi.z * c2;
         xi.x = x1; xi.z = x3;
         th = thn;
@@ -353,7 +360,7 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(StepArgs a) {
             sd = dphi * (R(1) - d2 * (R(1.0 / 6.0) - d2 * R(1.0 / 120.0)));
             cd = R(1) - d2 * (R(0.5) - d2 * (R(1.0 / 24.0) - d2 * R(1.0 / 720.0)));
           } else {
-            m_sincos(dphi, &sd, &cd);
+            f_sincos(dphi, &sd, &cd);
           }
           const R y1 = cd * xi.x - sd * xi.y, y2 = sd * xi.x + cd * xi.y;
           xi.x = y1; xi.y = y2;
@@ -362,7 +369,7 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(StepArgs a) {
           if (chig > R(kChigMax)) { chig = R(kChigMax); range = true; }
           R T0, T3;
           tb.nbw_rates(chig, T0, T3);
-          const R Pd = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) / om * (T0 - xi.z * T3) * dt;
+          const R Pd = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) * inv_om * (T0 - xi.z * T3) * dt;
           const URand<R> u = urand<R>(a.seed, id, a.step, 3u);
           decay = u.u0 < Pd;
           rmix = u.u1;
@@ -425,35 +432,39 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(StepArgs a) {
       // Boris push
       const R hq = R(0.5) * q * dt;
       const V3<R> pm = p + hq * f.E;
-      const R gm = sqrt(R(1) + dot(pm, pm));
-      const V3<R> tau = (hq / gm) * f.B;
+      const V3<R> tau = (hq * f_rsqrt(R(1) + dot(pm, pm))) * f.B;
       const V3<R> pp = pm + cross(pm, tau);
-      const V3<R> sig = (R(2) / (R(1) + dot(tau, tau))) * tau;
+      const V3<R> sig = (R(2) * f_rcp(R(1) + dot(tau, tau))) * tau;
       const V3<R> pn = pm + cross(pp, sig) + hq * f.E;
       // T-BMT with beta, gamma of the mean of p^{n-1/2} and p^{n+1/2}
       if (a.flags & QED_F_SPIN) {
         const V3<R> pa = R(0.5) * (p + pn);
-        const R ga = sqrt(R(1) + dot(pa, pa));
-        const V3<R> be = (R(1) / ga) * pa;
-        const R gg = ga / (ga + R(1));
-        const V3<R> Om = (-R(kAe) * gg * dot(be, f.B)) * be + (R(kAe) + R(1) / ga) * f.B +
-                         (-(R(kAe) + R(1) / (ga + R(1)))) * cross(be, f.E);
+        const R ga2 = R(1) + dot(pa, pa);
+        const R inv_ga = f_rsqrt(ga2);
+        const R ga = ga2 * inv_ga;
+        const V3<R> be = inv_ga * pa;
+        const R inv_gp1 = f_rcp(ga + R(1));
+        const R gg = ga * inv_gp1;
+        const V3<R> Om = (-R(kAe) * gg * dot(be, f.B)) * be + (R(kAe) + inv_ga) * f.B +
+                         (-(R(kAe) + inv_gp1)) * cross(be, f.E);
         const V3<R> tv = hq * Om;
-        const V3<R> ov = (R(2) / (R(1) + dot(tv, tv))) * tv;
+        const V3<R> ov = (R(2) * f_rcp(R(1) + dot(tv, tv))) * tv;
         const V3<R> S1 = S + cross(S, tv);
         S = S + cross(S1, ov);
       }
-      const R g1 = sqrt(R(1) + dot(pn, pn));
+      const R g12 = R(1) + dot(pn, pn);
+      const R inv_g1 = f_rsqrt(g12);
+      const R g1 = g12 * inv_g1;
       if (sizeof(R) == 8) {
         x += a.dt * (double)(pn.x / g1); y += a.dt * (double)(pn.y / g1); z += a.dt * (double)(pn.z / g1);
       } else {
-        const R c = dt / g1;
+        const R c = dt * inv_g1;
         x = add_pos(x, c * pn.x); y = add_pos(y, c * pn.y); z = add_pos(z, c * pn.z);
       }
       if (a.flags & QED_F_NCS) {
-        R pmag = norm(pn);
-        pmag = pmag > R(0) ? pmag : R(1e-30);
-        const V3<R> nn = (R(1) / pmag) * pn;
+        const R pm2 = dot(pn, pn);
+        const R inv_pm = pm2 > R(0) ? f_rsqrt(pm2) : R(0);
+        const V3<R> nn = inv_pm * pn;
         const R nE = dot(nn, f.E);
         V3<R> v = g1 * (f.E - nE * nn) + cross(pn, f.B);
         R vm2 = dot(v, v);
@@ -473,16 +484,16 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(StepArgs a) {
             vm2 = (R)(vx * vx + vy * vy + vz * vz);
           }
         }
-        const R vm = sqrt(vm2);
-        chi = R(kXiL) * sqrt(vm2 + nE * nE);
-        if (chi >= R(kChiMin) && vm > R(0)) {
+        const R c2 = vm2 + nE * nE;
+        chi = c2 > R(0) ? R(kXiL) * c2 * f_rsqrt(c2) : R(0);
+        if (chi >= R(kChiMin) && vm2 > R(0) && inv_pm > R(0)) {
           if (chi > R(kChiMax)) { chi = R(kChiMax); range = true; }
-          av = (q / vm) * v;    // unit acceleration direction
+          av = (q * f_rsqrt(vm2)) * v;    // unit acceleration direction
           const V3<R> zeta = cross(nn, av);
           R A, B;
           tb.ncs_rates(chi, A, B);
           const R s = dot(S, zeta);
-          const R pref = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) / g1;
+          const R pref = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) * inv_g1;
           const R Wa = pref * A, Wb = pref * B;
           const R Pe = (Wa - s * Wb) * dt;
           const URand<R> u = urand<R>(a.seed, id, a.step, 0u);
@@ -490,11 +501,12 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(StepArgs a) {
             emit = true;   // completed by k_ncs_ev
           } else {
             // no emission: posterior mean spin, then collapse with P(+) = (1+|S|)/2
-            const R den = R(1) / (R(1) - Pe);
+            const R den = f_rcp(R(1) - Pe);
             const V3<R> Sb = (den * (R(1) - Wa * dt)) * S + (den * Wb * dt) * zeta;
-            const R m = norm(Sb);
-            const R sg = (u.u1 < R(0.5) * (R(1) + m)) ? R(1) : R(-1);
-            S = (sg / m) * Sb;
+            const R m2 = dot(Sb, Sb);
+            const R inv_m = f_rsqrt(m2);
+            const R sg = (u.u1 < R(0.5) * (R(1) + m2 * inv_m)) ? R(1) : R(-1);
+            S = (sg * inv_m) * Sb;
           }
         }
       }
@@ -538,12 +550,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a) {
   const unsigned int* cnt = a.tile_cnt[which];
   unsigned int* pre = a.tile_pre[which];
   const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int kItems = 8;                      // consecutive tiles per thread per pass
   if (threadIdx.x == 0) s_run = 0;
   __syncthreads();
-  for (unsigned long long b = 0; b < ntiles; b += kScanThreads) {
-    const unsigned long long idx = b + threadIdx.x;
-    const unsigned int v = idx < ntiles ? cnt[idx] : 0u;
-    unsigned int c = v;
+  for (unsigned long long b = 0; b < ntiles; b += (unsigned long long)kScanThreads * kItems) {
+    const unsigned long long first = b + (unsigned long long)threadIdx.x * kItems;
+    unsigned int v[kItems];
+    unsigned int tsum = 0;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      v[j] = (first + j < ntiles) ? cnt[first + j] : 0u;
+      tsum += v[j];
+    }
+    unsigned int c = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned int t = __shfl_up_sync(0xffffffffu, c, o);
@@ -561,9 +580,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a) {
       s_w[lane] = w;   // inclusive over warps
     }
     __syncthreads();
-    const unsigned int woff = warp ? s_w[warp - 1] : 0u;
     const unsigned long long run = s_run;
-    if (idx < ntiles) pre[idx] = (unsigned int)(run + woff + c - v);
+    unsigned long long acc = run + (warp ? s_w[warp - 1] : 0u) + c - tsum;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      if (first + j < ntiles) pre[first + j] = (unsigned int)acc;
+      acc += v[j];
+    }
     __syncthreads();
     if (threadIdx.x == 0) s_run = run + s_w[kScanThreads / 32 - 1];
     __syncthreads();
