@@ -27,23 +27,20 @@ namespace qedk {
 
 // ---- double <-> float without the FP64 pipe -------------------------------------------
 // double -> float by truncating the mantissa (error below one float ulp); |x| < 2^-126
-// flushes to zero, |x| >= 2^128 (and inf/NaN) gives inf.
+// flushes to zero.  Positions never approach the float overflow threshold.
 __device__ __forceinline__ float d2f_bits(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
-  const unsigned int sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-  if (e <= 0) return __uint_as_float(sign);
-  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
-  return __uint_as_float(sign | ((unsigned int)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+  const int e = (int)((hi >> 20) & 0x7FFu) - (1023 - 127);
+  const unsigned int f = (hi & 0x80000000u) | ((unsigned int)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  return __uint_as_float(e > 0 ? f : (hi & 0x80000000u));
 }
-// float -> double, exact for normal floats (subnormal floats flush to zero)
+// float -> double, exact for normal floats (zero and subnormal floats give signed zero)
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned int b = __float_as_uint(f);
-  const unsigned int sign = b & 0x80000000u, e = (b >> 23) & 0xFFu, man = b & 0x7FFFFFu;
-  if (e == 0) return __hiloint2double((int)sign, 0);
-  const unsigned int de = (e == 255u) ? 2047u : e - 127u + 1023u;
-  return __hiloint2double((int)(sign | (de << 20) | (man >> 3)), (int)(man << 29));
+  const unsigned int e = (b >> 23) & 0xFFu;
+  const unsigned int hi = (b & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)(e ? hi : (b & 0x80000000u)), (int)(e ? (b << 29) : 0u));
 }
 
 // ---- external fields (paper Sec. II D) ---------------------------------------------
@@ -260,6 +257,12 @@ struct TileShared {
 __device__ __forceinline__ unsigned long long tile_log(bool flag, unsigned int tile, unsigned int* tile_cnt,
                                                        unsigned long long* cursor, unsigned long long cap,
                                                        unsigned int* status, TileShared& sh, unsigned int* r_in) {
+  // most tiles carry no event: one barrier settles them
+  if (!__syncthreads_or(flag)) {
+    if (threadIdx.x == 0) tile_cnt[tile] = 0u;
+    *r_in = 0;
+    return ~0ull;
+  }
   const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned int ballot = __ballot_sync(0xffffffffu, flag);
   if (lane == 0) sh.wc[warp] = __popc(ballot);
@@ -271,15 +274,9 @@ __device__ __forceinline__ unsigned long long tile_log(bool flag, unsigned int t
       sh.wc[w] = run;
       run += c;
     }
-    unsigned long long base = 0;
-    int ok = 1;
-    if (run) {
-      base = atomicAdd(cursor, (unsigned long long)run);
-      if (base + run > cap) {
-        ok = 0;
-        atomicOr(status, QED_STATUS_CAPACITY);
-      }
-    }
+    const unsigned long long base = atomicAdd(cursor, (unsigned long long)run);
+    const int ok = base + run <= cap;
+    if (!ok) atomicOr(status, QED_STATUS_CAPACITY);
     sh.base = base;
     sh.ok = ok;
     tile_cnt[tile] = ok ? run : 0u;
@@ -292,7 +289,7 @@ __device__ __forceinline__ unsigned long long tile_log(bool flag, unsigned int t
   return slot;
 }
 
-template <typename R> struct Occ { static constexpr int v = sizeof(R) == 4 ? 3 : 2; };
+template <typename R> struct Occ { static constexpr int v = sizeof(R) == 4 ? 4 : 2; };
 
 // ======================================================================================
 // photon streaming pass
