@@ -304,14 +304,15 @@ def main():
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy)", "traffic": None,
                      "bytes_per_launch": dom_bytes / max(info["kernel_steps"], 1),
                      "avg_launch_ms": dom_ms / max(info["kernel_steps"], 1)},
-        "kernels": {"k_photon_ms": k_ph_ms, "k_lepton_ms": k_lep_ms, "event_kernels_ms": k_ev_ms,
+        "kernels": {"k_photon_ms": k_ph_ms, "k_lepton_ms": k_lep_ms, "after_photon_to_end_ms": k_ev_ms,
+                    "step_GBs": (ph_bytes + lep_bytes) / (ms * 1e-3) / 1e9,
                     "k_photon_GBs": ph_bytes / (k_ph_ms * 1e-3) / 1e9 if k_ph_ms else None,
                     "k_lepton_GBs": lep_bytes / (k_lep_ms * 1e-3) / 1e9 if k_lep_ms else None},
         "cpu_baseline": {"value": cpu_v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.cpu_sample} electrons of the same beam recipe, 20 steps after "
                                    f"{PRE_STEPS} untimed"},
         "e2e": e2e,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "clocks": clk.summary(),
         "counts_after": {"e": info["final_counts"][0], "pos": info["final_counts"][1],
                          "ph": info["final_counts"][2]},
@@ -321,7 +322,7 @@ def main():
         v64 = f64["particles"] / (f64["ms"] * 1e-3)
         line["f64"] = {"value": v64, "ms_per_step": f64["ms"] / args.steps, "speedup_mixed": value / v64,
                        "k_photon_ms": f64["kernel_ms"][0], "k_lepton_ms": f64["kernel_ms"][1],
-                       "event_kernels_ms": f64["kernel_ms"][2]}
+                       "after_photon_to_end_ms": f64["kernel_ms"][2]}
     print(json.dumps(line))
     sim.close()
     if dist is not None:

@@ -162,7 +162,10 @@ qed_status qed_set_next_id(qed_ctx *ctx, uint64_t next_id, void *stream);
 qed_status qed_get_next_id(qed_ctx *ctx, uint64_t *next_id, void *stream);
 
 /* One time step of every live particle (async, graph-capturable: no host sync, no
- * allocation).  Order (paper Sec. IV and the leapfrog of Sec. II F):
+ * allocation).  The lepton pass runs on a side stream of the context, forked from and
+ * joined back into `stream` by events, so all of the step's work is ordered after earlier
+ * work on `stream` and before later work on it.  Order (paper Sec. IV and the leapfrog of
+ * Sec. II F):
  *   photons: gather E, B at x^n, t; rotate Stokes into the local pair frame (Eq.
  *     rotation); VB phase (Eq. rotation2) if QED_F_VB; NBW decision and pair sampling
  *     (Sec. III D) if QED_F_NBW; survivors move x += dt n; decayed photons are removed
@@ -220,11 +223,12 @@ qed_status qed_step_static(qed_ctx *ctx, qed_particles *e, qed_particles *pos, q
  * `stream`.  clear != 0 resets it. */
 qed_status qed_read_status(qed_ctx *ctx, uint32_t *status, int clear, void *stream);
 
-/* Diagnostics: per-kernel timing.  While enabled, qed_step records CUDA events on `stream`
- * around its photon streaming kernel, its lepton streaming kernel and the remaining
- * event-processing kernels, and waits for them, adding the elapsed milliseconds to three
- * accumulators (so every step syncs its stream).  qed_get_timing returns and clears them
- * with the number of steps timed.  Off by default. */
+/* Diagnostics: per-kernel timing.  While enabled, qed_step records CUDA events around its
+ * photon streaming kernel (on `stream`) and its lepton streaming kernel (on the context's
+ * side stream, where it overlaps the photon chain), and from the end of the photon kernel
+ * to the end of the step, and waits for them, adding the elapsed milliseconds to three
+ * accumulators (so every step syncs).  qed_get_timing returns and clears them with the
+ * number of steps timed.  Off by default. */
 qed_status qed_set_timing(qed_ctx *ctx, int enable);
 qed_status qed_get_timing(qed_ctx *ctx, double ms[3], uint64_t *steps);
 

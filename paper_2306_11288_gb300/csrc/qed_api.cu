@@ -67,6 +67,15 @@ extern "C" qed_status qed_init_tables(qed_ctx** out, void* stream) {
     cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st); free(c);
     return r;
   }
+  if (r == QED_OK) {
+    e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st); free(c);
+      FAIL(QED_ERR_CUDA, "qed_init_tables: side stream: %s", cudaGetErrorString(e));
+    }
+  }
   c->alive = 1;
   *out = c;
   return QED_OK;
@@ -80,8 +89,11 @@ extern "C" qed_status qed_destroy(qed_ctx* c) {
     cudaFree(c->tile_cnt[k]); cudaFree(c->tile_pre[k]); cudaFree(c->rec[k]);
   }
   cudaFree(c->holes);
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < 6; ++k)
     if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
+  if (c->side) cudaStreamDestroy(c->side);
   c->alive = 0;
   free(c);
   return QED_OK;
@@ -317,12 +329,18 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
   a.holes = c->holes;
   a.user_stats = dev_stats;
   const int pi = prec == QED_PREC_F64 ? 0 : 1;
-  r = launch_step(a, prec, c->nblk[pi], S(stream), c->timing ? c->tev : nullptr);
+  StreamSet ss{c->side, c->fork, c->join, c->timing ? c->tev : nullptr};
+  r = launch_step(a, prec, c->nblk[pi], S(stream), ss);
   if (r != QED_OK || !c->timing) return r;
   CK(cudaEventSynchronize(c->tev[3]));
-  float m[3] = {0, 0, 0};
-  for (int k = 0; k < 3; ++k) CK(cudaEventElapsedTime(&m[k], c->tev[k], c->tev[k + 1]));
-  for (int k = 0; k < 3; ++k) c->tms[k] += m[k];
+  CK(cudaEventSynchronize(c->tev[5]));
+  float m[3] = {0, 0, 0}, tot = 0;
+  CK(cudaEventElapsedTime(&m[0], c->tev[0], c->tev[1]));
+  CK(cudaEventElapsedTime(&m[1], c->tev[4], c->tev[5]));
+  CK(cudaEventElapsedTime(&tot, c->tev[1], c->tev[3]));
+  c->tms[0] += m[0];
+  c->tms[1] += m[1];
+  c->tms[2] += tot;
   c->tsteps += 1;
   return QED_OK;
 }
@@ -330,7 +348,7 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
 extern "C" qed_status qed_set_timing(qed_ctx* c, int enable) {
   if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_set_timing: invalid context");
   if (enable && !c->tev[0]) {
-    for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&c->tev[k]));
+    for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&c->tev[k]));
   }
   c->timing = enable ? 1 : 0;
   return QED_OK;

@@ -48,10 +48,18 @@ struct StepArgs {
   qed_step_stats* user_stats;
 };
 
+// side stream and events of one step.  side == nullptr runs everything on the caller's
+// stream.  tev (optional, timing): [0] step start, [1] end of the photon pass, [3] step
+// end (caller's stream); [4], [5] around the lepton pass (on the stream that runs it).
+struct StreamSet {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+  cudaEvent_t* tev;
+};
+
 // launches one step; prec selects the instantiation; nblk = grid sizes (photon, lepton,
-// events).  ev (optional): four events recorded before the photon pass, between the
-// passes, after the lepton pass and at the end.
-qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, cudaEvent_t* ev);
+// events)
+qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, const StreamSet& ss);
 // occupancy-derived persistent grid sizes
 qed_status step_grid_sizes(qed_precision prec, int* nblk);
 size_t nbw_rec_bytes(qed_precision p);
@@ -76,8 +84,10 @@ struct qed_ctx {
   unsigned int* holes;
   int nblk[2][3];   // [precision][photon, lepton, events]
   int alive;
+  cudaStream_t side;                  // lepton pass runs here, overlapping the photon chain
+  cudaEvent_t fork, join;
   int timing;
-  cudaEvent_t tev[4];
+  cudaEvent_t tev[6];
   double tms[3];
   unsigned long long tsteps;
 };

@@ -186,5 +186,6 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
   a.rec_cap[1] = kStRecNcs;
   a.user_stats = dev_stats;
   const int pi = pr == QED_PREC_F64 ? 0 : 1;
-  return launch_step(a, pr, c->nblk[pi], s, nullptr);
+  const StreamSet ss{c->side, c->fork, c->join, nullptr};
+  return launch_step(a, pr, c->nblk[pi], s, ss);
 }

@@ -526,15 +526,14 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(StepArgs a) {
 }
 
 // ======================================================================================
-// exclusive scans of the tile counts (block 0: photon tiles, block 1: lepton tiles)
+// exclusive scan of the tile counts (which = 0: photon tiles, 1: lepton tiles), one block
 // ======================================================================================
 constexpr int kScanThreads = 1024;
 
-__global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a) {
+__global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a, int which) {
   __shared__ unsigned int s_w[kScanThreads / 32];
   __shared__ unsigned long long s_run;
   DevState* st = a.st;
-  const int which = blockIdx.x;
   unsigned long long ntiles, nph = 0;
   if (which == 0) {
     nph = a.sp[2].present ? st->n_live[2] : 0ull;
@@ -890,18 +889,37 @@ __global__ void __launch_bounds__(kTile) k_ncs_ev(StepArgs a) {
   }
 }
 
+// Photon chain on the caller's stream; the lepton pass on the context's side stream
+// (forked after all earlier work on the caller's stream, joined before the lepton scan):
+// the lepton pass reads only particles below the counts of the step start, the pair
+// births of k_nbw_ev go above them, so the two chains are independent until k_ncs_ev.
 template <typename R>
-static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, cudaEvent_t* ev) {
-  if (ev) cudaEventRecord(ev[0], s);
+static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, const StreamSet& ss) {
+  const bool fork = ss.side != nullptr;
+  if (ss.tev) cudaEventRecord(ss.tev[0], s);
+  if (fork) {
+    cudaEventRecord(ss.fork, s);
+    cudaStreamWaitEvent(ss.side, ss.fork, 0);
+    if (ss.tev) cudaEventRecord(ss.tev[4], ss.side);
+    k_lepton<R><<<nb[1], kTile, 0, ss.side>>>(a);
+    if (ss.tev) cudaEventRecord(ss.tev[5], ss.side);
+    cudaEventRecord(ss.join, ss.side);
+  }
   k_photon<R><<<nb[0], kTile, 0, s>>>(a);
-  if (ev) cudaEventRecord(ev[1], s);
-  k_lepton<R><<<nb[1], kTile, 0, s>>>(a);
-  if (ev) cudaEventRecord(ev[2], s);
-  k_scan<<<2, kScanThreads, 0, s>>>(a);
+  if (ss.tev) cudaEventRecord(ss.tev[1], s);
+  k_scan<<<1, kScanThreads, 0, s>>>(a, 0);
   k_nbw_ev<R><<<nb[2], kTile, 0, s>>>(a);
   k_fill<R><<<nb[2], kTile, 0, s>>>(a);
+  if (fork) {
+    cudaStreamWaitEvent(s, ss.join, 0);
+  } else {
+    if (ss.tev) cudaEventRecord(ss.tev[4], s);
+    k_lepton<R><<<nb[1], kTile, 0, s>>>(a);
+    if (ss.tev) cudaEventRecord(ss.tev[5], s);
+  }
+  k_scan<<<1, kScanThreads, 0, s>>>(a, 1);
   k_ncs_ev<R><<<nb[2], kTile, 0, s>>>(a);
-  if (ev) cudaEventRecord(ev[3], s);
+  if (ss.tev) cudaEventRecord(ss.tev[3], s);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error("step launch failed: %s", cudaGetErrorString(e));
@@ -910,8 +928,8 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, cud
   return QED_OK;
 }
 
-qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, cudaEvent_t* ev) {
-  return prec == QED_PREC_F64 ? launch_t<double>(a, nblk, s, ev) : launch_t<float>(a, nblk, s, ev);
+qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, const StreamSet& ss) {
+  return prec == QED_PREC_F64 ? launch_t<double>(a, nblk, s, ss) : launch_t<float>(a, nblk, s, ss);
 }
 
 qed_status step_grid_sizes(qed_precision prec, int* nblk) {
