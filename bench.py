@@ -54,10 +54,18 @@ def c2_workload(n, seed):
 
 
 # algorithmic bytes per particle-step (state that must be read and written)
+#   photon pass: read x,y,z + k + xi + theta + id, write x,y,z + xi + theta
+#   lepton pass: read x,y,z + p + S + id, write x,y,z + p + S
 BYTES = {
-    "mixed": {"lep": 104, "ph": 104, "ncs_birth": 68, "nbw_birth": 120},
-    "f64": {"lep": 152, "ph": 152, "ncs_birth": 104, "nbw_birth": 176},
+    "mixed": {"lep": 104, "ph": 100, "ncs_birth": 68, "nbw_birth": 120},
+    "f64": {"lep": 152, "ph": 144, "ncs_birth": 104, "nbw_birth": 176},
 }
+
+# DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of one launch divided
+# by the particles it processed) from the ncu capture summarised in
+# profiles/k_photon_k_lepton_c2_1e6_traffic.md; scaled to a launch by its particle count.
+# Must be re-captured whenever either streaming kernel changes.
+TRAFFIC_PER_UNIT = {"k_photon": 365369088 / 4228162, "k_lepton": 85388032 / 1331934}
 
 
 class ClockSampler:
@@ -301,13 +309,17 @@ def main():
                    "processes": "NCS+NBW+VB+T-BMT, compaction every step", "pre_steps": PRE_STEPS,
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy)", "traffic": None,
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy)",
+                     "traffic": TRAFFIC_PER_UNIT[dom] * (info["ph_units"] if dom == "k_photon"
+                                                         else info["lep_units"]) / args.steps,
                      "bytes_per_launch": dom_bytes / max(info["kernel_steps"], 1),
                      "avg_launch_ms": dom_ms / max(info["kernel_steps"], 1)},
         "kernels": {"k_photon_ms": k_ph_ms, "k_lepton_ms": k_lep_ms, "after_photon_to_end_ms": k_ev_ms,
                     "step_GBs": (ph_bytes + lep_bytes) / (ms * 1e-3) / 1e9,
                     "k_photon_GBs": ph_bytes / (k_ph_ms * 1e-3) / 1e9 if k_ph_ms else None,
-                    "k_lepton_GBs": lep_bytes / (k_lep_ms * 1e-3) / 1e9 if k_lep_ms else None},
+                    "k_lepton_GBs": lep_bytes / (k_lep_ms * 1e-3) / 1e9 if k_lep_ms else None,
+                    "photons_per_launch": info["ph_units"] / args.steps,
+                    "leptons_per_launch": info["lep_units"] / args.steps},
         "cpu_baseline": {"value": cpu_v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.cpu_sample} electrons of the same beam recipe, 20 steps after "
                                    f"{PRE_STEPS} untimed"},
