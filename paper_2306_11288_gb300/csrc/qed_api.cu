@@ -241,6 +241,7 @@ static qed_status fill_species(SpeciesArgs& a, const qed_particles* p) {
   a.theta = p->soa.theta; a.w = p->soa.w; a.id = p->soa.id;
   a.cap = p->cap;
   a.present = p->cap > 0 ? 1 : 0;
+  a.stage = soa_aligned16(a);
   return QED_OK;
 }
 

@@ -1,0 +1,162 @@
+"""Parity at full size, in the launch configuration the benchmark times.
+
+1. Bulk-staged and direct tile loads agree bit for bit: the same mixed-path run on arrays
+   that are 16-byte aligned (full tiles staged through shared memory) and on arrays
+   offset by one element (every tile loaded directly), with ragged e-, e+ and photon
+   counts spanning several tiles per block.
+2. The 1e6-electron focused-pulse workload at its benchmark state (150 steps in, the
+   beam at the focus): after one more GPU step, a random sample of particles is stepped
+   by the oracle from the same pre-step state (the random numbers of a particle depend
+   only on its id, the step and the seed) and compared one by one.  FP64 path: decisions
+   exact except the oracle's logged near-ties, values within 1e-10.  Mixed path: values
+   within 2e-5; decisions may differ only where float rounding moves the threshold,
+   bounded at 0.5 % of the sample."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2306_11288_gb300 as q  # noqa: E402
+
+ALL = q.QED_F_NCS | q.QED_F_NBW | q.QED_F_VB | q.QED_F_SPIN
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    q.build()
+    c = q.qed_init_tables()
+    yield c
+    torch.cuda.synchronize()
+
+
+def _crossed_field_sets(ne, npos, nph, seed):
+    rng = np.random.default_rng(seed)
+
+    def lep(n, first):
+        s = rng.normal(size=(n, 3))
+        s /= np.linalg.norm(s, axis=1, keepdims=True)
+        p = rng.normal(size=(n, 3)) * 30 + np.array([0, 0, 4000.0])
+        return {"x": rng.normal(size=n), "y": rng.normal(size=n), "z": rng.normal(size=n),
+                "px": p[:, 0], "py": p[:, 1], "pz": p[:, 2], "s1": s[:, 0], "s2": s[:, 1], "s3": s[:, 2],
+                "w": rng.uniform(0.5, 2, n), "id": np.arange(first, first + n, dtype=np.uint64)}
+
+    e, pos = lep(ne, 0), lep(npos, ne)
+    k = rng.normal(size=(nph, 3)) * 50 + np.array([0, 0, 3000.0])
+    xi = rng.normal(size=(nph, 3))
+    xi *= rng.uniform(0, 1, (nph, 1)) / np.linalg.norm(xi, axis=1, keepdims=True)
+    first = ne + npos
+    ph = {"x": rng.normal(size=nph), "y": rng.normal(size=nph), "z": rng.normal(size=nph), "px": k[:, 0],
+          "py": k[:, 1], "pz": k[:, 2], "s1": xi[:, 0], "s2": xi[:, 1], "s3": xi[:, 2],
+          "theta": rng.uniform(-3, 3, nph), "w": np.ones(nph), "id": np.arange(first, first + nph, dtype=np.uint64)}
+    E0 = 150.0
+    return {"e": e, "pos": pos, "ph": ph, "field": {"kind": "uniform", "E": (E0, 0, 0), "B": (0, -E0, 0)},
+            "dt": math.pi / 100, "seed": 9, "next_id": first + nph}
+
+
+def test_staged_and_direct_tile_loads_agree_bit_for_bit(ctx):
+    blocks = torch.cuda.get_device_properties(0).multi_processor_count * 4   # mixed-path grid
+    per = blocks * 256
+    ne, npos, nph = 3 * per + 1234, per + 77, 4 * per + 99   # ragged, several tiles per block
+    wl = _crossed_field_sets(ne, npos, nph, seed=61)
+    runs = []
+    for misalign in (False, True):
+        sim = q.Simulation(wl, prec=q.QED_PREC_MIXED, ctx=ctx, misalign=misalign)
+        sim.run(6, ALL)
+        runs.append((sim.state(), sim.counters(), sim.status()))
+        sim.close()
+    (a, ca, sa), (b, cb, sb) = runs
+    assert sa == 0 and sb == 0
+    assert ca == cb and ca["n_ncs_e"] > 0 and ca["n_ncs_p"] > 0 and ca["n_nbw"] > 0
+    assert a["next_id"] == b["next_id"]
+    for sp in ("e", "pos", "ph"):
+        for k in a[sp]:
+            assert np.array_equal(a[sp][k], b[sp][k]), (sp, k)
+
+
+# ---------------------------------------------------------------------------------------
+N_BENCH, PRE_STEPS, T_SHIFT = 1_000_000, 150, 8.5 * math.pi   # the benchmark's workload
+
+
+def _bench_workload():
+    wl = workloads.c2(n=N_BENCH, seed=2)
+    wl["e"]["z"] = wl["e"]["z"] + T_SHIFT
+    wl["t0"] = T_SHIFT
+    wl["step0"] = int(round(T_SHIFT / wl["dt"]))
+    return wl
+
+
+def _take(d, ids):
+    o = np.argsort(d["id"])
+    pos = np.searchsorted(d["id"], ids, sorter=o)
+    pos = np.clip(pos, 0, len(o) - 1) if len(o) else pos
+    idx = o[pos] if len(o) else np.zeros(0, dtype=np.int64)
+    found = (d["id"][idx] == ids) if len(o) else np.zeros(len(ids), dtype=bool)
+    return {k: v[idx] for k, v in d.items()}, found
+
+
+def _sample_step(orc, ctx, prec, tol, max_mismatch):
+    wl = _bench_workload()
+    sim = q.Simulation(wl, prec=prec, ctx=ctx, cap_e=N_BENCH + 2_000_000, cap_p=2_000_000, cap_ph=10_000_000)
+    sim.run(PRE_STEPS, ALL)
+    pre = sim.state()
+    t, step = sim.t, sim.step_no
+    sim.run(1, ALL)
+    post = sim.state()
+    assert sim.status() == 0
+    sim.close()
+    assert len(pre["ph"]["id"]) > N_BENCH and len(pre["pos"]["id"]) > N_BENCH // 1000
+
+    rng = np.random.default_rng(5)
+    pick = {sp: np.sort(rng.choice(pre[sp]["id"], size=min(n, len(pre[sp]["id"])), replace=False))
+            for sp, n in (("e", 4000), ("pos", 2000), ("ph", 6000))}
+    owl = {"field": wl["field"], "dt": wl["dt"], "seed": wl["seed"], "t0": t, "step0": step,
+           "next_id": int(pre["next_id"])}
+    for sp in ("e", "pos", "ph"):
+        owl[sp], found = _take(pre[sp], pick[sp])
+        assert found.all()
+    n_near0 = len(orc.near_log()[0])
+    osim = oracle.Sim(orc, owl)
+    osim.run(1, ALL)
+    near_ids, near_steps, _ = orc.near_log()
+    near = set(int(i) for i, s in zip(near_ids[n_near0:], near_steps[n_near0:]) if s == step)
+    ost = osim.state()
+
+    mism = 0
+    total = 0
+    for sp in ("e", "pos", "ph"):
+        g, gf = _take(post[sp], pick[sp])
+        o, of = _take(ost[sp], pick[sp])
+        if sp != "ph":
+            assert gf.all() and of.all()
+        ok = gf & of
+        # photons: decayed on one side only is a decision mismatch
+        dec_mis = (gf != of)
+        p_g = np.stack([g["px"], g["py"], g["pz"]], 1)
+        p_o = np.stack([o["px"], o["py"], o["pz"]], 1)
+        dp = np.linalg.norm(p_g - p_o, axis=1) / np.maximum(np.linalg.norm(p_o, axis=1), 1.0)
+        ds = np.abs(np.stack([g[k] - o[k] for k in ("s1", "s2", "s3")], 1)).max(1)
+        dx = np.abs(np.stack([(g[k] - o[k]) / (np.abs(o[k]) + 1.0) for k in ("x", "y", "z")], 1)).max(1)
+        bad = dec_mis | (ok & ((dp > tol) | (ds > tol) | (dx > tol)))
+        exempt = np.array([int(i) in near for i in pick[sp]], dtype=bool)
+        mism += int((bad & ~exempt).sum())
+        total += len(pick[sp])
+        good = ok & ~bad
+        assert good.sum() > 0.9 * len(pick[sp]), sp
+        assert np.array_equal(g["w"][good], o["w"][good])
+    assert mism <= max_mismatch * total, f"{mism} of {total} sampled particles differ"
+
+
+def test_bench_workload_sampled_parity_fp64(orc, ctx):
+    _sample_step(orc, ctx, q.QED_PREC_F64, 1e-10, 0.0)
+
+
+def test_bench_workload_sampled_parity_mixed(orc, ctx):
+    _sample_step(orc, ctx, q.QED_PREC_MIXED, 2e-5, 0.005)
