@@ -138,7 +138,7 @@ qed_status qed_destroy(qed_ctx *ctx);
 
 /* Wrap caller-owned device arrays as one species (paper Sec. IV: ParticleList).
  * `buffers` pointers are copied; the arrays must outlive the returned object.  All
- * particle sets stepped together must share one precision.  `n` <= `capacity` < 2^32.
+ * particle sets stepped together must share one precision.  `n` <= `capacity` <= 2^32 - 256.
  * The live count lives in the context (one set per species per context).  Grows the
  * context's step scratch (event logs, per-tile counts) to the capacity.
  * Syncs `stream`.  Errors: QED_ERR_INVALID_ARG (NULL array, n > capacity, photon
@@ -223,12 +223,12 @@ qed_status qed_step_static(qed_ctx *ctx, qed_particles *e, qed_particles *pos, q
  * `stream`.  clear != 0 resets it. */
 qed_status qed_read_status(qed_ctx *ctx, uint32_t *status, int clear, void *stream);
 
-/* Diagnostics: per-kernel timing.  While enabled, qed_step records CUDA events around its
- * photon streaming kernel (on `stream`) and its lepton streaming kernel (on the context's
- * side stream, where it overlaps the photon chain), and from the end of the photon kernel
- * to the end of the step, and waits for them, adding the elapsed milliseconds to three
- * accumulators (so every step syncs).  qed_get_timing returns and clears them with the
- * number of steps timed.  Off by default. */
+/* Diagnostics: per-kernel timing.  While enabled, qed_step runs all its kernels on `stream`
+ * one after the other (no side stream, no programmatic dependent launches), records CUDA
+ * events around the photon streaming kernel, the lepton streaming kernel and the event
+ * kernels, and waits for them, adding the elapsed milliseconds to three accumulators (so
+ * every step syncs and is slower than an untimed one).  qed_get_timing returns and clears
+ * them with the number of steps timed.  Off by default. */
 qed_status qed_set_timing(qed_ctx *ctx, int enable);
 qed_status qed_get_timing(qed_ctx *ctx, double ms[3], uint64_t *steps);
 

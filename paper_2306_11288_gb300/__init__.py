@@ -209,21 +209,18 @@ _NAMES = ("x", "y", "z", "px", "py", "pz", "s1", "s2", "s3", "theta", "w")
 class Species:
     """Device SoA (torch tensors) for one species, wrapped as a qed_particles handle."""
 
-    def __init__(self, ctx, species, cap, prec=QED_PREC_F64, device="cuda", pin_host=False, misalign=False):
-        """misalign: start every array one element past an allocation boundary, so that no
-        array is 16-byte aligned and the step loads every tile directly (no bulk staging)."""
+    def __init__(self, ctx, species, cap, prec=QED_PREC_F64, device="cuda", pin_host=False):
         import torch
         self.torch = torch
         self.ctx, self.species, self.cap, self.prec = ctx, species, int(cap), prec
         rt = torch.float64 if prec == QED_PREC_F64 else torch.float32
-        off = 1 if misalign else 0
         self.t = {}
         for k in _NAMES:
             if k == "theta" and species != QED_PHOTON:
                 continue
             dt = torch.float64 if k in ("x", "y", "z") else rt
-            self.t[k] = torch.zeros(max(self.cap, 1) + off, dtype=dt, device=device)[off:]
-        self.t["id"] = torch.zeros(max(self.cap, 1) + off, dtype=torch.int64, device=device)[off:]
+            self.t[k] = torch.zeros(max(self.cap, 1), dtype=dt, device=device)
+        self.t["id"] = torch.zeros(max(self.cap, 1), dtype=torch.int64, device=device)
         self.soa = qed_soa()
         for k, v in self.t.items():
             setattr(self.soa, k, v.data_ptr())
@@ -294,19 +291,18 @@ def fields_from_spec(spec: dict, grid=None) -> qed_fields:
 class Simulation:
     """One context + e-, e+, photon sets stepping together (device resident)."""
 
-    def __init__(self, wl: dict, prec=QED_PREC_F64, cap_e=None, cap_p=None, cap_ph=None, ctx=None, misalign=False):
+    def __init__(self, wl: dict, prec=QED_PREC_F64, cap_e=None, cap_p=None, cap_ph=None, ctx=None):
         import torch
         self.torch = torch
         self.ctx = ctx if ctx is not None else qed_init_tables()
         self.own_ctx = ctx is None
         ne, npos, nph = len(wl["e"]["id"]), len(wl["pos"]["id"]), len(wl["ph"]["id"])
-        ma = {"misalign": misalign}
-        self.e = Species(self.ctx, QED_ELECTRON, cap_e if cap_e is not None else max(4 * (ne + nph), 16), prec,
-                         **ma).load(wl["e"])
+        self.e = Species(self.ctx, QED_ELECTRON, cap_e if cap_e is not None else max(4 * (ne + nph), 16),
+                         prec).load(wl["e"])
         self.pos = Species(self.ctx, QED_POSITRON, cap_p if cap_p is not None else max(4 * (ne + npos + nph), 16),
-                           prec, **ma).load(wl["pos"])
+                           prec).load(wl["pos"])
         self.ph = Species(self.ctx, QED_PHOTON, cap_ph if cap_ph is not None else max(8 * (ne + npos + nph), 16),
-                          prec, **ma).load(wl["ph"])
+                          prec).load(wl["ph"])
         self.grid = None
         if wl["field"]["kind"] == "grid2d":
             g = wl["grid"]

@@ -152,7 +152,8 @@ extern "C" qed_status particles_create(qed_ctx* c, qed_species sp, const qed_soa
   if (prec != QED_PREC_F64 && prec != QED_PREC_MIXED) FAIL(QED_ERR_INVALID_ARG, "particles_create: bad precision");
   if (n > cap) FAIL(QED_ERR_INVALID_ARG, "particles_create: n (%llu) > capacity (%llu)",
                     (unsigned long long)n, (unsigned long long)cap);
-  if (cap >= (1ull << 32)) FAIL(QED_ERR_INVALID_ARG, "particles_create: capacity must be below 2^32");
+  if (cap > (1ull << 32) - 256)
+    FAIL(QED_ERR_INVALID_ARG, "particles_create: capacity must not exceed 2^32 - 256");
   if (cap > 0) {
     const void* req[] = {b->x, b->y, b->z, b->px, b->py, b->pz, b->s1, b->s2, b->s3, b->w, b->id};
     for (const void* p : req)
@@ -241,7 +242,6 @@ static qed_status fill_species(SpeciesArgs& a, const qed_particles* p) {
   a.theta = p->soa.theta; a.w = p->soa.w; a.id = p->soa.id;
   a.cap = p->cap;
   a.present = p->cap > 0 ? 1 : 0;
-  a.stage = soa_aligned16(a);
   return QED_OK;
 }
 
@@ -330,7 +330,9 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
   a.holes = c->holes;
   a.user_stats = dev_stats;
   const int pi = prec == QED_PREC_F64 ? 0 : 1;
-  StreamSet ss{c->side, c->fork, c->join, c->timing ? c->tev : nullptr};
+  // per-kernel timing runs the passes one after the other, so that each duration is the
+  // kernel's own (no overlap of the lepton pass with the photon chain)
+  StreamSet ss{c->timing ? nullptr : c->side, c->fork, c->join, c->timing ? c->tev : nullptr};
   r = launch_step(a, prec, c->nblk[pi], S(stream), ss);
   if (r != QED_OK || !c->timing) return r;
   CK(cudaEventSynchronize(c->tev[3]));
@@ -338,10 +340,10 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
   float m[3] = {0, 0, 0}, tot = 0;
   CK(cudaEventElapsedTime(&m[0], c->tev[0], c->tev[1]));
   CK(cudaEventElapsedTime(&m[1], c->tev[4], c->tev[5]));
-  CK(cudaEventElapsedTime(&tot, c->tev[1], c->tev[3]));
+  CK(cudaEventElapsedTime(&tot, c->tev[1], c->tev[3]));   // event kernels and the lepton pass
   c->tms[0] += m[0];
   c->tms[1] += m[1];
-  c->tms[2] += tot;
+  c->tms[2] += tot - m[1];
   c->tsteps += 1;
   return QED_OK;
 }

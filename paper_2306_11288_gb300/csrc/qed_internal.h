@@ -23,16 +23,7 @@ struct SpeciesArgs {
   uint64_t* id;
   unsigned long long cap;
   int present;
-  int stage;   // every array 16-byte aligned: full tiles may be bulk-copied to shared memory
 };
-
-// 1 when every array of the set starts on a 16-byte boundary
-inline int soa_aligned16(const SpeciesArgs& a) {
-  const void* p[] = {a.x, a.y, a.z, a.px, a.py, a.pz, a.s1, a.s2, a.s3, a.theta, a.id};
-  for (const void* q : p)
-    if (reinterpret_cast<uintptr_t>(q) & 15u) return 0;
-  return 1;
-}
 
 // float copies of per-step constants for the mixed path (no FP64 arithmetic in kernels)
 struct FloatConsts {

@@ -75,7 +75,6 @@ static void species_args(SpeciesArgs& a, const qed_particles* p) {
   a.theta = p->soa.theta; a.w = p->soa.w; a.id = p->soa.id;
   a.cap = p->cap;
   a.present = p->cap > 0 ? 1 : 0;
-  a.stage = soa_aligned16(a);
 }
 
 }  // namespace qedk

@@ -294,17 +294,6 @@ __device__ __forceinline__ unsigned long long tile_log(bool flag, unsigned int t
 
 template <typename R> struct Occ { static constexpr int v = sizeof(R) == 4 ? 4 : 2; };
 
-// Bulk staging of the next tile in the mixed-path streaming kernels (compile-time choice).
-// Both passes are issue-bound at four blocks per SM: on the 1e6-electron focused-pulse
-// workload staging made the photon pass slower (extra instructions, barrier waits behind
-// the issuing warp) and left the lepton pass unchanged, so only the lepton pass stages.
-#ifndef QED_STAGE_PHOTON
-#define QED_STAGE_PHOTON 0
-#endif
-#ifndef QED_STAGE_LEPTON
-#define QED_STAGE_LEPTON 1
-#endif
-
 // ---- programmatic dependent launch ------------------------------------------------------
 // The event kernels are launched as programmatic dependents of the kernel before them on
 // the stream: they may be scheduled while it drains and wait here for its completion (and
@@ -313,162 +302,32 @@ template <typename R> struct Occ { static constexpr int v = sizeof(R) == 4 ? 4 :
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// ---- bulk-copy staging of the next tile (mixed path) ----------------------------------
-// A block walks its tiles in a grid-stride loop.  While it computes one tile, the particle
-// arrays of its next tile stream into the other half of a double buffer in shared memory
-// by cp.async.bulk (one thread issues; an mbarrier counts the bytes), so the global-load
-// latency of the next tile hides behind the arithmetic of this one.  Only full tiles of
-// sets whose arrays are 16-byte aligned are staged; the ragged last tile loads directly.
-__device__ __forceinline__ unsigned int smem_u32(const void* p) {
-  return (unsigned int)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned int bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned int bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned long long* bar, unsigned int parity) {
-  unsigned int ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait for phase `parity` of `bar`: gives up after 2^31 SM clocks (about a second)
-__device__ __noinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity) {
-  const long long t0 = clock64();
-  for (unsigned int it = 0; it < (1u << 26); ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if (clock64() - t0 > (1ll << 31)) break;
-  }
-  return false;
-}
-// waits for a staged tile; on time-out flags QED_STATUS_TIMEOUT, waits once more (bounded)
-// for the copy still in flight and reports the tile as not loaded
-__device__ __forceinline__ bool stage_wait(unsigned long long* bar, unsigned int parity, unsigned int* status) {
-  if (mbar_wait(bar, parity)) return true;
-  atomicOr(status, QED_STATUS_TIMEOUT);
-  mbar_wait(bar, parity);
-  return false;
-}
-
-struct PhStage {               // one photon tile, mixed layout: 15360 bytes
-  double x[kTile], y[kTile], z[kTile];
-  unsigned long long id[kTile];
-  float k[3][kTile], xi[3][kTile], th[kTile];
-};
-struct LepStage {              // one lepton tile, mixed layout: 14336 bytes
-  double x[kTile], y[kTile], z[kTile];
-  unsigned long long id[kTile];
-  float p[3][kTile], s[3][kTile];
-};
-
-__device__ __forceinline__ void issue_ph(PhStage& s, const SpeciesArgs& P, unsigned long long i0,
-                                         unsigned long long* bar) {
-  constexpr unsigned int D = kTile * 8, F = kTile * 4;
-  mbar_expect(bar, (unsigned int)sizeof(PhStage));
-  bulk_g2s(s.x, P.x + i0, D, bar);
-  bulk_g2s(s.y, P.y + i0, D, bar);
-  bulk_g2s(s.z, P.z + i0, D, bar);
-  bulk_g2s(s.id, P.id + i0, D, bar);
-  bulk_g2s(s.k[0], (const float*)P.px + i0, F, bar);
-  bulk_g2s(s.k[1], (const float*)P.py + i0, F, bar);
-  bulk_g2s(s.k[2], (const float*)P.pz + i0, F, bar);
-  bulk_g2s(s.xi[0], (const float*)P.s1 + i0, F, bar);
-  bulk_g2s(s.xi[1], (const float*)P.s2 + i0, F, bar);
-  bulk_g2s(s.xi[2], (const float*)P.s3 + i0, F, bar);
-  bulk_g2s(s.th, (const float*)P.theta + i0, F, bar);
-}
-__device__ __forceinline__ void issue_lep(LepStage& s, const SpeciesArgs& L, unsigned long long i0,
-                                          unsigned long long* bar) {
-  constexpr unsigned int D = kTile * 8, F = kTile * 4;
-  mbar_expect(bar, (unsigned int)sizeof(LepStage));
-  bulk_g2s(s.x, L.x + i0, D, bar);
-  bulk_g2s(s.y, L.y + i0, D, bar);
-  bulk_g2s(s.z, L.z + i0, D, bar);
-  bulk_g2s(s.id, L.id + i0, D, bar);
-  bulk_g2s(s.p[0], (const float*)L.px + i0, F, bar);
-  bulk_g2s(s.p[1], (const float*)L.py + i0, F, bar);
-  bulk_g2s(s.p[2], (const float*)L.pz + i0, F, bar);
-  bulk_g2s(s.s[0], (const float*)L.s1 + i0, F, bar);
-  bulk_g2s(s.s[1], (const float*)L.s2 + i0, F, bar);
-  bulk_g2s(s.s[2], (const float*)L.s3 + i0, F, bar);
-}
-
 // ======================================================================================
 // photon streaming pass
 // ======================================================================================
 template <typename R>
 __global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(StepArgs a) {
   pdl_trigger();
-  constexpr bool kStg = sizeof(R) == 4 && QED_STAGE_PHOTON;
   __shared__ R s_rates[kSmemRateLen];
   __shared__ TileShared s_tile;
-  __shared__ __align__(128) unsigned char s_stg[kStg ? 2 * sizeof(PhStage) : 16];
-  __shared__ __align__(8) unsigned long long s_bar[2];
   DevState* st = a.st;
   const SpeciesArgs& P = a.sp[2];
   const unsigned long long n = P.present ? st->n_live[2] : 0ull;
   const unsigned int ntiles = (unsigned int)((n + kTile - 1) / kTile);
-  const bool stage = kStg && P.stage;
-  PhStage* stg = reinterpret_cast<PhStage*>(s_stg);
-  if (stage && threadIdx.x == 0) {
-    mbar_init(&s_bar[0]);
-    mbar_init(&s_bar[1]);
-    mbar_fence_init();
-  }
   const Tabs<R> tb{reinterpret_cast<const R*>(a.tables), s_rates};
   stage_rates(tb.g, s_rates);
   __syncthreads();
-  if (stage && threadIdx.x == 0 && blockIdx.x < ntiles && (unsigned long long)(blockIdx.x + 1) * kTile <= n)
-    issue_ph(stg[0], P, (unsigned long long)blockIdx.x * kTile, &s_bar[0]);
   const unsigned int epoch = st->epoch;
   const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.ff.dt;
   NbwRec<R>* evlog = reinterpret_cast<NbwRec<R>*>(a.rec[0]);
-  // kk selects the buffer; bit b of phase is the parity of buffer b's next fill, flipped
-  // each time a staged tile is taken from it (unstaged tiles leave it alone)
-  unsigned int kk = 0, phase = 0;
-  for (unsigned int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++kk) {
-    const unsigned long long i = (unsigned long long)tile * kTile + threadIdx.x;
-    // the buffer for the next tile was last read in the previous iteration, before the
-    // barriers of its tile_log
-    const unsigned int nxt = tile + gridDim.x;
-    if (stage && threadIdx.x == 0 && nxt < ntiles && (unsigned long long)(nxt + 1) * kTile <= n)
-      issue_ph(stg[(kk + 1) & 1], P, (unsigned long long)nxt * kTile, &s_bar[(kk + 1) & 1]);
-    const bool staged = stage && (unsigned long long)(tile + 1) * kTile <= n;
-    bool loaded = true;
-    if (staged) {
-      loaded = stage_wait(&s_bar[kk & 1], (phase >> (kk & 1)) & 1u, &st->status);
-      phase ^= 1u << (kk & 1);
-    }
-    const bool live = i < n && loaded;
+  for (unsigned int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const unsigned int i = tile * kTile + threadIdx.x;   // capacity <= 2^32 - 256: no wrap
+    const bool live = i < (unsigned int)n;
     double x = 0, y = 0, z = 0;
     V3<R> k = mk<R>(1, 0, 0), xi = mk<R>(0, 0, 0);
     R th = 0;
     uint64_t id = 0;
-    if (live && staged) {
-      const PhStage& S = stg[kk & 1];
-      const unsigned int t = threadIdx.x;
-      x = S.x[t]; y = S.y[t]; z = S.z[t];
-      k = mk<R>((R)S.k[0][t], (R)S.k[1][t], (R)S.k[2][t]);
-      xi = mk<R>((R)S.xi[0][t], (R)S.xi[1][t], (R)S.xi[2][t]);
-      th = (R)S.th[t];
-      id = S.id[t];
-    } else if (live) {
+    if (live) {
       x = P.x[i]; y = P.y[i]; z = P.z[i];
       k = mk<R>(ld<R>(P.px, i), ld<R>(P.py, i), ld<R>(P.pz, i));
       xi = mk<R>(ld<R>(P.s1, i), ld<R>(P.s2, i), ld<R>(P.s3, i));
@@ -550,82 +409,34 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(StepArgs a) {
 // ======================================================================================
 template <typename R>
 __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(StepArgs a) {
-  constexpr bool kStg = sizeof(R) == 4 && QED_STAGE_LEPTON;
   __shared__ R s_rates[kSmemRateLen];
   __shared__ TileShared s_tile;
-  __shared__ __align__(128) unsigned char s_stg[kStg ? 2 * sizeof(LepStage) : 16];
-  __shared__ __align__(8) unsigned long long s_bar[2];
   DevState* st = a.st;
   const unsigned long long n0 = a.sp[0].present ? st->n_live[0] : 0ull;
   const unsigned long long n1 = a.sp[1].present ? st->n_live[1] : 0ull;
   const unsigned int t0 = (unsigned int)((n0 + kTile - 1) / kTile);
   const unsigned int ntiles = t0 + (unsigned int)((n1 + kTile - 1) / kTile);
-  LepStage* stg = reinterpret_cast<LepStage*>(s_stg);
-  // a tile is staged when it is full and its set's arrays are 16-byte aligned
-  auto staged_tile = [&](unsigned int t, unsigned long long& i0) -> bool {
-    const int sp = t < t0 ? 0 : 1;
-    i0 = (unsigned long long)(t - (sp == 0 ? 0u : t0)) * kTile;
-    return kStg && a.sp[sp].stage && i0 + kTile <= (sp == 0 ? n0 : n1);
-  };
-  if (kStg && threadIdx.x == 0) {
-    mbar_init(&s_bar[0]);
-    mbar_init(&s_bar[1]);
-    mbar_fence_init();
-  }
   const Tabs<R> tb{reinterpret_cast<const R*>(a.tables), s_rates};
   stage_rates(tb.g, s_rates);
   __syncthreads();
-  if (kStg && threadIdx.x == 0 && blockIdx.x < ntiles) {
-    unsigned long long i0;
-    if (staged_tile(blockIdx.x, i0)) issue_lep(stg[0], a.sp[blockIdx.x < t0 ? 0 : 1], i0, &s_bar[0]);
-  }
   const unsigned int epoch = st->epoch;
   const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.ff.dt;
   NcsRec<R>* evlog = reinterpret_cast<NcsRec<R>*>(a.rec[1]);
-  // kk selects the buffer; bit b of phase is the parity of buffer b's next fill, flipped
-  // each time a staged tile is taken from it (the ragged last e- tile is not staged)
-  unsigned int kk = 0, phase = 0;
-  for (unsigned int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++kk) {
+  for (unsigned int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int sp_idx = tile < t0 ? 0 : 1;
     const SpeciesArgs& L = a.sp[sp_idx];
     const unsigned long long nsp = sp_idx == 0 ? n0 : n1;
-    const unsigned long long i = (unsigned long long)(tile - (sp_idx == 0 ? 0u : t0)) * kTile + threadIdx.x;
-    // the buffer for the next tile was last read in the previous iteration, before the
-    // barriers of its tile_log
-    const unsigned int nxt = tile + gridDim.x;
-    if (kStg && threadIdx.x == 0 && nxt < ntiles) {
-      unsigned long long i0;
-      if (staged_tile(nxt, i0)) issue_lep(stg[(kk + 1) & 1], a.sp[nxt < t0 ? 0 : 1], i0, &s_bar[(kk + 1) & 1]);
-    }
-    unsigned long long i0c;
-    const bool staged = staged_tile(tile, i0c);
-    bool loaded = true;
-    if (staged) {
-      loaded = stage_wait(&s_bar[kk & 1], (phase >> (kk & 1)) & 1u, &st->status);
-      phase ^= 1u << (kk & 1);
-    }
-    const bool live = i < nsp && loaded;
+    const unsigned int i = (tile - (sp_idx == 0 ? 0u : t0)) * kTile + threadIdx.x;
+    const bool live = i < (unsigned int)nsp;
     const R q = sp_idx == 0 ? R(-1) : R(1);
     bool emit = false, range = false;
     R chi = 0;
     V3<R> av = mk<R>(0, 0, 0);
     if (live) {
-      double x, y, z;
-      V3<R> p, S;
-      uint64_t id;
-      if (staged) {
-        const LepStage& G = stg[kk & 1];
-        const unsigned int t = threadIdx.x;
-        x = G.x[t]; y = G.y[t]; z = G.z[t];
-        p = mk<R>((R)G.p[0][t], (R)G.p[1][t], (R)G.p[2][t]);
-        S = mk<R>((R)G.s[0][t], (R)G.s[1][t], (R)G.s[2][t]);
-        id = G.id[t];
-      } else {
-        x = L.x[i]; y = L.y[i]; z = L.z[i];
-        p = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
-        S = mk<R>(ld<R>(L.s1, i), ld<R>(L.s2, i), ld<R>(L.s3, i));
-        id = L.id[i];
-      }
+      double x = L.x[i], y = L.y[i], z = L.z[i];
+      V3<R> p = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
+      V3<R> S = mk<R>(ld<R>(L.s1, i), ld<R>(L.s2, i), ld<R>(L.s3, i));
+      const uint64_t id = L.id[i];
       const EB<R> f = gather<R>(a, x, y, z);
       // Boris push
       const R hq = R(0.5) * q * dt;
