@@ -168,6 +168,28 @@ def run_gpu_path(q, torch, wl, prec, steps, warmup, flush, flags, kernel_steps):
     return sim, info
 
 
+def run_diag(q, torch, sim, reps=5):
+    """End-of-run observables on the final state: photon spectrum with the Stokes parameters
+    in the (x, y) detection basis, electron spectrum with the mean spin (mixed layout reads
+    k, xi, theta, w = 32 B per photon and p, S, w = 28 B per electron)."""
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, sp, bytes_per in (("photon_spectrum", sim.ph, 32), ("electron_spectrum", sim.e, 28)):
+        spec = q.diag_spec(q.QED_DIAG_SPECTRUM, 256, 1, 1.0, 3e4)
+        buf = torch.zeros(5 * 257 + 2, dtype=torch.float64, device="cuda")
+        q.qed_diag(sim.ctx, sp.handle, spec, buf.data_ptr())
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            q.qed_diag(sim.ctx, sp.handle, spec, buf.data_ptr())
+        ev1.record()
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        n = sp.count()
+        out[name] = {"ms": ms, "particles": n, "GBs": n * bytes_per / (ms * 1e-3) / 1e9}
+    return out
+
+
 def run_e2e(q, torch, sim, prec, steps, flags):
     """Host-resident particles: every step copies the live state in and out (pinned)."""
     import ctypes as C
@@ -284,6 +306,7 @@ def main():
         sim64, f64 = run_gpu_path(q, torch, c2_workload(args.n, seed=2 + rank), q.QED_PREC_F64, args.steps,
                                   args.warmup, flush, flags, min(args.kernel_steps, args.steps))
         sim64.close()
+    diag = run_diag(q, torch, sim)
     e2e = run_e2e(q, torch, sim, q.QED_PREC_MIXED, args.e2e_steps, flags)
 
     ms, parts = info["ms"], info["particles"]
@@ -334,6 +357,7 @@ def main():
                          "sample": f"{args.cpu_sample} electrons of the same beam recipe, 20 steps after "
                                    f"{PRE_STEPS} untimed"},
         "e2e": e2e,
+        "diag": diag,
         "gpu_launches": 7 * args.steps,   # per step: photon, lepton, 2 scans, pairs, refill, NCS
         "clocks": clk.summary(),
         "counts_after": {"e": info["final_counts"][0], "pos": info["final_counts"][1],

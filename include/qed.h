@@ -247,6 +247,36 @@ qed_status qed_get_timing(qed_ctx *ctx, double ms[3], uint64_t *steps);
  * >= the count.  Errors: QED_ERR_INVALID_ARG (bad which, cap too small). */
 qed_status qed_copy_table(qed_ctx *ctx, int which, double *host, uint64_t cap, uint64_t *len, void *stream);
 
+/* ---- End-of-run observables (paper Sec. IV: post-processing of the photon polarization,
+ * Figs. of spectra, mean spin and pair yield) ------------------------------------------
+ * qed_diag histograms one particle set on the device.
+ *   kind QED_DIAG_SPECTRUM: nx bins uniform in ln(energy) over [lo_x, hi_x) (0 < lo_x <
+ *     hi_x); energy = |k| for photons, gamma = sqrt(1 + p^2) for leptons; ny must be 1.
+ *   kind QED_DIAG_DETECTOR: nx * ny cells uniform in the particle position (x, y) over
+ *     [lo_x, hi_x) x [lo_y, hi_y) (the detection plane of the paper's VB post-processing).
+ * Per bin the call accumulates {sum w, sum w o1, sum w o2, sum w o3, count}, where o is the
+ * spin vector (Sx, Sy, Sz) for leptons and, for photons, the Stokes parameters rotated by
+ * Eq. (rotation) from the photon's stored basis to the detection basis (d1, d2 = n x d1),
+ * d1 = unit(ref - (ref . n) n) with ref = spec->ref (x if ref is zero; the canonical basis
+ * vector e1 of n if ref is parallel to n).
+ * dev_out (device, caller-owned, FP64) receives 5 * (nx * ny) bin values (bin-major: bin
+ * i at [5 i .. 5 i + 4], bin index ix + nx * iy), then the same five values over every
+ * particle of the set, then sum w below and sum w above the range (x axis; for the
+ * detector, outside in either coordinate counts as "above"): 5 * (nx * ny + 1) + 2
+ * doubles.  Sums are FP64: per-block partials, then a fixed-order compensated (Neumaier)
+ * sum over blocks.  Async; no host sync unless the context's diagnostic scratch must
+ * grow.  Errors: QED_ERR_INVALID_ARG (NULL pointers, nx * ny outside [1, 1024], bad
+ * ranges, ny != 1 for a spectrum). */
+typedef enum { QED_DIAG_SPECTRUM = 0, QED_DIAG_DETECTOR = 1 } qed_diag_kind;
+typedef struct {
+  int kind;
+  int nx, ny;
+  double lo_x, hi_x, lo_y, hi_y;
+  double ref[3];
+} qed_diag_spec;
+qed_status qed_diag(qed_ctx *ctx, const qed_particles *set, const qed_diag_spec *spec, double *dev_out,
+                    void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *qed_last_error(void);
 

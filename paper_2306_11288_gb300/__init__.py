@@ -27,7 +27,8 @@ FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
 ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particles_count",
                  "particles_set_count", "particles_destroy", "qed_set_next_id", "qed_get_next_id",
                  "qed_step", "qed_step_host", "qed_step_static", "qed_read_status", "qed_copy_table",
-                 "qed_set_timing", "qed_get_timing", "qed_last_error")
+                 "qed_set_timing", "qed_get_timing", "qed_diag", "qed_last_error")
+QED_DIAG_SPECTRUM, QED_DIAG_DETECTOR = 0, 1
 
 
 class qed_soa(C.Structure):
@@ -47,6 +48,11 @@ class qed_fields(C.Structure):
 class qed_step_stats(C.Structure):
     _fields_ = [("n_ncs", C.c_uint64 * 2), ("n_nbw", C.c_uint64), ("n_range", C.c_uint64),
                 ("n_drop", C.c_uint64), ("n_steps", C.c_uint64)]
+
+
+class qed_diag_spec(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("lo_x", C.c_double), ("hi_x", C.c_double),
+                ("lo_y", C.c_double), ("hi_y", C.c_double), ("ref", C.c_double * 3)]
 
 
 class QedError(RuntimeError):
@@ -81,6 +87,7 @@ def lib():
         L.qed_copy_table.argtypes = [vp, C.c_int, C.POINTER(C.c_double), u64, C.POINTER(u64), vp]
         L.qed_set_timing.argtypes = [vp, C.c_int]
         L.qed_get_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(u64)]
+        L.qed_diag.argtypes = [vp, vp, C.POINTER(qed_diag_spec), vp, vp]
         L.qed_last_error.restype = C.c_char_p
         for name in ABI_FUNCTIONS:
             if name != "qed_last_error":
@@ -184,6 +191,31 @@ def qed_copy_table(ctx, which, stream=None) -> np.ndarray:
     _check(lib().qed_copy_table(ctx, int(which), out.ctypes.data_as(C.POINTER(C.c_double)), n.value,
                                 C.byref(n), _stream(stream)), "qed_copy_table")
     return out
+
+
+def diag_spec(kind, nx, ny=1, lo_x=1.0, hi_x=2.0, lo_y=0.0, hi_y=1.0, ref=(0.0, 0.0, 0.0)) -> qed_diag_spec:
+    sp = qed_diag_spec()
+    sp.kind, sp.nx, sp.ny = int(kind), int(nx), int(ny)
+    sp.lo_x, sp.hi_x, sp.lo_y, sp.hi_y = float(lo_x), float(hi_x), float(lo_y), float(hi_y)
+    for k in range(3):
+        sp.ref[k] = float(ref[k])
+    return sp
+
+
+def qed_diag(ctx, handle, spec: qed_diag_spec, dev_out_ptr: int, stream=None):
+    _check(lib().qed_diag(ctx, handle, C.byref(spec), C.c_void_p(dev_out_ptr), _stream(stream)), "qed_diag")
+
+
+def diag(species: "Species", spec: qed_diag_spec, stream=None) -> dict:
+    """Histogram of one device set (see qed_diag): returns bins [ny, nx, 5] (sum w, sum w o1..o3,
+    count), total [5], below, above."""
+    import torch
+    nb = spec.nx * spec.ny
+    out = torch.zeros(5 * (nb + 1) + 2, dtype=torch.float64, device="cuda")
+    qed_diag(species.ctx, species.handle, spec, out.data_ptr(), stream)
+    v = out.cpu().numpy()
+    return {"bins": v[:5 * nb].reshape(spec.ny, spec.nx, 5), "total": v[5 * nb:5 * nb + 5],
+            "below": float(v[5 * nb + 5]), "above": float(v[5 * nb + 6])}
 
 
 def qed_set_timing(ctx, enable: bool):

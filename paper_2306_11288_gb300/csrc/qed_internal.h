@@ -90,6 +90,8 @@ struct qed_ctx {
   cudaEvent_t tev[6];
   double tms[3];
   unsigned long long tsteps;
+  void* diag_buf;                     // per-block partial histograms of qed_diag
+  size_t diag_bytes;
 };
 
 struct qed_particles {

@@ -59,6 +59,9 @@ def test_host_validation_without_gpu(lib):
     h = C.c_void_p()
     soa = q.qed_soa()
     assert L.particles_create(None, 0, C.byref(soa), 0, 0, 0, None, C.byref(h)) == q.QED_ERR_NOT_INITIALIZED
+    spec = q.diag_spec(q.QED_DIAG_SPECTRUM, 8, 1, 1.0, 10.0)
+    assert L.qed_diag(None, None, C.byref(spec), None, None) == q.QED_ERR_NOT_INITIALIZED
+    assert "invalid context" in q.qed_last_error()
 
 
 def test_binding_refuses_missing_library(tmp_path, monkeypatch):
