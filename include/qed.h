@@ -277,6 +277,74 @@ typedef struct {
 qed_status qed_diag(qed_ctx *ctx, const qed_particles *set, const qed_diag_spec *spec, double *dev_out,
                     void *stream);
 
+/* ---- Batches of independent ensembles (many collisions stepped together) ---------------
+ * The paper's method applies per macroparticle; a batch steps many independent ensembles
+ * (each a set of e-, e+, photons in its own external field, with its own clock, step
+ * counter, RNG key and id counter) with one launch of each step kernel over all of them
+ * (work items = (ensemble, tile)).  Each ensemble's results are those qed_step would give
+ * it alone.  The paper has no counterpart of batching: it is an execution scheme. */
+
+/* A context that uses `parent`'s tables (built once) with its own device state: live
+ * counts, id counter, step scratch.  An ensemble's particle sets are created on such a
+ * context.  `parent` must own its tables and outlive the shared context.  Syncs nothing.
+ * Errors: QED_ERR_NOT_INITIALIZED (parent), QED_ERR_INVALID_ARG, QED_ERR_CUDA. */
+qed_status qed_ctx_share(qed_ctx *parent, void *stream, qed_ctx **out);
+
+typedef struct {
+  qed_ctx *ctx;                 /* the ensemble's context (made by qed_ctx_share) */
+  qed_particles *e, *pos, *ph;  /* its sets, created on ctx (any may be NULL) */
+  qed_fields fields;            /* its external field (copied; grid arrays must stay valid) */
+  double t0;                    /* its time at the batch's first step */
+  uint32_t step0;               /* its step number at the first step (RNG counter) */
+  uint64_t seed;                /* its RNG key */
+  qed_step_stats *dev_stats;    /* optional device statistics, accumulated */
+} qed_ensemble;
+
+/* launch shape of a batched step (see qed_batch_tune) */
+typedef struct {
+  int stream_blocks_per_sm;     /* streaming passes: 1..4 (capped by occupancy) */
+  int event_blocks_per_sm;      /* event kernels: 1..8 */
+  int smem_rates;               /* 1: 1-D rate tables staged in shared memory; 0: read via L1/L2 */
+} qed_batch_config;
+
+typedef struct qed_batch qed_batch;
+
+/* Creates a batch of n_ens (1..1024) ensembles on the context `ctx` (its tables; the
+ * ensembles' contexts must share them).  All sets must have one precision.  Every step
+ * advances each ensemble's clock by dt and its step number by one, on the device.
+ * Allocates the batch's scratch (sized from the sets' capacities) and copies the clocks to
+ * the ensembles' device state (syncs `stream`).  Errors: QED_ERR_INVALID_ARG (sizes,
+ * mixed precisions, a set not on its ensemble's context, contexts not sharing ctx's
+ * tables, flags), QED_ERR_CUDA. */
+qed_status qed_batch_create(qed_ctx *ctx, const qed_ensemble *ens, int n_ens, double dt, uint32_t flags,
+                            void *stream, qed_batch **out);
+
+/* One step of every ensemble (async, graph-capturable, no allocation): a tile-map kernel,
+ * then the kernels of qed_step with (ensemble, tile) work items, the lepton pass on the
+ * batch's side stream. */
+qed_status qed_batch_step(qed_batch *b, void *stream);
+
+/* nsteps steps by replaying one captured step as a CUDA graph (captured on first use and
+ * again after a configuration change).  Async. */
+qed_status qed_batch_run(qed_batch *b, uint32_t nsteps, void *stream);
+
+/* Reads ensemble e's clock (syncs).  Errors: QED_ERR_INVALID_ARG (e out of range). */
+qed_status qed_batch_clock(qed_batch *b, int e, double *t, uint32_t *step, void *stream);
+
+qed_status qed_batch_get_config(const qed_batch *b, qed_batch_config *cfg);
+/* Errors: QED_ERR_INVALID_ARG (values out of range). */
+qed_status qed_batch_set_config(qed_batch *b, const qed_batch_config *cfg);
+
+/* Autotuner: runs steps_per_candidate real steps of the batch under each candidate launch
+ * shape (streaming blocks per SM x event blocks per SM x rate-table placement), times
+ * them with CUDA events, and keeps the fastest.  The steps advance the simulation; the
+ * results do not depend on the launch shape.  Syncs.  *ms_per_step (optional) receives
+ * the best time.  Errors: QED_ERR_INVALID_ARG, QED_ERR_CUDA. */
+qed_status qed_batch_tune(qed_batch *b, uint32_t steps_per_candidate, void *stream, qed_batch_config *chosen,
+                          double *ms_per_step);
+
+qed_status qed_batch_destroy(qed_batch *b);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *qed_last_error(void);
 

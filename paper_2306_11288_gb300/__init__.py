@@ -27,7 +27,9 @@ FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
 ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particles_count",
                  "particles_set_count", "particles_destroy", "qed_set_next_id", "qed_get_next_id",
                  "qed_step", "qed_step_host", "qed_step_static", "qed_read_status", "qed_copy_table",
-                 "qed_set_timing", "qed_get_timing", "qed_diag", "qed_last_error")
+                 "qed_set_timing", "qed_get_timing", "qed_diag", "qed_ctx_share", "qed_batch_create",
+                 "qed_batch_step", "qed_batch_run", "qed_batch_clock", "qed_batch_get_config",
+                 "qed_batch_set_config", "qed_batch_tune", "qed_batch_destroy", "qed_last_error")
 QED_DIAG_SPECTRUM, QED_DIAG_DETECTOR = 0, 1
 
 
@@ -53,6 +55,16 @@ class qed_step_stats(C.Structure):
 class qed_diag_spec(C.Structure):
     _fields_ = [("kind", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("lo_x", C.c_double), ("hi_x", C.c_double),
                 ("lo_y", C.c_double), ("hi_y", C.c_double), ("ref", C.c_double * 3)]
+
+
+class qed_ensemble(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("e", C.c_void_p), ("pos", C.c_void_p), ("ph", C.c_void_p),
+                ("fields", qed_fields), ("t0", C.c_double), ("step0", C.c_uint32), ("seed", C.c_uint64),
+                ("dev_stats", C.c_void_p)]
+
+
+class qed_batch_config(C.Structure):
+    _fields_ = [("stream_blocks_per_sm", C.c_int), ("event_blocks_per_sm", C.c_int), ("smem_rates", C.c_int)]
 
 
 class QedError(RuntimeError):
@@ -88,6 +100,15 @@ def lib():
         L.qed_set_timing.argtypes = [vp, C.c_int]
         L.qed_get_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(u64)]
         L.qed_diag.argtypes = [vp, vp, C.POINTER(qed_diag_spec), vp, vp]
+        L.qed_ctx_share.argtypes = [vp, vp, C.POINTER(vp)]
+        L.qed_batch_create.argtypes = [vp, C.POINTER(qed_ensemble), C.c_int, d, u32, vp, C.POINTER(vp)]
+        L.qed_batch_step.argtypes = [vp, vp]
+        L.qed_batch_run.argtypes = [vp, u32, vp]
+        L.qed_batch_clock.argtypes = [vp, C.c_int, C.POINTER(d), C.POINTER(u32), vp]
+        L.qed_batch_get_config.argtypes = [vp, C.POINTER(qed_batch_config)]
+        L.qed_batch_set_config.argtypes = [vp, C.POINTER(qed_batch_config)]
+        L.qed_batch_tune.argtypes = [vp, u32, vp, C.POINTER(qed_batch_config), C.POINTER(d)]
+        L.qed_batch_destroy.argtypes = [vp]
         L.qed_last_error.restype = C.c_char_p
         for name in ABI_FUNCTIONS:
             if name != "qed_last_error":
@@ -123,6 +144,58 @@ def qed_init_tables(stream=None):
 
 def qed_destroy(ctx):
     _check(lib().qed_destroy(ctx), "qed_destroy")
+
+
+def qed_ctx_share(parent, stream=None):
+    h = C.c_void_p()
+    _check(lib().qed_ctx_share(parent, _stream(stream), C.byref(h)), "qed_ctx_share")
+    return h
+
+
+def qed_batch_create(ctx, ens, dt, flags, stream=None):
+    arr = (qed_ensemble * len(ens))(*ens)
+    h = C.c_void_p()
+    _check(lib().qed_batch_create(ctx, arr, len(ens), float(dt), int(flags), _stream(stream), C.byref(h)),
+           "qed_batch_create")
+    return h
+
+
+def qed_batch_step(b, stream=None):
+    _check(lib().qed_batch_step(b, _stream(stream)), "qed_batch_step")
+
+
+def qed_batch_run(b, nsteps, stream=None):
+    _check(lib().qed_batch_run(b, int(nsteps), _stream(stream)), "qed_batch_run")
+
+
+def qed_batch_clock(b, e, stream=None):
+    t, st = C.c_double(), C.c_uint32()
+    _check(lib().qed_batch_clock(b, int(e), C.byref(t), C.byref(st), _stream(stream)), "qed_batch_clock")
+    return float(t.value), int(st.value)
+
+
+def qed_batch_get_config(b) -> dict:
+    c = qed_batch_config()
+    _check(lib().qed_batch_get_config(b, C.byref(c)), "qed_batch_get_config")
+    return {"stream_blocks_per_sm": c.stream_blocks_per_sm, "event_blocks_per_sm": c.event_blocks_per_sm,
+            "smem_rates": c.smem_rates}
+
+
+def qed_batch_set_config(b, stream_blocks_per_sm, event_blocks_per_sm, smem_rates):
+    c = qed_batch_config(int(stream_blocks_per_sm), int(event_blocks_per_sm), int(smem_rates))
+    _check(lib().qed_batch_set_config(b, C.byref(c)), "qed_batch_set_config")
+
+
+def qed_batch_tune(b, steps_per_candidate, stream=None):
+    c, ms = qed_batch_config(), C.c_double()
+    _check(lib().qed_batch_tune(b, int(steps_per_candidate), _stream(stream), C.byref(c), C.byref(ms)),
+           "qed_batch_tune")
+    return {"stream_blocks_per_sm": c.stream_blocks_per_sm, "event_blocks_per_sm": c.event_blocks_per_sm,
+            "smem_rates": c.smem_rates}, float(ms.value)
+
+
+def qed_batch_destroy(b):
+    _check(lib().qed_batch_destroy(b), "qed_batch_destroy")
 
 
 def particles_create(ctx, species, soa: qed_soa, n, cap, prec, stream=None):
@@ -376,3 +449,50 @@ class Simulation:
             s.close()
         if self.own_ctx:
             qed_destroy(self.ctx)
+
+
+class Batch:
+    """Independent ensembles stepped together (qed_batch_*): one Simulation per workload,
+    each on a context sharing `ctx`'s tables.  All workloads must share dt."""
+
+    def __init__(self, wls: list, prec=QED_PREC_F64, flags=None, ctx=None, caps=None):
+        import torch
+        self.torch = torch
+        self.ctx = ctx if ctx is not None else qed_init_tables()
+        self.own_ctx = ctx is None
+        dts = {float(w["dt"]) for w in wls}
+        if len(dts) != 1:
+            raise ValueError("all ensembles of a batch share dt")
+        self.dt = dts.pop()
+        self.flags = (QED_F_NCS | QED_F_NBW | QED_F_VB | QED_F_SPIN) if flags is None else flags
+        caps = caps or [{}] * len(wls)
+        self.sims = [Simulation(w, prec=prec, ctx=qed_ctx_share(self.ctx), **c) for w, c in zip(wls, caps)]
+        ens = []
+        for s in self.sims:
+            ens.append(qed_ensemble(s.ctx, s.e.handle, s.pos.handle, s.ph.handle, s.fields, s.t, s.step_no, s.seed,
+                                    s.stats.data_ptr()))
+        torch.cuda.synchronize()
+        self.b = qed_batch_create(self.ctx, ens, self.dt, self.flags)
+
+    def step(self, n=1, stream=None):
+        for _ in range(n):
+            qed_batch_step(self.b, stream)
+
+    def run(self, n, stream=None):
+        qed_batch_run(self.b, n, stream)
+
+    def clocks(self):
+        return [qed_batch_clock(self.b, e) for e in range(len(self.sims))]
+
+    def close(self):
+        if self.b is not None:
+            qed_batch_destroy(self.b)
+            self.b = None
+        for s in self.sims:
+            c = s.ctx
+            s.close()
+            qed_destroy(c)
+        self.sims = []
+        if self.own_ctx:
+            qed_destroy(self.ctx)
+            self.own_ctx = False

@@ -81,10 +81,46 @@ extern "C" qed_status qed_init_tables(qed_ctx** out, void* stream) {
   return QED_OK;
 }
 
+extern "C" qed_status qed_ctx_share(qed_ctx* parent, void* stream, qed_ctx** out) {
+  if (!out) FAIL(QED_ERR_INVALID_ARG, "qed_ctx_share: out is NULL");
+  *out = nullptr;
+  if (!parent || !parent->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_ctx_share: invalid parent context");
+  if (parent->shared) FAIL(QED_ERR_INVALID_ARG, "qed_ctx_share: the parent must own its tables");
+  qed_ctx* c = (qed_ctx*)calloc(1, sizeof(qed_ctx));
+  if (!c) FAIL(QED_ERR_INVALID_ARG, "qed_ctx_share: host allocation failed");
+  c->device = parent->device;
+  c->tab64 = parent->tab64;
+  c->tab32 = parent->tab32;
+  c->shared = 1;
+  memcpy(c->nblk, parent->nblk, sizeof(c->nblk));
+  cudaError_t e = cudaMalloc(&c->st, sizeof(DevState));
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  h.epoch = 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, S(stream));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaFree(c->st);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork) cudaEventDestroy(c->fork);
+    free(c);
+    FAIL(QED_ERR_CUDA, "qed_ctx_share: %s", cudaGetErrorString(e));
+  }
+  c->alive = 1;
+  *out = c;
+  return QED_OK;
+}
+
 extern "C" qed_status qed_destroy(qed_ctx* c) {
   if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_destroy: invalid context");
   cudaDeviceSynchronize();
-  cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st);
+  if (!c->shared) {
+    cudaFree(c->tab64);
+    cudaFree(c->tab32);
+  }
+  cudaFree(c->st);
   for (int k = 0; k < 2; ++k) {
     cudaFree(c->tile_cnt[k]); cudaFree(c->tile_pre[k]); cudaFree(c->rec[k]);
   }
@@ -234,17 +270,74 @@ extern "C" qed_status qed_read_status(qed_ctx* c, uint32_t* status, int clear, v
   return QED_OK;
 }
 
-static qed_status fill_species(SpeciesArgs& a, const qed_particles* p) {
+static void fill_species(SpeciesArgs& a, const qed_particles* p) {
   memset(&a, 0, sizeof(a));
-  if (!p) return QED_OK;
+  if (!p) return;
   a.x = (double*)p->soa.x; a.y = (double*)p->soa.y; a.z = (double*)p->soa.z;
   a.px = p->soa.px; a.py = p->soa.py; a.pz = p->soa.pz;
   a.s1 = p->soa.s1; a.s2 = p->soa.s2; a.s3 = p->soa.s3;
   a.theta = p->soa.theta; a.w = p->soa.w; a.id = p->soa.id;
   a.cap = p->cap;
   a.present = p->cap > 0 ? 1 : 0;
+}
+
+namespace qedk {
+// float(t - phi0) and float(t mod 2 pi), formed in FP64 with one explicit fma so that the
+// batched kernels' clock advance on the device gives the same values
+void step_time_floats(double t, double phi0, float* t_rel, float* t_mod) {
+  *t_rel = (float)(t - phi0);
+  *t_mod = (float)std::fma(-kTwoPi, std::floor(t / kTwoPi), t);
+}
+
+void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos, const qed_particles* ph,
+                   const qed_fields* f, double t, uint64_t seed, uint32_t step, DevState* st,
+                   qed_step_stats* stats) {
+  memset(&E, 0, sizeof(E));
+  fill_species(E.sp[0], e);
+  fill_species(E.sp[1], pos);
+  fill_species(E.sp[2], ph);
+  E.f = *f;
+  E.t = t;
+  E.seed = seed;
+  E.step = step;
+  E.st = st;
+  E.user_stats = stats;
+  const double len = f->len > 0.0 ? f->len : 1.0;
+  E.inv_len = 1.0 / len;
+  E.ff.inv_len = (float)E.inv_len;
+  step_time_floats(t, f->phi0, &E.ff.t_rel, &E.ff.t_mod);
+  E.ff.a0 = (float)f->a0;
+  E.ff.w0 = (float)f->w0;
+  E.ff.zf = (float)f->zf;
+  E.ff.zr = (float)(0.5 * f->w0 * f->w0);
+  E.ff.inv_zr = f->w0 > 0.0 ? (float)(2.0 / (f->w0 * f->w0)) : 0.0f;
+  E.ff.inv_w02 = f->w0 > 0.0 ? (float)(1.0 / (f->w0 * f->w0)) : 0.0f;
+}
+}  // namespace qedk
+
+namespace qedk {
+qed_status check_fields(const qed_fields* f, const char* who) {
+  switch (f->kind) {
+    case QED_FIELD_NONE:
+    case QED_FIELD_UNIFORM:
+      break;
+    case QED_FIELD_PLANE:
+      if (!(f->len > 0.0)) FAIL(QED_ERR_INVALID_ARG, "%s: envelope length must be positive", who);
+      break;
+    case QED_FIELD_GAUSS:
+      if (!(f->len > 0.0) || !(f->w0 > 0.0)) FAIL(QED_ERR_INVALID_ARG, "%s: len and w0 must be positive", who);
+      break;
+    case QED_FIELD_GRID2D:
+      if (!f->gEx || !f->gEy || !f->gEz || !f->gBx || !f->gBy || !f->gBz)
+        FAIL(QED_ERR_INVALID_ARG, "%s: grid arrays must be non-NULL", who);
+      if (f->nx < 1 || f->ny < 1 || !(f->dx > 0) || !(f->dy > 0)) FAIL(QED_ERR_INVALID_ARG, "%s: bad grid geometry", who);
+      break;
+    default:
+      FAIL(QED_ERR_INVALID_ARG, "%s: unknown field kind %d", who, f->kind);
+  }
   return QED_OK;
 }
+}  // namespace qedk
 
 static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
                                 const qed_fields* f, double dt, uint32_t flags, qed_precision* prec) {
@@ -264,25 +357,9 @@ static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos
   }
   *prec = have < 0 ? QED_PREC_F64 : (qed_precision)have;
   if ((flags & QED_F_NBW) && (!e || !pos)) FAIL(QED_ERR_INVALID_ARG, "qed_step: NBW needs e- and e+ sets");
-  switch (f->kind) {
-    case QED_FIELD_NONE:
-    case QED_FIELD_UNIFORM:
-      break;
-    case QED_FIELD_PLANE:
-      if (!(f->len > 0.0)) FAIL(QED_ERR_INVALID_ARG, "qed_step: envelope length must be positive");
-      break;
-    case QED_FIELD_GAUSS:
-      if (!(f->len > 0.0) || !(f->w0 > 0.0)) FAIL(QED_ERR_INVALID_ARG, "qed_step: len and w0 must be positive");
-      break;
-    case QED_FIELD_GRID2D:
-      if (!f->gEx || !f->gEy || !f->gEz || !f->gBx || !f->gBy || !f->gBz)
-        FAIL(QED_ERR_INVALID_ARG, "qed_step: grid arrays must be non-NULL");
-      if (f->nx < 1 || f->ny < 1 || !(f->dx > 0) || !(f->dy > 0))
-        FAIL(QED_ERR_INVALID_ARG, "qed_step: bad grid geometry");
-      break;
-    default:
-      FAIL(QED_ERR_INVALID_ARG, "qed_step: unknown field kind %d", f->kind);
-  }
+  qed_status r_;
+  r_ = check_fields(f, "qed_step");
+  if (r_ != QED_OK) return r_;
   const unsigned long long tp = ph ? tiles_of(ph->cap) : 0;
   const unsigned long long tl = (e ? tiles_of(e->cap) : 0) + (pos ? tiles_of(pos->cap) : 0);
   if (tp > c->tile_cap[0] || tl > c->tile_cap[1] || !c->rec[0] || !c->rec[1])
@@ -298,30 +375,12 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
   if (r != QED_OK) return r;
   StepArgs a;
   memset(&a, 0, sizeof(a));
-  fill_species(a.sp[0], e);
-  fill_species(a.sp[1], pos);
-  fill_species(a.sp[2], ph);
-  a.f = *f;
-  a.t = t;
+  fill_ensemble(a.e0, e, pos, ph, f, t, seed, step, c->st, dev_stats);
   a.dt = dt;
-  a.seed = seed;
-  a.step = step;
+  a.fdt = (float)dt;
   a.flags = flags;
   a.tables = prec == QED_PREC_F64 ? (const void*)c->tab64 : (const void*)c->tab32;
   a.st = c->st;
-  const double len = f->len > 0.0 ? f->len : 1.0;
-  a.inv_len = 1.0 / len;
-  const double two_pi = 6.283185307179586477;
-  a.ff.dt = (float)dt;
-  a.ff.inv_len = (float)a.inv_len;
-  a.ff.t_rel = (float)(t - f->phi0);
-  a.ff.t_mod = (float)(t - two_pi * std::floor(t / two_pi));
-  a.ff.a0 = (float)f->a0;
-  a.ff.w0 = (float)f->w0;
-  a.ff.zf = (float)f->zf;
-  a.ff.zr = (float)(0.5 * f->w0 * f->w0);
-  a.ff.inv_zr = f->w0 > 0.0 ? (float)(2.0 / (f->w0 * f->w0)) : 0.0f;
-  a.ff.inv_w02 = f->w0 > 0.0 ? (float)(1.0 / (f->w0 * f->w0)) : 0.0f;
   for (int k = 0; k < 2; ++k) {
     a.tile_cnt[k] = c->tile_cnt[k];
     a.tile_pre[k] = c->tile_pre[k];
@@ -329,7 +388,6 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
     a.rec_cap[k] = c->rec_cap[k];
   }
   a.holes = c->holes;
-  a.user_stats = dev_stats;
   const int pi = prec == QED_PREC_F64 ? 0 : 1;
   // per-kernel timing runs the passes one after the other, so that each duration is the
   // kernel's own (no overlap of the lepton pass with the photon chain)

@@ -12,6 +12,7 @@ namespace qedk {
 
 // ---- constants (CODATA 2018; lambda = 1 um) -----------------------------------
 constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 2.0 * kPi;
 constexpr double kAlpha = 7.2973525693e-3;
 constexpr double kXiL = 2.42631023867e-6;     // hbar omega0 / (m c^2)
 constexpr double kAe = 1.15965218128e-3;      // g/2 - 1
@@ -253,6 +254,10 @@ struct DevState {
   unsigned int done;                 // finished-block counter of the last kernel
   unsigned int epoch;                // stamp of this step's log entries
   unsigned int status;               // QED_STATUS_* bits (sticky)
+  // batched steps: the ensemble's clock, advanced on the device by every step
+  double t;
+  unsigned int step;
+  float t_rel, t_mod;                // float(t - phi0), float(t mod 2 pi)
 };
 
 }  // namespace qedk

@@ -30,22 +30,45 @@ struct FloatConsts {
   float dt, inv_len, t_rel, t_mod, a0, w0, zf, zr, inv_zr, inv_w02;
 };
 
-struct StepArgs {
+// the arguments of one ensemble (a set of e-, e+, photons in one field)
+struct EnsArgs {
   SpeciesArgs sp[3];                 // e-, e+, photon
   qed_fields f;
-  double t, dt;
+  double t;                          // time (single-ensemble launches; batched: DevState::t)
   double inv_len;                    // 1 / envelope length
-  FloatConsts ff;
+  FloatConsts ff;                    // float constants; t_rel, t_mod only for single launches
   unsigned long long seed;
-  unsigned int step, flags;
+  unsigned int step;                 // step number (single launches; batched: DevState::step)
+  DevState* st;                      // the ensemble's counts, id counter, per-step totals
+  qed_step_stats* user_stats;
+};
+
+// Batched steps: where each ensemble's tiles and events start.  Rebuilt on the device at
+// the start of every batched step from the live counts (k_bmap) and by the scans.
+constexpr int kMaxEns = 1024;
+struct BatchMap {
+  unsigned int ph_tile0[kMaxEns + 1];     // first photon tile of each ensemble; [n] = total
+  unsigned int lep_tile0[kMaxEns + 1];    // first lepton tile (its e- tiles, then its e+ tiles)
+  unsigned int lep_e_tiles[kMaxEns];      // e- tiles of each ensemble
+  unsigned int ev_base[2][kMaxEns + 1];   // first rank of each ensemble's decays / emissions
+};
+
+// per-launch parameters of the step kernels (one struct, passed by value)
+struct StepArgs {
+  EnsArgs e0;                        // single-ensemble launches
+  const EnsArgs* ens;                // batched launches: n_ens entries in device memory
+  BatchMap* map;
+  int n_ens;
+  double dt;
+  float fdt;
+  unsigned int flags;
   const void* tables;                // double* or float* depending on precision
-  DevState* st;
+  DevState* st;                      // log cursors, epoch, finished-block counter, status
   unsigned int* tile_cnt[2];         // events per tile: photon tiles, lepton tiles
   unsigned int* tile_pre[2];         // their exclusive prefixes
   void* rec[2];                      // event logs: NBW decays, NCS emissions
   unsigned long long rec_cap[2];
   unsigned int* holes;               // ranked slots of decayed photons
-  qed_step_stats* user_stats;
 };
 
 // side stream and events of one step.  side == nullptr runs everything on the caller's
@@ -57,9 +80,16 @@ struct StreamSet {
   cudaEvent_t* tev;
 };
 
-// launches one step; prec selects the instantiation; nblk = grid sizes (photon, lepton,
-// events)
+// launches one step of one ensemble (a.e0); prec selects the instantiation; nblk = grid
+// sizes (photon, lepton, events)
 qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, const StreamSet& ss);
+// fills one ensemble's arguments (sets may be NULL; t, step: the ensemble's clock)
+void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos, const qed_particles* ph,
+                   const qed_fields* f, double t, uint64_t seed, uint32_t step, DevState* st,
+                   qed_step_stats* stats);
+void step_time_floats(double t, double phi0, float* t_rel, float* t_mod);
+// host validation of a field descriptor (message prefixed by who)
+qed_status check_fields(const qed_fields* f, const char* who);
 // occupancy-derived persistent grid sizes
 qed_status step_grid_sizes(qed_precision prec, int* nblk);
 size_t nbw_rec_bytes(qed_precision p);
@@ -71,6 +101,7 @@ constexpr int kTile = 256;   // particles per tile (= threads per block, one par
 
 struct qed_ctx {
   int device;
+  int shared;                         // tables belong to another context (qed_ctx_share)
   double* tab64;
   float* tab32;
   qedk::DevState* st;

@@ -66,16 +66,6 @@ static qed_status scratch_address(void** out) {
   return QED_OK;
 }
 
-static void species_args(SpeciesArgs& a, const qed_particles* p) {
-  memset(&a, 0, sizeof(a));
-  if (!p) return;
-  a.x = (double*)p->soa.x; a.y = (double*)p->soa.y; a.z = (double*)p->soa.z;
-  a.px = p->soa.px; a.py = p->soa.py; a.pz = p->soa.pz;
-  a.s1 = p->soa.s1; a.s2 = p->soa.s2; a.s3 = p->soa.s3;
-  a.theta = p->soa.theta; a.w = p->soa.w; a.id = p->soa.id;
-  a.cap = p->cap;
-  a.present = p->cap > 0 ? 1 : 0;
-}
 
 }  // namespace qedk
 
@@ -151,30 +141,12 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
   }
   StepArgs a;
   memset(&a, 0, sizeof(a));
-  species_args(a.sp[0], e);
-  species_args(a.sp[1], pos);
-  species_args(a.sp[2], ph);
-  a.f = *f;
-  a.t = t;
+  fill_ensemble(a.e0, e, pos, ph, f, t, seed, step, c->st, dev_stats);
   a.dt = dt;
-  a.seed = seed;
-  a.step = step;
+  a.fdt = (float)dt;
   a.flags = flags;
   a.tables = pr == QED_PREC_F64 ? (const void*)c->tab64 : (const void*)c->tab32;
   a.st = c->st;
-  const double len = f->len > 0.0 ? f->len : 1.0;
-  a.inv_len = 1.0 / len;
-  const double two_pi = 6.283185307179586477;
-  a.ff.dt = (float)dt;
-  a.ff.inv_len = (float)a.inv_len;
-  a.ff.t_rel = (float)(t - f->phi0);
-  a.ff.t_mod = (float)(t - two_pi * std::floor(t / two_pi));
-  a.ff.a0 = (float)f->a0;
-  a.ff.w0 = (float)f->w0;
-  a.ff.zf = (float)f->zf;
-  a.ff.zr = (float)(0.5 * f->w0 * f->w0);
-  a.ff.inv_zr = f->w0 > 0.0 ? (float)(2.0 / (f->w0 * f->w0)) : 0.0f;
-  a.ff.inv_w02 = f->w0 > 0.0 ? (float)(1.0 / (f->w0 * f->w0)) : 0.0f;
   a.tile_cnt[0] = reinterpret_cast<unsigned int*>(b + kSoCntPh);
   a.tile_pre[0] = reinterpret_cast<unsigned int*>(b + kSoPrePh);
   a.tile_cnt[1] = reinterpret_cast<unsigned int*>(b + kSoCntLep);
@@ -184,7 +156,6 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
   a.rec[1] = b + kSoLogNcs;
   a.rec_cap[0] = kStRecNbw;
   a.rec_cap[1] = kStRecNcs;
-  a.user_stats = dev_stats;
   const int pi = pr == QED_PREC_F64 ? 0 : 1;
   const StreamSet ss{c->side, c->fork, c->join, nullptr};
   return launch_step(a, pr, c->nblk[pi], s, ss);

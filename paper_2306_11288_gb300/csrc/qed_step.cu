@@ -1,947 +1,11 @@
-// qed_step.cu -- the per-step kernels of the spin/polarization-resolved SF-QED hot path
-// (Wan et al., arXiv:2306.11288, Secs. II-IV) for sm_103a.
-//
-// One step = seven launches.  Caller's stream: k_photon, k_scan(photon tiles), k_nbw_ev,
-// k_fill, then (after joining the side stream) k_scan(lepton tiles), k_ncs_ev; the context's
-// side stream runs k_lepton concurrently with the photon chain.  The event kernels are
-// programmatic dependents of the kernel before them.
-//   k_photon   : streaming pass over photons -- gather, Stokes frame rotation (Eq. rotation),
-//                VB phase (Eq. rotation2), NBW decision (Sec. III D); photons are updated in
-//                place and every decay is logged (tile, rank inside the tile) in an event log.
-//   k_lepton   : streaming pass over e- then e+ -- gather, Boris (Eqs. boris1-6), T-BMT
-//                (Eqs. bmt-boris1-4), x update, chi_e, NCS decision; the no-emission spin
-//                update and collapse is done here; emissions are logged.
-//   k_scan     : exclusive scan of the per-tile event counts (one block): the rank of an
-//                event is the prefix of its tile plus its rank inside the tile, which orders
-//                events by particle index exactly as a sequential pass would.
-//   k_nbw_ev   : one thread per logged decay: pair energy, spins, birth of e- and e+.
-//   k_fill     : decayed photon slots below the new count are refilled from the tail.
-//   k_ncs_ev   : one thread per logged emission: photon energy, recoil, spin collapse,
-//                photon Stokes, photon birth; its last block closes the step (counts, ids).
-// The streaming passes carry no cross-block waits; the rare events run at full warp width.
-//
-// GB300's FP64 pipe (and every FP32<->FP64 conversion, which runs on it) is ~70x slower
-// than FP32.  The mixed path therefore touches it only for the three position additions;
-// double<->float conversions of positions are done with integer bit operations.
-#include "qed_common.cuh"
-#include "qed_internal.h"
+// qed_step.cu -- one step of one ensemble: launch sequence of the kernels of
+// qed_kernels.cuh (single-ensemble instantiations) and the persistent grid sizes.
+#include "qed_kernels.cuh"
 
 namespace qedk {
 
-// ---- double <-> float without the FP64 pipe -------------------------------------------
-// double -> float by truncating the mantissa (error below one float ulp); |x| < 2^-126
-// flushes to zero.  Positions never approach the float overflow threshold.
-__device__ __forceinline__ float d2f_bits(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
-  const int e = (int)((hi >> 20) & 0x7FFu) - (1023 - 127);
-  const unsigned int f = (hi & 0x80000000u) | ((unsigned int)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  return __uint_as_float(e > 0 ? f : (hi & 0x80000000u));
-}
-// float -> double, exact for normal floats (zero and subnormal floats give signed zero)
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned int b = __float_as_uint(f);
-  const unsigned int e = (b >> 23) & 0xFFu;
-  const unsigned int hi = (b & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((b & 0x7FFFFFu) >> 3);
-  return __hiloint2double((int)(e ? hi : (b & 0x80000000u)), (int)(e ? (b << 29) : 0u));
-}
-
-// ---- external fields (paper Sec. II D) ---------------------------------------------
-template <typename R>
-struct EB { V3<R> E, B; };
-
-template <typename R>
-__device__ __forceinline__ R tsc_gather(const float* g, int nx, int ny, double X, double Y) {
-  const double fx = floor(X + 0.5), fy = floor(Y + 0.5);
-  const int ig = (int)fx, jg = (int)fy;
-  const R dx = (R)(X - fx), dy = (R)(Y - fy);
-  const R wx[3] = {R(0.5) * (R(0.5) - dx) * (R(0.5) - dx), R(0.75) - dx * dx, R(0.5) * (R(0.5) + dx) * (R(0.5) + dx)};
-  const R wy[3] = {R(0.5) * (R(0.5) - dy) * (R(0.5) - dy), R(0.75) - dy * dy, R(0.5) * (R(0.5) + dy) * (R(0.5) + dy)};
-  R acc = R(0);
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const int j = jg - 1 + b;
-    if (j < 0 || j >= ny) continue;
-    R row = R(0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int i = ig - 1 + c;
-      if (i < 0 || i >= nx) continue;
-      row += wx[c] * (R)__ldg(g + (size_t)j * nx + i);
-    }
-    acc += wy[b] * row;
-  }
-  return acc;
-}
-
-// FP64 path: the field formulas in double.  Mixed path: the phase is formed in float from
-// host-reduced time offsets (t - phi0 and t mod 2 pi) plus float(z).
-template <typename R>
-__device__ __forceinline__ EB<R> gather(const StepArgs& a, double x, double y, double z) {
-  const qed_fields& f = a.f;
-  EB<R> r;
-  r.E = mk<R>(0, 0, 0);
-  r.B = mk<R>(0, 0, 0);
-  if (f.kind == QED_FIELD_UNIFORM) {
-    r.E = mk<R>((R)f.E[0], (R)f.E[1], (R)f.E[2]);
-    r.B = mk<R>((R)f.B[0], (R)f.B[1], (R)f.B[2]);
-  } else if (f.kind == QED_FIELD_PLANE || f.kind == QED_FIELD_GAUSS) {
-    R s, ph, zl = R(0), xr = R(0), yr = R(0);
-    if (sizeof(R) == 8) {
-      const double phi = a.t + z;
-      s = (R)((phi - f.phi0) * a.inv_len);
-      ph = (R)phi;
-      zl = (R)(f.zf - z);
-    } else {
-      const float zf = d2f_bits(z);
-      s = (a.ff.t_rel + zf) * a.ff.inv_len;
-      ph = a.ff.t_mod + zf;
-      zl = a.ff.zf - zf;
-    }
-    if (s < R(0) || s > R(1)) return r;
-    R sn, cs;
-    f_sincos(R(kPi) * s, &sn, &cs);
-    R g = (sizeof(R) == 8 ? (R)f.a0 : (R)a.ff.a0) * sn * sn;
-    if (f.kind == QED_FIELD_GAUSS) {
-      if (sizeof(R) == 8) {
-        const R r2 = (R)(x * x + y * y);
-        const R zr_ = (R)(0.5 * f.w0 * f.w0);
-        const R w0 = (R)f.w0;
-        const R q = zl / zr_;
-        const R w2 = w0 * w0 * (R(1) + q * q);
-        g = g * (w0 / sqrt(w2)) * m_exp(-r2 / w2);
-        ph = ph - R(0.5) * r2 * zl / (zl * zl + zr_ * zr_) + m_atan(q);
-      } else {
-        // division-free form: with q = zeta/zR, w0/w = (1+q^2)^{-1/2}
-        xr = d2f_bits(x);
-        yr = d2f_bits(y);
-        const R r2 = xr * xr + yr * yr;
-        const R q = zl * (R)a.ff.inv_zr;
-        const R rs = f_rsqrt(R(1) + q * q);
-        const R inv = rs * rs;
-        g = g * rs * f_exp(-r2 * (R)a.ff.inv_w02 * inv);
-        ph = ph - R(0.5) * r2 * q * (R)a.ff.inv_zr * inv + f_atan(q);
-      }
-    }
-    R sp, cp;
-    f_sincos(ph, &sp, &cp);
-    r.E.x = g * cp;
-    r.E.y = f.circular ? g * sp : R(0);
-    r.B.x = r.E.y;
-    r.B.y = -r.E.x;
-  } else if (f.kind == QED_FIELD_GRID2D) {
-    const double X = (x - f.x0) / f.dx, Y = (y - f.y0) / f.dy;
-    r.E.x = tsc_gather<R>(f.gEx, f.nx, f.ny, X - 0.5, Y);
-    r.E.y = tsc_gather<R>(f.gEy, f.nx, f.ny, X, Y - 0.5);
-    r.E.z = tsc_gather<R>(f.gEz, f.nx, f.ny, X, Y);
-    r.B.x = tsc_gather<R>(f.gBx, f.nx, f.ny, X, Y - 0.5);
-    r.B.y = tsc_gather<R>(f.gBy, f.nx, f.ny, X - 0.5, Y);
-    r.B.z = tsc_gather<R>(f.gBz, f.nx, f.ny, X - 0.5, Y - 0.5);
-  }
-  return r;
-}
-
-// x + d with d in the path's precision (mixed: exact float->double by bit operations)
-__device__ __forceinline__ double add_pos(double x, double d) { return x + d; }
-__device__ __forceinline__ double add_pos(double x, float d) { return x + f2d_bits(d); }
-
-// canonical transverse frame of n: e1 = unit(y x n) (unit(n x x) near +-y), e2 = n x e1
-template <typename R>
-__device__ __forceinline__ void frame(V3<R> n, V3<R>& e1, V3<R>& e2) {
-  R a = n.z, b = R(0), c = -n.x;
-  R m2 = a * a + c * c;
-  if (m2 < R(1e-20)) { a = R(0); b = n.z; c = -n.y; m2 = b * b + c * c; }
-  const R inv = f_rsqrt(m2);
-  e1 = mk<R>(a * inv, b * inv, c * inv);
-  e2 = cross(n, e1);
-}
-
-// ---- uniforms in the path's precision ------------------------------------------------
-// FP64: the exact 53-bit uniforms.  Mixed: the same numbers rounded to float (within one
-// float ulp), built from the Philox words with 32-bit conversions only.
-template <typename R>
-struct URand { R u0, u1; };
-
-template <typename R>
-__device__ __forceinline__ URand<R> urand(uint64_t seed, uint64_t id, uint32_t step, uint32_t ctr) {
-  URand<R> r;
-  if (sizeof(R) == 8) {
-    const Uni2 u = uniforms(seed, id, step, ctr);
-    r.u0 = (R)u.u0;
-    r.u1 = (R)u.u1;
-  } else {
-    const U4 o = philox10((uint32_t)id, (uint32_t)(id >> 32), step, ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
-    r.u0 = (R)(__uint2float_rn(o.a >> 5) * 0x1p-27f + __uint2float_rn(o.b >> 6) * 0x1p-53f);
-    r.u1 = (R)(__uint2float_rn(o.c >> 5) * 0x1p-27f + __uint2float_rn(o.d >> 6) * 0x1p-53f);
-  }
-  return r;
-}
-
-// ---- table access --------------------------------------------------------------------
-template <typename R>
-struct Tabs {
-  const R* g;     // full table block in global memory
-  const R* s;     // copy of the 1-D rate tables (shared memory in the streaming kernels)
-  __device__ __forceinline__ void ncs_rates(R chi, R& A, R& B) const {
-    const R X = (f_log(chi) - R(kRLo)) * R((kNR - 1) / (kRHi - kRLo));
-    A = chi * lagrange4(s, kNR, X);
-    B = chi * lagrange4(s + kNR, kNR, X);
-  }
-  __device__ __forceinline__ R ncs_inv(int comp, R chi, R t) const {
-    const R X = (m_log(chi) - R(kRLo)) * R((kNCX - 1) / (kRHi - kRLo));
-    const R ht = R((kCTHi - kCTLo) / (kNCT - 1));
-    const size_t o = (size_t)comp * kNCX * kNCT;
-    return table2d(g + kOffCY + o, g + kOffCD + o, kNCX, kNCT, X, (t - R(kCTLo)) / ht, ht);
-  }
-  __device__ __forceinline__ void nbw_rates(R chig, R& T0, R& T3) const {
-    const R X = (f_log(chig) - R(kBLo)) * R((kNBX - 1) / (kBHi - kBLo));
-    const R damp = f_exp(R(-8.0 / 3.0) * f_rcp(chig));
-    T0 = damp * lagrange4(s + (kOffT0 - kOffRA), kNBX, X);
-    T3 = damp * lagrange4(s + (kOffT3 - kOffRA), kNBX, X);
-  }
-  __device__ __forceinline__ R nbw_inv(int comp, R chig, R t) const {
-    const R X = (m_log(chig) - R(kBLo)) * R((kNBX - 1) / (kBHi - kBLo));
-    const R ht = R((kBTHi - kBTLo) / (kNBT - 1));
-    const size_t o = (size_t)comp * kNBX * kNBT;
-    return table2d(g + kOffBY + o, g + kOffBD + o, kNBX, kNBT, X, (t - R(kBTLo)) / ht, ht);
-  }
-  __device__ __forceinline__ void vb_m(R chig, R& mp, R& mq) const {
-    if (chig < R(kVbMin)) { mp = R(4); mq = R(7); return; }
-    const R X = (f_log(chig) - R(kVLo)) * R((kNV - 1) / (kVHi - kVLo));
-    mp = lagrange4(s + (kOffMP - kOffRA), kNV, X);
-    mq = lagrange4(s + (kOffMQ - kOffRA), kNV, X);
-  }
-  __device__ __forceinline__ void k(R x, R& k13, R& k23, R& ik) const { kfun(g, x, k13, k23, ik); }
-};
-
-template <typename R>
-__device__ __forceinline__ void stage_rates(const R* g, R* s) {
-  for (int i = threadIdx.x; i < (int)kSmemRateLen; i += blockDim.x) s[i] = g[kOffRA + i];
-}
-
-template <typename T>
-__device__ __forceinline__ T ld(const void* p, unsigned long long i) { return reinterpret_cast<const T*>(p)[i]; }
-template <typename T>
-__device__ __forceinline__ void stv(void* p, unsigned long long i, T v) { reinterpret_cast<T*>(p)[i] = v; }
-
-__device__ __forceinline__ void count_event(unsigned long long* ctr, bool flag) {
-  const unsigned int b = __ballot_sync(0xffffffffu, flag);
-  if ((threadIdx.x & 31) == 0 && b) atomicAdd(ctr, (unsigned long long)__popc(b));
-}
-
-// ---- event logs ------------------------------------------------------------------------
-template <typename R>
-struct NbwRec {
-  unsigned long long i;      // photon slot
-  unsigned int tile, r_in;   // tile and rank inside the tile
-  unsigned int stamp, pad;
-  double x, y, z;            // x^n (the photon itself has moved on in its slot)
-  R chig, rmix, p1x, p1y, p1z;
-};
-template <typename R>
-struct NcsRec {
-  unsigned long long i;      // lepton slot
-  unsigned int tile, r_in, stamp, species;
-  R chi, ax, ay, az;         // chi_e and the unit acceleration direction
-};
-
 size_t nbw_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NbwRec<double>) : sizeof(NbwRec<float>); }
 size_t ncs_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NcsRec<double>) : sizeof(NcsRec<float>); }
-
-// In-tile ranks of flagged threads and one reservation in the event log per tile.
-// Returns the thread's slot in the log, or ~0 when the tile's events were not logged
-// (log full: QED_STATUS_CAPACITY).  tile_cnt[tile] receives the logged count.
-struct TileShared {
-  unsigned int wc[kTile / 32];
-  unsigned long long base;
-  int ok;
-};
-
-__device__ __forceinline__ unsigned long long tile_log(bool flag, unsigned int tile, unsigned int* tile_cnt,
-                                                       unsigned long long* cursor, unsigned long long cap,
-                                                       unsigned int* status, TileShared& sh, unsigned int* r_in) {
-  // most tiles carry no event: one barrier settles them
-  if (!__syncthreads_or(flag)) {
-    if (threadIdx.x == 0) tile_cnt[tile] = 0u;
-    *r_in = 0;
-    return ~0ull;
-  }
-  const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned int ballot = __ballot_sync(0xffffffffu, flag);
-  if (lane == 0) sh.wc[warp] = __popc(ballot);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int run = 0;
-    for (int w = 0; w < kTile / 32; ++w) {
-      const unsigned int c = sh.wc[w];
-      sh.wc[w] = run;
-      run += c;
-    }
-    const unsigned long long base = atomicAdd(cursor, (unsigned long long)run);
-    const int ok = base + run <= cap;
-    if (!ok) atomicOr(status, QED_STATUS_CAPACITY);
-    sh.base = base;
-    sh.ok = ok;
-    tile_cnt[tile] = ok ? run : 0u;
-  }
-  __syncthreads();
-  const unsigned int r = sh.wc[warp] + __popc(ballot & ((1u << lane) - 1u));
-  *r_in = r;
-  const unsigned long long slot = (flag && sh.ok) ? sh.base + r : ~0ull;
-  __syncthreads();   // sh is reused by the next tile
-  return slot;
-}
-
-template <typename R> struct Occ { static constexpr int v = sizeof(R) == 4 ? 4 : 2; };
-
-// ---- programmatic dependent launch ------------------------------------------------------
-// The event kernels are launched as programmatic dependents of the kernel before them on
-// the stream: they may be scheduled while it drains and wait here for its completion (and
-// the visibility of its writes) before touching any data.  Without the launch attribute
-// both instructions return at once.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// ======================================================================================
-// photon streaming pass
-// ======================================================================================
-template <typename R>
-__global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(StepArgs a) {
-  pdl_trigger();
-  __shared__ R s_rates[kSmemRateLen];
-  __shared__ TileShared s_tile;
-  DevState* st = a.st;
-  const SpeciesArgs& P = a.sp[2];
-  const unsigned long long n = P.present ? st->n_live[2] : 0ull;
-  const unsigned int ntiles = (unsigned int)((n + kTile - 1) / kTile);
-  const Tabs<R> tb{reinterpret_cast<const R*>(a.tables), s_rates};
-  stage_rates(tb.g, s_rates);
-  __syncthreads();
-  const unsigned int epoch = st->epoch;
-  const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.ff.dt;
-  NbwRec<R>* evlog = reinterpret_cast<NbwRec<R>*>(a.rec[0]);
-  for (unsigned int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const unsigned int i = tile * kTile + threadIdx.x;   // capacity <= 2^32 - 256: no wrap
-    const bool live = i < (unsigned int)n;
-    double x = 0, y = 0, z = 0;
-    V3<R> k = mk<R>(1, 0, 0), xi = mk<R>(0, 0, 0);
-    R th = 0;
-    uint64_t id = 0;
-    if (live) {
-      x = P.x[i]; y = P.y[i]; z = P.z[i];
-      k = mk<R>(ld<R>(P.px, i), ld<R>(P.py, i), ld<R>(P.pz, i));
-      xi = mk<R>(ld<R>(P.s1, i), ld<R>(P.s2, i), ld<R>(P.s3, i));
-      th = ld<R>(P.theta, i);
-      id = P.id[i];
-    }
-    bool decay = false, range = false;
-    const R om2 = dot(k, k);
-    const R inv_om = f_rsqrt(om2);
-    const R om = om2 * inv_om;
-    const V3<R> nn = inv_om * k;
-    V3<R> P1 = mk<R>(0, 0, 0);
-    R chig = 0, rmix = 0;
-    if (live && (a.flags & (QED_F_VB | QED_F_NBW))) {
-      const EB<R> f = gather<R>(a, x, y, z);
-      const R ne = dot(nn, f.E);
-      const V3<R> Er = f.E - ne * nn + cross(nn, f.B);
-      const R er2 = dot(Er, Er);
-      if (er2 > R(0)) {
-        const R inv_er = f_rsqrt(er2);
-        const R er = er2 * inv_er;
-        chig = R(kXiL) * om * er;
-        P1 = inv_er * Er;
-        V3<R> e1, e2;
-        frame(nn, e1, e2);
-        const R thn = f_atan2(dot(P1, e2), dot(P1, e1));
-        R s2, c2;
-        f_sincos(R(2) * (thn - th), &s2, &c2);
-        const R x1 = xi.x * c2 - xi.z * s2, x3 = xi.x * s2 + xi.z * c2;
-        xi.x = x1; xi.z = x3;
-        th = thn;
-        if (a.flags & QED_F_VB) {
-          R mp, mq;
-          tb.vb_m(chig > R(kVbMax) ? R(kVbMax) : chig, mp, mq);
-          const R dphi = (mp - mq) * R(kAlpha / (90.0 * kPi) * kXiL) * om * er * er * dt;
-          R sd, cd;
-          if (dphi < R(1e-2) && dphi > R(-1e-2)) {   // Taylor to 5th/6th order: error below 2e-15
-            const R d2 = dphi * dphi;
-            sd = dphi * (R(1) - d2 * (R(1.0 / 6.0) - d2 * R(1.0 / 120.0)));
-            cd = R(1) - d2 * (R(0.5) - d2 * (R(1.0 / 24.0) - d2 * R(1.0 / 720.0)));
-          } else {
-            f_sincos(dphi, &sd, &cd);
-          }
-          const R y1 = cd * xi.x - sd * xi.y, y2 = sd * xi.x + cd * xi.y;
-          xi.x = y1; xi.y = y2;
-        }
-        if ((a.flags & QED_F_NBW) && om >= R(2) && chig >= R(kChigMin)) {
-          if (chig > R(kChigMax)) { chig = R(kChigMax); range = true; }
-          R T0, T3;
-          tb.nbw_rates(chig, T0, T3);
-          const R Pd = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) * inv_om * (T0 - xi.z * T3) * dt;
-          const URand<R> u = urand<R>(a.seed, id, a.step, 3u);
-          decay = u.u0 < Pd;
-          rmix = u.u1;
-        }
-      }
-    }
-    if (live) {
-      stv<R>(P.s1, i, xi.x); stv<R>(P.s2, i, xi.y); stv<R>(P.s3, i, xi.z);
-      stv<R>(P.theta, i, th);
-      P.x[i] = add_pos(x, dt * nn.x); P.y[i] = add_pos(y, dt * nn.y); P.z[i] = add_pos(z, dt * nn.z);
-    }
-    count_event(&st->ev[3], range);
-    unsigned int r_in;
-    const unsigned long long slot = tile_log(decay, tile, a.tile_cnt[0], &st->cursor[0], a.rec_cap[0], &st->status,
-                                             s_tile, &r_in);
-    if (slot != ~0ull) {
-      NbwRec<R> rec;
-      rec.i = i; rec.tile = tile; rec.r_in = r_in; rec.stamp = epoch; rec.pad = 0;
-      rec.x = x; rec.y = y; rec.z = z;
-      rec.chig = chig; rec.rmix = rmix; rec.p1x = P1.x; rec.p1y = P1.y; rec.p1z = P1.z;
-      evlog[slot] = rec;
-    }
-  }
-}
-
-// ======================================================================================
-// lepton streaming pass
-// ======================================================================================
-template <typename R>
-__global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(StepArgs a) {
-  __shared__ R s_rates[kSmemRateLen];
-  __shared__ TileShared s_tile;
-  DevState* st = a.st;
-  const unsigned long long n0 = a.sp[0].present ? st->n_live[0] : 0ull;
-  const unsigned long long n1 = a.sp[1].present ? st->n_live[1] : 0ull;
-  const unsigned int t0 = (unsigned int)((n0 + kTile - 1) / kTile);
-  const unsigned int ntiles = t0 + (unsigned int)((n1 + kTile - 1) / kTile);
-  const Tabs<R> tb{reinterpret_cast<const R*>(a.tables), s_rates};
-  stage_rates(tb.g, s_rates);
-  __syncthreads();
-  const unsigned int epoch = st->epoch;
-  const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.ff.dt;
-  NcsRec<R>* evlog = reinterpret_cast<NcsRec<R>*>(a.rec[1]);
-  for (unsigned int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int sp_idx = tile < t0 ? 0 : 1;
-    const SpeciesArgs& L = a.sp[sp_idx];
-    const unsigned long long nsp = sp_idx == 0 ? n0 : n1;
-    const unsigned int i = (tile - (sp_idx == 0 ? 0u : t0)) * kTile + threadIdx.x;
-    const bool live = i < (unsigned int)nsp;
-    const R q = sp_idx == 0 ? R(-1) : R(1);
-    bool emit = false, range = false;
-    R chi = 0;
-    V3<R> av = mk<R>(0, 0, 0);
-    if (live) {
-      double x = L.x[i], y = L.y[i], z = L.z[i];
-      V3<R> p = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
-      V3<R> S = mk<R>(ld<R>(L.s1, i), ld<R>(L.s2, i), ld<R>(L.s3, i));
-      const uint64_t id = L.id[i];
-      const EB<R> f = gather<R>(a, x, y, z);
-      // Boris push
-      const R hq = R(0.5) * q * dt;
-      const V3<R> pm = p + hq * f.E;
-      const V3<R> tau = (hq * f_rsqrt(R(1) + dot(pm, pm))) * f.B;
-      const V3<R> pp = pm + cross(pm, tau);
-      const V3<R> sig = (R(2) * f_rcp(R(1) + dot(tau, tau))) * tau;
-      const V3<R> pn = pm + cross(pp, sig) + hq * f.E;
-      // T-BMT with beta, gamma of the mean of p^{n-1/2} and p^{n+1/2}
-      if (a.flags & QED_F_SPIN) {
-        const V3<R> pa = R(0.5) * (p + pn);
-        const R ga2 = R(1) + dot(pa, pa);
-        const R inv_ga = f_rsqrt(ga2);
-        const R ga = ga2 * inv_ga;
-        const V3<R> be = inv_ga * pa;
-        const R inv_gp1 = f_rcp(ga + R(1));
-        const R gg = ga * inv_gp1;
-        const V3<R> Om = (-R(kAe) * gg * dot(be, f.B)) * be + (R(kAe) + inv_ga) * f.B +
-                         (-(R(kAe) + inv_gp1)) * cross(be, f.E);
-        const V3<R> tv = hq * Om;
-        const V3<R> ov = (R(2) * f_rcp(R(1) + dot(tv, tv))) * tv;
-        const V3<R> S1 = S + cross(S, tv);
-        S = S + cross(S1, ov);
-      }
-      const R g12 = R(1) + dot(pn, pn);
-      const R inv_g1 = f_rsqrt(g12);
-      const R g1 = g12 * inv_g1;
-      if (sizeof(R) == 8) {
-        x += a.dt * (double)(pn.x / g1); y += a.dt * (double)(pn.y / g1); z += a.dt * (double)(pn.z / g1);
-      } else {
-        const R c = dt * inv_g1;
-        x = add_pos(x, c * pn.x); y = add_pos(y, c * pn.y); z = add_pos(z, c * pn.z);
-      }
-      if (a.flags & QED_F_NCS) {
-        const R pm2 = dot(pn, pn);
-        const R inv_pm = pm2 > R(0) ? f_rsqrt(pm2) : R(0);
-        const V3<R> nn = inv_pm * pn;
-        const R nE = dot(nn, f.E);
-        V3<R> v = g1 * (f.E - nE * nn) + cross(pn, f.B);
-        R vm2 = dot(v, v);
-        if (sizeof(R) == 4) {
-          // FP64 island: gamma E_perp and p x B cancel (co-propagation)
-          const V3<R> a1 = g1 * (f.E - nE * nn), a2 = cross(pn, f.B);
-          if (vm2 < R(1e-4) * (dot(a1, a1) + dot(a2, a2))) {
-            const double px = pn.x, py = pn.y, pz = pn.z;
-            const double G1 = sqrt(1.0 + px * px + py * py + pz * pz), pmd = sqrt(px * px + py * py + pz * pz);
-            const double nx = px / pmd, ny = py / pmd, nz = pz / pmd;
-            const double Ex = f.E.x, Ey = f.E.y, Ez = f.E.z, Bx = f.B.x, By = f.B.y, Bz = f.B.z;
-            const double ne = nx * Ex + ny * Ey + nz * Ez;
-            const double vx = G1 * (Ex - ne * nx) + (py * Bz - pz * By);
-            const double vy = G1 * (Ey - ne * ny) + (pz * Bx - px * Bz);
-            const double vz = G1 * (Ez - ne * nz) + (px * By - py * Bx);
-            v = mk<R>((R)vx, (R)vy, (R)vz);
-            vm2 = (R)(vx * vx + vy * vy + vz * vz);
-          }
-        }
-        const R c2 = vm2 + nE * nE;
-        chi = c2 > R(0) ? R(kXiL) * c2 * f_rsqrt(c2) : R(0);
-        if (chi >= R(kChiMin) && vm2 > R(0) && inv_pm > R(0)) {
-          if (chi > R(kChiMax)) { chi = R(kChiMax); range = true; }
-          av = (q * f_rsqrt(vm2)) * v;    // unit acceleration direction
-          const V3<R> zeta = cross(nn, av);
-          R A, B;
-          tb.ncs_rates(chi, A, B);
-          const R s = dot(S, zeta);
-          const R pref = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) * inv_g1;
-          const R Wa = pref * A, Wb = pref * B;
-          const R Pe = (Wa - s * Wb) * dt;
-          const URand<R> u = urand<R>(a.seed, id, a.step, 0u);
-          if (u.u0 < Pe) {
-            emit = true;   // completed by k_ncs_ev
-          } else {
-            // no emission: posterior mean spin, then collapse with P(+) = (1+|S|)/2
-            const R den = f_rcp(R(1) - Pe);
-            const V3<R> Sb = (den * (R(1) - Wa * dt)) * S + (den * Wb * dt) * zeta;
-            const R m2 = dot(Sb, Sb);
-            const R inv_m = f_rsqrt(m2);
-            const R sg = (u.u1 < R(0.5) * (R(1) + m2 * inv_m)) ? R(1) : R(-1);
-            S = (sg * inv_m) * Sb;
-          }
-        }
-      }
-      L.x[i] = x; L.y[i] = y; L.z[i] = z;
-      stv<R>(L.px, i, pn.x); stv<R>(L.py, i, pn.y); stv<R>(L.pz, i, pn.z);
-      stv<R>(L.s1, i, S.x); stv<R>(L.s2, i, S.y); stv<R>(L.s3, i, S.z);
-    }
-    count_event(&st->ev[sp_idx], emit);
-    count_event(&st->ev[3], range);
-    unsigned int r_in;
-    const unsigned long long slot = tile_log(emit, tile, a.tile_cnt[1], &st->cursor[1], a.rec_cap[1], &st->status,
-                                             s_tile, &r_in);
-    if (slot != ~0ull) {
-      NcsRec<R> rec;
-      rec.i = i; rec.tile = tile; rec.r_in = r_in; rec.stamp = epoch; rec.species = (unsigned int)sp_idx;
-      rec.chi = chi; rec.ax = av.x; rec.ay = av.y; rec.az = av.z;
-      evlog[slot] = rec;
-    }
-  }
-}
-
-// ======================================================================================
-// exclusive scan of the tile counts (which = 0: photon tiles, 1: lepton tiles), one block;
-// 32 consecutive counts per thread (vector loads) so that a pass covers 32768 tiles
-// ======================================================================================
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 32;
-
-__global__ void __launch_bounds__(kScanThreads) k_scan(StepArgs a, int which) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ unsigned int s_w[kScanThreads / 32];
-  __shared__ unsigned long long s_run;
-  DevState* st = a.st;
-  unsigned long long ntiles, nph = 0;
-  if (which == 0) {
-    nph = a.sp[2].present ? st->n_live[2] : 0ull;
-    ntiles = (nph + kTile - 1) / kTile;
-  } else {
-    const unsigned long long n0 = a.sp[0].present ? st->n_live[0] : 0ull;
-    const unsigned long long n1 = a.sp[1].present ? st->n_live[1] : 0ull;
-    ntiles = (n0 + kTile - 1) / kTile + (n1 + kTile - 1) / kTile;
-  }
-  const unsigned int* cnt = a.tile_cnt[which];
-  unsigned int* pre = a.tile_pre[which];
-  const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_run = 0;
-  __syncthreads();
-  for (unsigned long long b = 0; b < ntiles; b += (unsigned long long)kScanThreads * kScanItems) {
-    const unsigned long long first = b + (unsigned long long)threadIdx.x * kScanItems;
-    const bool full = first + kScanItems <= ntiles;   // first is a multiple of 32: 16-byte aligned
-    unsigned int v[kScanItems];
-    if (full) {
-      const uint4* c4 = reinterpret_cast<const uint4*>(cnt + first);
-#pragma unroll
-      for (int j = 0; j < kScanItems / 4; ++j) {
-        const uint4 q = c4[j];
-        v[4 * j] = q.x; v[4 * j + 1] = q.y; v[4 * j + 2] = q.z; v[4 * j + 3] = q.w;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < kScanItems; ++j) v[j] = (first + j < ntiles) ? cnt[first + j] : 0u;
-    }
-    unsigned int tsum = 0;
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) tsum += v[j];
-    unsigned int c = tsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned int t = __shfl_up_sync(0xffffffffu, c, o);
-      if (lane >= (unsigned)o) c += t;
-    }
-    if (lane == 31) s_w[warp] = c;
-    __syncthreads();
-    if (warp == 0) {
-      unsigned int w = s_w[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int t = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= (unsigned)o) w += t;
-      }
-      s_w[lane] = w;   // inclusive over warps
-    }
-    __syncthreads();
-    const unsigned long long run = s_run;
-    unsigned int acc = (unsigned int)run + (warp ? s_w[warp - 1] : 0u) + c - tsum;
-#pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-      const unsigned int e = acc;
-      acc += v[j];
-      v[j] = e;
-    }
-    if (full) {
-      uint4* p4 = reinterpret_cast<uint4*>(pre + first);
-#pragma unroll
-      for (int j = 0; j < kScanItems / 4; ++j) p4[j] = make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < kScanItems; ++j)
-        if (first + j < ntiles) pre[first + j] = v[j];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s_run = run + s_w[kScanThreads / 32 - 1];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    if (which == 0) {
-      st->n_nbw = s_run;
-      st->n_surv = nph - s_run;
-    } else {
-      st->n_ncs_tot = s_run;
-    }
-  }
-}
-
-// ======================================================================================
-// NBW events: pair energy split (mixture over xi3' = +-1), SQAs D and D', joint spin
-// sampling from Eqs. G0-G3, birth of the pair at the photon's x^n (Sec. III D)
-// ======================================================================================
-template <typename R>
-__global__ void __launch_bounds__(kTile) k_nbw_ev(StepArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  DevState* st = a.st;
-  const Tabs<R> tb{reinterpret_cast<const R*>(a.tables), reinterpret_cast<const R*>(a.tables) + kOffRA};
-  const unsigned long long nrec = min(st->cursor[0], a.rec_cap[0]);
-  const unsigned int epoch = st->epoch;
-  const NbwRec<R>* evlog = reinterpret_cast<const NbwRec<R>*>(a.rec[0]);
-  const SpeciesArgs& P = a.sp[2];
-  const unsigned long long ne0 = st->n_live[0], np0 = st->n_live[1];
-  const unsigned long long id0 = st->next_id;
-  for (unsigned long long kk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; kk < nrec;
-       kk += (unsigned long long)gridDim.x * blockDim.x) {
-    const NbwRec<R> rec = evlog[kk];
-    if (rec.stamp != epoch || a.tile_cnt[0][rec.tile] == 0) continue;
-    const unsigned long long rank = (unsigned long long)a.tile_pre[0][rec.tile] + rec.r_in;
-    const unsigned long long i = rec.i;
-    a.holes[rank] = (unsigned int)i;
-    const V3<R> k = mk<R>(ld<R>(P.px, i), ld<R>(P.py, i), ld<R>(P.pz, i));
-    const V3<R> xi = mk<R>(ld<R>(P.s1, i), ld<R>(P.s2, i), ld<R>(P.s3, i));
-    const R wgt = ld<R>(P.w, i);
-    const uint64_t id = P.id[i];
-    const R om = norm(k);
-    const V3<R> nn = (R(1) / om) * k;
-    const V3<R> P1 = mk<R>(rec.p1x, rec.p1y, rec.p1z);
-    const V3<R> P2 = cross(nn, P1);
-    const R chig = rec.chig;
-    R T0, T3;
-    tb.nbw_rates(chig, T0, T3);
-    const Uni2 u2 = uniforms(a.seed, id, a.step, 4u);
-    const R w0 = R(0.5) * (R(1) + xi.z) * (T0 - T3);
-    const int comp = (rec.rmix * (T0 - xi.z * T3) < w0) ? 0 : 1;
-    const double l = u2.u0;
-    const bool upper = l >= 0.5;
-    const double lam = upper ? 2.0 * (1.0 - l) : 2.0 * l;
-    R tt = lam > 0.0 ? m_log((R)lam) : R(kBTLo);
-    tt = tt < R(kBTLo) ? R(kBTLo) : tt;
-    const R dh = m_exp(tb.nbw_inv(comp, chig, tt));
-    R ep = upper ? (R(1) - dh) * om : dh * om;
-    ep = ep < R(1) ? R(1) : ep;
-    ep = ep > om - R(1) ? om - R(1) : ep;
-    const R em = om - ep;
-    const R delta = ep / om;
-    R k13, k23, ik;
-    tb.k(R(2) / (R(3) * chig * delta * (R(1) - delta)), k13, k23, ik);
-    const R epm = ep * em;
-    const R dif2 = (ep * ep - em * em) / epm, sum2 = (ep * ep + em * em) / epm, sq = (ep - em) * (ep - em) / epm;
-    const R oe = om / ep, om_ = om / em;
-    // SQAs: S+ along D (Eq. BWposAxis2), S- along D' (Eq. BWeleAxis1); a+ = P1', b+ = P2'
-    const V3<R> D = (-(oe - xi.z * om_) * k13) * P2 + (-xi.x * om_ * k13) * P1 + (xi.y * (dif2 * k23 + oe * ik)) * nn;
-    const V3<R> Dp = ((om_ - xi.z * oe) * k13) * P2 + (xi.x * oe * k13) * P1 + (-xi.y * (dif2 * k23 - om_ * ik)) * nn;
-    const R dn = norm(D), dpn = norm(Dp);
-    const V3<R> Sp = dn > R(0) ? (R(1) / dn) * D : P2;
-    const V3<R> Sm = dpn > R(0) ? (R(1) / dpn) * Dp : P2;
-    R pk[4];
-    R tot = R(0);
-    const R g2 = om * om / (R(2) * epm);
-#pragma unroll
-    for (int o = 0; o < 4; ++o) {
-      const R sp = (o < 2) ? R(1) : R(-1), sm = (o % 2 == 0) ? R(1) : R(-1);
-      const V3<R> A1 = sp * Sp, A2 = sm * Sm;
-      const R SpSm = dot(A1, A2);
-      const R Spb = dot(A1, P2), Smb = dot(A2, P2), Spa = dot(A1, P1), Sma = dot(A2, P1);
-      const R Spv = dot(A1, nn), Smv = dot(A2, nn);
-      const V3<R> X = cross(A2, A1);
-      const R G0 = ik + sum2 * k23 + (ik - R(2) * k23) * SpSm + k13 * (-oe * Spb + om_ * Smb) +
-                   (sum2 * ik - sq * k23) * Spv * Smv;
-      const R G1 = k13 * (-om_ * Spa + oe * Sma) + R(0.5) * dif2 * k23 * dot(X, nn) - g2 * ik * (Spa * Smb + Sma * Spb);
-      const R G2 = g2 * k13 * dot(X, P1) + R(0.5) * dif2 * k13 * (Smv * Spb + Spv * Smb) + (om_ * ik - dif2 * k23) * Smv +
-                   (oe * ik + dif2 * k23) * Spv;
-      const R G3 = -k23 + R(0.5) * sum2 * k23 * SpSm - k13 * (oe * Smb - om_ * Spb) + g2 * ik * (Spb * Smb - Spa * Sma) -
-                   R(0.5) * sq * k23 * Spv * Smv;
-      R v = G0 + xi.x * G1 + xi.y * G2 + xi.z * G3;
-      v = v < R(0) ? R(0) : v;
-      pk[o] = v;
-      tot += v;
-    }
-    const R rr = (R)u2.u1 * tot;
-    int o = 3;
-    R acc = R(0);
-#pragma unroll
-    for (int qq = 0; qq < 4; ++qq) {
-      acc += pk[qq];
-      if (o == 3 && qq < 3 && rr < acc) o = qq;
-    }
-    const R sp = (o < 2) ? R(1) : R(-1), sm = (o % 2 == 0) ? R(1) : R(-1);
-    const R pp = sqrt(ep * ep - R(1)), pm = sqrt(em * em - R(1));
-    const unsigned long long base[2] = {ne0, np0};
-    const R pmag[2] = {pm, pp};
-    const V3<R> spin[2] = {sm * Sm, sp * Sp};
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const SpeciesArgs& L = a.sp[s];
-      const unsigned long long j = base[s] + rank;
-      if (!L.present || j >= L.cap) {
-        atomicOr(&st->status, QED_STATUS_CAPACITY);
-        atomicAdd(&st->ev[4], 1ull);
-        continue;
-      }
-      L.x[j] = rec.x; L.y[j] = rec.y; L.z[j] = rec.z;
-      stv<R>(L.px, j, pmag[s] * nn.x); stv<R>(L.py, j, pmag[s] * nn.y); stv<R>(L.pz, j, pmag[s] * nn.z);
-      stv<R>(L.s1, j, spin[s].x); stv<R>(L.s2, j, spin[s].y); stv<R>(L.s3, j, spin[s].z);
-      stv<R>(L.w, j, wgt);
-      L.id[j] = id0 + 2ull * rank + (unsigned long long)s;
-    }
-  }
-}
-
-// ======================================================================================
-// removal of decayed photons: the k-th decayed slot below the new count M = N - D receives
-// the k-th surviving photon at or above M (both in index order)
-// ======================================================================================
-__device__ __forceinline__ unsigned long long upper_bound_u32(const unsigned int* h, unsigned long long n,
-                                                              unsigned long long v) {
-  unsigned long long lo = 0, hi = n;
-  while (lo < hi) {
-    const unsigned long long m = (lo + hi) >> 1;
-    if ((unsigned long long)h[m] <= v) lo = m + 1; else hi = m;
-  }
-  return lo;
-}
-
-template <typename R>
-__global__ void __launch_bounds__(kTile) k_fill(StepArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  DevState* st = a.st;
-  const SpeciesArgs& P = a.sp[2];
-  if (!P.present) return;
-  const unsigned long long D = st->n_nbw, N = st->n_live[2], M = N - D;
-  const unsigned int* h = a.holes;
-  // H holes lie below M (they are refilled); the D - H holes at or above M are skipped
-  // over: with g(p) = h[H + p] - M - p survivors ahead of hole H + p (non-decreasing), the
-  // kk-th survivor at or above M is M + kk + #{p : g(p) <= kk}
-  const unsigned long long H = M == 0 ? 0 : upper_bound_u32(h, D, M - 1);
-  for (unsigned long long kk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; kk < H;
-       kk += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long dst = h[kk];
-    unsigned long long lo = 0, hi = D - H;
-    while (lo < hi) {
-      const unsigned long long m = (lo + hi) >> 1;
-      if ((unsigned long long)h[H + m] - M - m <= kk) lo = m + 1; else hi = m;
-    }
-    const unsigned long long src = M + kk + lo;
-    P.x[dst] = P.x[src]; P.y[dst] = P.y[src]; P.z[dst] = P.z[src];
-    stv<R>(P.px, dst, ld<R>(P.px, src)); stv<R>(P.py, dst, ld<R>(P.py, src)); stv<R>(P.pz, dst, ld<R>(P.pz, src));
-    stv<R>(P.s1, dst, ld<R>(P.s1, src)); stv<R>(P.s2, dst, ld<R>(P.s2, src)); stv<R>(P.s3, dst, ld<R>(P.s3, src));
-    stv<R>(P.theta, dst, ld<R>(P.theta, src));
-    stv<R>(P.w, dst, ld<R>(P.w, src));
-    P.id[dst] = P.id[src];
-  }
-}
-
-// ======================================================================================
-// NCS events: photon energy (two-component mixture of Eq. Wspin2 at s = S.zeta), recoil,
-// spin collapse along the SQA of Eq. F0, photon pure state from Eqs. F1-F3, photon birth
-// at x^{n+1}; the last block to finish closes the step.
-// ======================================================================================
-template <typename R>
-__global__ void __launch_bounds__(kTile) k_ncs_ev(StepArgs a) {
-  pdl_wait();
-  DevState* st = a.st;
-  const Tabs<R> tb{reinterpret_cast<const R*>(a.tables), reinterpret_cast<const R*>(a.tables) + kOffRA};
-  const unsigned long long nrec = min(st->cursor[1], a.rec_cap[1]);
-  const unsigned int epoch = st->epoch;
-  const NcsRec<R>* evlog = reinterpret_cast<const NcsRec<R>*>(a.rec[1]);
-  const SpeciesArgs& G = a.sp[2];
-  const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
-  const unsigned long long nsurv = st->n_surv;
-  const unsigned long long id0 = st->next_id + 2ull * st->n_nbw;
-  for (unsigned long long kk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; kk < nrec;
-       kk += (unsigned long long)gridDim.x * blockDim.x) {
-    const NcsRec<R> rec = evlog[kk];
-    if (rec.stamp != epoch || a.tile_cnt[1][rec.tile] == 0) continue;
-    const unsigned long long rank = (unsigned long long)a.tile_pre[1][rec.tile] + rec.r_in;
-    const SpeciesArgs& L = a.sp[rec.species];
-    const unsigned long long i = rec.i;
-    const V3<R> pn = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
-    const V3<R> S = mk<R>(ld<R>(L.s1, i), ld<R>(L.s2, i), ld<R>(L.s3, i));
-    const uint64_t id = L.id[i];
-    const R chi = rec.chi;
-    const V3<R> av = mk<R>(rec.ax, rec.ay, rec.az);
-    const R g1 = sqrt(R(1) + dot(pn, pn));
-    R pmag = norm(pn);
-    pmag = pmag > R(0) ? pmag : R(1e-30);
-    const V3<R> nn = (R(1) / pmag) * pn;
-    const V3<R> zeta = cross(nn, av);
-    R A, B;
-    tb.ncs_rates(chi, A, B);
-    const R s = dot(S, zeta);
-    const Uni2 um = uniforms(a.seed, id, a.step, 1u);
-    const Uni2 us = uniforms(a.seed, id, a.step, 2u);
-    const R wplus = R(0.5) * (R(1) + s) * (A - B);
-    const int comp = ((R)um.u0 * (A - s * B) < wplus) ? 0 : 1;
-    const double l = um.u1;
-    R tt;
-    if (sizeof(R) == 8) tt = (R)(log(l) - log1p(-l));
-    else tt = m_log((R)l) - m_log((R)(1.0 - l));
-    tt = tt < R(kCTLo) ? R(kCTLo) : (tt > R(kCTHi) ? R(kCTHi) : tt);
-    const R uu = m_exp(tb.ncs_inv(comp, chi, tt));
-    const R omr = R(1) / (R(1) + uu), rr = uu * omr;
-    const R om = rr * g1;
-    R k13, k23, ik;
-    tb.k(R(2) * uu / (R(3) * chi), k13, k23, ik);
-    const R sin_ = dot(S, nn);
-    const R c0 = R(4) * ((R(2) + R(2) * uu + uu * uu) * k23 - (R(1) + uu) * ik - uu * s * k13);
-    const V3<R> gv = (R(-4) * (R(1) + uu) * (ik - R(2) * k23)) * S + (R(-4) * uu * (R(1) + uu) * k13) * zeta +
-                     (R(-4) * uu * uu * (ik - k23) * sin_) * nn;
-    const R gmg = norm(gv);
-    V3<R> Sf = S;
-    if (gmg > R(0)) {
-      const R sg = ((R)us.u0 < R(0.5) * (R(1) + gmg / c0)) ? R(1) : R(-1);
-      Sf = (sg / gmg) * gv;
-    }
-    const R F0 = c0 + dot(gv, Sf);
-    const R Sif = dot(S, Sf), Siz = s, Sfz = dot(Sf, zeta), Sin = sin_, Sfn = dot(Sf, nn);
-    const R Sia = dot(S, av), Sfa = dot(Sf, av);
-    const V3<R> fxs = cross(Sf, S);
-    const R u2 = uu * uu;
-    const R F1 = R(-2) * u2 * ik * (Sia * Sfz + Sfa * Siz) + R(4) * uu * (Sia * (R(1) + uu) + Sfa) * k13 +
-                 R(2) * uu * (R(2) + uu) * dot(nn, fxs) * k23;
-    const R F2 = -(R(2) * u2 * (Sin * Sfz + Sfn * Siz) + R(2) * uu * (R(2) + uu) * dot(av, fxs)) * k13 -
-                 R(4) * uu * (Sin + Sfn * (R(1) + uu)) * ik + R(4) * uu * (R(2) + uu) * (Sin + Sfn) * k23;
-    const R F3 = R(4) * (R(1) + uu + (R(1) + uu + R(0.5) * u2) * Sif - R(0.5) * u2 * Sin * Sfn) * k23 +
-                 R(2) * u2 * (Siz * Sfz - Sia * Sfa) * ik - R(4) * uu * ((R(1) + uu) * Siz + Sfz) * k13;
-    const R fm = sqrt(F1 * F1 + F2 * F2 + F3 * F3);
-    V3<R> xiph = mk<R>(0, 0, 0);
-    if (fm > R(0)) {
-      const R sg = ((R)us.u1 < R(0.5) * (R(1) + fm / F0)) ? R(1) : R(-1);
-      xiph = mk<R>(sg * F1 / fm, sg * F2 / fm, sg * F3 / fm);
-    }
-    stv<R>(L.s1, i, Sf.x); stv<R>(L.s2, i, Sf.y); stv<R>(L.s3, i, Sf.z);
-    if (!(a.flags & QED_F_NO_RECOIL)) {
-      // recoil p_f = p_i - omega n, |p_f| = (1-r) gamma - (gamma - |p|)
-      const R pf = omr * g1 - R(1) / (g1 + pmag);
-      stv<R>(L.px, i, pf * nn.x); stv<R>(L.py, i, pf * nn.y); stv<R>(L.pz, i, pf * nn.z);
-    }
-    if (births) {
-      const unsigned long long j = nsurv + rank;
-      if (!G.present || j >= G.cap) {
-        atomicOr(&st->status, QED_STATUS_CAPACITY);
-        atomicAdd(&st->ev[4], 1ull);
-      } else {
-        V3<R> e1, e2;
-        frame(nn, e1, e2);
-        G.x[j] = L.x[i]; G.y[j] = L.y[i]; G.z[j] = L.z[i];
-        stv<R>(G.px, j, om * nn.x); stv<R>(G.py, j, om * nn.y); stv<R>(G.pz, j, om * nn.z);
-        stv<R>(G.s1, j, xiph.x); stv<R>(G.s2, j, xiph.y); stv<R>(G.s3, j, xiph.z);
-        stv<R>(G.theta, j, m_atan2(dot(av, e2), dot(av, e1)));
-        stv<R>(G.w, j, ld<R>(L.w, i));
-        G.id[j] = id0 + rank;
-      }
-    }
-  }
-  // the last block to finish closes the step: counts, id counter, statistics, resets
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int d = atomicAdd(&st->done, 1u);
-    if (d == gridDim.x - 1) {
-      __threadfence();
-      volatile DevState* v = st;
-      const unsigned long long nbw = v->n_nbw, ncs = births ? v->n_ncs_tot : 0ull, surv = v->n_surv;
-      for (int s = 0; s < 2; ++s) {
-        if (!a.sp[s].present) continue;
-        const unsigned long long nn = v->n_live[s] + nbw;
-        v->n_live[s] = nn > a.sp[s].cap ? a.sp[s].cap : nn;
-      }
-      if (G.present) {
-        const unsigned long long nn = surv + ncs;
-        v->n_live[2] = nn > G.cap ? G.cap : nn;
-      }
-      v->next_id = v->next_id + 2ull * nbw + ncs;
-      if (a.user_stats) {
-        a.user_stats->n_ncs[0] += v->ev[0];
-        a.user_stats->n_ncs[1] += v->ev[1];
-        a.user_stats->n_nbw += nbw;
-        a.user_stats->n_range += v->ev[3];
-        a.user_stats->n_drop += v->ev[4];
-        a.user_stats->n_steps += 1;
-      }
-      if (v->ev[3]) v->status |= QED_STATUS_TABLE_RANGE;
-      for (int k = 0; k < 6; ++k) v->ev[k] = 0;
-      v->n_nbw = 0; v->n_surv = 0; v->n_ncs_tot = 0;
-      v->cursor[0] = 0; v->cursor[1] = 0;
-      v->done = 0;
-      v->epoch = v->epoch + 1;
-      __threadfence();
-    }
-  }
-}
-
-template <typename... P, typename... A>
-static void launch_k(void (*k)(P...), int grid, int block, cudaStream_t s, bool pdl, A... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned int)grid);
-  cfg.blockDim = dim3((unsigned int)block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = pdl ? at : nullptr;
-  cfg.numAttrs = pdl ? 1u : 0u;
-  cudaLaunchKernelEx(&cfg, k, args...);
-}
 
 // Photon chain on the caller's stream; the lepton pass on the context's side stream
 // (forked after all earlier work on the caller's stream, joined before the lepton scan):
@@ -956,24 +20,24 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     cudaEventRecord(ss.fork, s);
     cudaStreamWaitEvent(ss.side, ss.fork, 0);
     if (ss.tev) cudaEventRecord(ss.tev[4], ss.side);
-    k_lepton<R><<<nb[1], kTile, 0, ss.side>>>(a);
+    k_lepton<R, false, true><<<nb[1], kTile, 0, ss.side>>>(a);
     if (ss.tev) cudaEventRecord(ss.tev[5], ss.side);
     cudaEventRecord(ss.join, ss.side);
   }
-  k_photon<R><<<nb[0], kTile, 0, s>>>(a);
+  k_photon<R, false, true><<<nb[0], kTile, 0, s>>>(a);
   if (ss.tev) cudaEventRecord(ss.tev[1], s);
-  launch_k(k_scan, 1, kScanThreads, s, pdl, a, 0);
-  launch_k(k_nbw_ev<R>, nb[2], kTile, s, pdl, a);
-  launch_k(k_fill<R>, nb[2], kTile, s, pdl, a);
+  launch_k(k_scan<false>, 1, kScanThreads, s, pdl, a, 0);
+  launch_k(k_nbw_ev<R, false>, nb[2], kTile, s, pdl, a);
+  launch_k(k_fill<R, false>, nb[2], kTile, s, pdl, a);
   if (fork) {
     cudaStreamWaitEvent(s, ss.join, 0);
   } else {
     if (ss.tev) cudaEventRecord(ss.tev[4], s);
-    k_lepton<R><<<nb[1], kTile, 0, s>>>(a);
+    k_lepton<R, false, true><<<nb[1], kTile, 0, s>>>(a);
     if (ss.tev) cudaEventRecord(ss.tev[5], s);
   }
-  k_scan<<<1, kScanThreads, 0, s>>>(a, 1);
-  launch_k(k_ncs_ev<R>, nb[2], kTile, s, pdl, a);
+  k_scan<false><<<1, kScanThreads, 0, s>>>(a, 1);
+  launch_k(k_ncs_ev<R, false>, nb[2], kTile, s, pdl, a);
   if (ss.tev) cudaEventRecord(ss.tev[3], s);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -993,11 +57,11 @@ qed_status step_grid_sizes(qed_precision prec, int* nblk) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaError_t e;
   if (prec == QED_PREC_F64) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_photon<double>, kTile, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_lepton<double>, kTile, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_photon<double, false, true>, kTile, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_lepton<double, false, true>, kTile, 0);
   } else {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_photon<float>, kTile, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_lepton<float>, kTile, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_photon<float, false, true>, kTile, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_lepton<float, false, true>, kTile, 0);
   }
   if (e != cudaSuccess || b0 < 1 || b1 < 1) {
     set_error("occupancy query failed: %s", cudaGetErrorString(e));
