@@ -168,6 +168,77 @@ def run_gpu_path(q, torch, wl, prec, steps, warmup, flush, flags, kernel_steps):
     return sim, info
 
 
+C4_PRE = 150   # the ensembles start 150 steps before the beam centres reach the focus
+
+
+def c4_workload(seed=4):
+    """64 independent collisions of uneven size (10^U(3,6) particles each), a0, gamma0,
+    polarisation and spin states varying, every fourth a gamma beam, each moved like the
+    1e6-electron workload so that its collision falls in the timed window."""
+    import workloads
+    wls = workloads.c4(n_ens=64, seed=seed)
+    for wl in wls:
+        for sp in ("e", "ph"):
+            if len(wl[sp]["id"]):
+                wl[sp]["z"] = wl[sp]["z"] + T_SHIFT
+        wl["t0"] = T_SHIFT
+        wl["step0"] = int(round(T_SHIFT / wl["dt"]))
+    return wls
+
+
+def run_c4(q, torch, steps, warmup, seq_steps=5, tune_steps=2):
+    """Batched ensembles: CUDA-graph replay of one batched step after the autotuner picked
+    the launch shape; then the same ensembles stepped one by one with qed_step."""
+    wls = c4_workload()
+    caps = []
+    for wl in wls:
+        n = len(wl["e"]["id"]) + len(wl["ph"]["id"])
+        caps.append({"cap_e": n + n // 2 + 4096, "cap_p": n // 2 + 4096, "cap_ph": 24 * n + 4096})
+    flags = q.QED_F_NCS | q.QED_F_NBW | q.QED_F_VB | q.QED_F_SPIN
+    b = q.Batch(wls, prec=q.QED_PREC_MIXED, flags=flags, caps=caps)
+    n0 = sum(len(w["e"]["id"]) + len(w["ph"]["id"]) for w in wls)
+    b.run(C4_PRE)
+    cfg, tune_ms = q.qed_batch_tune(b.b, tune_steps)
+    b.run(warmup)
+    torch.cuda.synchronize()
+
+    def processed():
+        return int(torch.stack([s.stats for s in b.sims]).sum(0)[6].item())
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0 = processed()
+    ev0.record()
+    b.run(steps)
+    ev1.record()
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    p1 = processed()
+    status = q.qed_read_status(b.ctx)
+    # the same ensembles, one qed_step per ensemble per step
+    for k, (t, st) in enumerate(b.clocks()):
+        b.sims[k].t, b.sims[k].step_no = t, st
+    torch.cuda.synchronize()
+    p2 = processed()
+    ev0.record()
+    for _ in range(seq_steps):
+        for s in b.sims:
+            s.run(1, flags)
+    ev1.record()
+    ev1.synchronize()
+    ms_seq = ev0.elapsed_time(ev1)
+    p3 = processed()
+    value = (p1 - p0) / (ms * 1e-3)
+    seq_value = (p3 - p2) / (ms_seq * 1e-3)
+    out = {"workload": "c4_64_ensembles_loguniform_1e3_1e6", "value": value, "unit": "particle-steps/s",
+           "ensembles": len(wls), "particles_at_start": n0, "pre_steps": C4_PRE, "steps": steps,
+           "ms_per_step": ms / steps, "launch": "cuda_graph", "tuned_config": cfg, "tune_best_ms": tune_ms,
+           "sequential_qed_step": {"value": seq_value, "steps": seq_steps, "ms_per_step": ms_seq / seq_steps},
+           "batched_over_sequential": value / seq_value, "status": status,
+           "l2": "not flushed: every step streams > 1 GB of particle state (L2 is 129 MB)"}
+    b.close()
+    return out
+
+
 def run_diag(q, torch, sim, reps=5):
     """End-of-run observables on the final state: photon spectrum with the Stokes parameters
     in the (x, y) detection basis, electron spectrum with the mean spin (mixed layout reads
@@ -251,6 +322,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=20_000)
     ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--c4-steps", type=int, default=100,
+                    help="timed steps of the 64-ensemble batch (0: skip)")
     ap.add_argument("--kernel-steps", type=int, default=20,
                     help="steps after the timed ones with per-kernel timing (roofline)")
     args = ap.parse_args()
@@ -307,6 +380,7 @@ def main():
                                   args.warmup, flush, flags, min(args.kernel_steps, args.steps))
         sim64.close()
     diag = run_diag(q, torch, sim)
+    c4 = run_c4(q, torch, args.c4_steps, args.warmup) if args.c4_steps > 0 else None
     e2e = run_e2e(q, torch, sim, q.QED_PREC_MIXED, args.e2e_steps, flags)
 
     ms, parts = info["ms"], info["particles"]
@@ -358,7 +432,8 @@ def main():
                                    f"{PRE_STEPS} untimed"},
         "e2e": e2e,
         "diag": diag,
-        "gpu_launches": 7 * args.steps,   # per step: photon, lepton, 2 scans, pairs, refill, NCS
+        "c4": c4,
+        "gpu_launches": 7 * args.steps,   # headline loop; per step: photon, lepton, 2 scans, pairs, refill, NCS
         "clocks": clk.summary(),
         "counts_after": {"e": info["final_counts"][0], "pos": info["final_counts"][1],
                          "ph": info["final_counts"][2]},

@@ -118,6 +118,7 @@ typedef struct {
   uint64_t n_range;      /* chi clamped at a table's upper edge                */
   uint64_t n_drop;       /* births dropped for lack of capacity                */
   uint64_t n_steps;      /* steps accumulated                                  */
+  uint64_t n_processed;  /* particle-steps: live e-, e+, photons at each step start */
 } qed_step_stats;
 
 typedef struct qed_ctx qed_ctx;             /* tables, id counter, scratch, status   */

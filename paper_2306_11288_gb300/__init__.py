@@ -49,7 +49,7 @@ class qed_fields(C.Structure):
 
 class qed_step_stats(C.Structure):
     _fields_ = [("n_ncs", C.c_uint64 * 2), ("n_nbw", C.c_uint64), ("n_range", C.c_uint64),
-                ("n_drop", C.c_uint64), ("n_steps", C.c_uint64)]
+                ("n_drop", C.c_uint64), ("n_steps", C.c_uint64), ("n_processed", C.c_uint64)]
 
 
 class qed_diag_spec(C.Structure):
@@ -420,7 +420,7 @@ class Simulation:
         self.t = float(wl.get("t0", 0.0))
         self.seed = int(wl["seed"])
         self.step_no = int(wl.get("step0", 0))
-        self.stats = torch.zeros(6, dtype=torch.int64, device="cuda")
+        self.stats = torch.zeros(7, dtype=torch.int64, device="cuda")
         qed_set_next_id(self.ctx, int(wl["next_id"]))
         qed_read_status(self.ctx, clear=True)
 
@@ -439,7 +439,7 @@ class Simulation:
     def counters(self) -> dict:
         s = self.stats.cpu().numpy()
         return {"n_ncs_e": int(s[0]), "n_ncs_p": int(s[1]), "n_nbw": int(s[2]), "n_range": int(s[3]),
-                "n_drop": int(s[4]), "n_steps": int(s[5])}
+                "n_drop": int(s[4]), "n_steps": int(s[5]), "n_processed": int(s[6])}
 
     def status(self, clear=False) -> int:
         return qed_read_status(self.ctx, clear)

@@ -349,12 +349,13 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(const __grid_consta
   __shared__ unsigned int s_off[kB ? kMaxEns + 1 : 1];
   DevState* gst = a.st;
   unsigned int ntiles;
+  unsigned long long n_one = 0;   // single ensemble: its photon count, read once
   if constexpr (kB) {
     for (int e = threadIdx.x; e <= a.n_ens; e += blockDim.x) s_off[e] = a.map->ph_tile0[e];
     ntiles = a.map->ph_tile0[a.n_ens];
   } else {
-    const unsigned long long n0 = a.e0.sp[2].present ? a.e0.st->n_live[2] : 0ull;
-    ntiles = (unsigned int)((n0 + kTile - 1) / kTile);
+    n_one = a.e0.sp[2].present ? a.e0.st->n_live[2] : 0ull;
+    ntiles = (unsigned int)((n_one + kTile - 1) / kTile);
   }
   const Tabs<R> tb{reinterpret_cast<const R*>(a.tables),
                    kSm ? s_rates : reinterpret_cast<const R*>(a.tables) + kOffRA};
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(const __grid_consta
     const EnsTime tm = time_of<kB>(E);
     DevState* st = E.st;
     const SpeciesArgs& P = E.sp[2];
-    const unsigned long long n = P.present ? st->n_live[2] : 0ull;
+    const unsigned long long n = kB ? (P.present ? st->n_live[2] : 0ull) : n_one;
     const unsigned int i = (tile - (kB ? s_off[ens] : 0u)) * kTile + threadIdx.x;   // capacity <= 2^32 - 256
     const bool live = i < (unsigned int)n;
     double x = 0, y = 0, z = 0;
@@ -464,6 +465,7 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(const __grid_consta
   __shared__ unsigned int s_et[kB ? kMaxEns : 1];
   DevState* gst = a.st;
   unsigned int ntiles, t0s = 0;
+  unsigned long long n0s = 0, n1s = 0;   // single ensemble: its e-, e+ counts, read once
   if constexpr (kB) {
     for (int e = threadIdx.x; e <= a.n_ens; e += blockDim.x) {
       s_off[e] = a.map->lep_tile0[e];
@@ -471,10 +473,10 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(const __grid_consta
     }
     ntiles = a.map->lep_tile0[a.n_ens];
   } else {
-    const unsigned long long n0 = a.e0.sp[0].present ? a.e0.st->n_live[0] : 0ull;
-    const unsigned long long n1 = a.e0.sp[1].present ? a.e0.st->n_live[1] : 0ull;
-    t0s = (unsigned int)((n0 + kTile - 1) / kTile);
-    ntiles = t0s + (unsigned int)((n1 + kTile - 1) / kTile);
+    n0s = a.e0.sp[0].present ? a.e0.st->n_live[0] : 0ull;
+    n1s = a.e0.sp[1].present ? a.e0.st->n_live[1] : 0ull;
+    t0s = (unsigned int)((n0s + kTile - 1) / kTile);
+    ntiles = t0s + (unsigned int)((n1s + kTile - 1) / kTile);
   }
   const Tabs<R> tb{reinterpret_cast<const R*>(a.tables),
                    kSm ? s_rates : reinterpret_cast<const R*>(a.tables) + kOffRA};
@@ -492,7 +494,7 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(const __grid_consta
     const unsigned int t0 = kB ? s_et[ens] : t0s;               // its e- tiles come first
     const int sp_idx = lt < t0 ? 0 : 1;
     const SpeciesArgs& L = E.sp[sp_idx];
-    const unsigned long long nsp = L.present ? st->n_live[sp_idx] : 0ull;
+    const unsigned long long nsp = kB ? (L.present ? st->n_live[sp_idx] : 0ull) : (sp_idx == 0 ? n0s : n1s);
     const unsigned int i = (lt - (sp_idx == 0 ? 0u : t0)) * kTile + threadIdx.x;
     const bool live = i < (unsigned int)nsp;
     const R q = sp_idx == 0 ? R(-1) : R(1);
@@ -1034,6 +1036,9 @@ __global__ void __launch_bounds__(kTile) k_ncs_ev(const __grid_constant__ StepAr
     const EnsArgs& E = ens_of<kB>(a, e);
     volatile DevState* v = E.st;
     const unsigned long long nbw = v->n_nbw, ncs = births ? v->n_ncs_tot : 0ull, surv = v->n_surv;
+    const unsigned long long processed = (E.sp[0].present ? v->n_live[0] : 0ull) +   // step-start counts
+                                         (E.sp[1].present ? v->n_live[1] : 0ull) +
+                                         (E.sp[2].present ? v->n_live[2] : 0ull);
     for (int s = 0; s < 2; ++s) {
       if (!E.sp[s].present) continue;
       const unsigned long long nn = v->n_live[s] + nbw;
@@ -1045,6 +1050,7 @@ __global__ void __launch_bounds__(kTile) k_ncs_ev(const __grid_constant__ StepAr
     }
     v->next_id = v->next_id + 2ull * nbw + ncs;
     if (E.user_stats) {
+      E.user_stats->n_processed += processed;
       E.user_stats->n_ncs[0] += v->ev[0];
       E.user_stats->n_ncs[1] += v->ev[1];
       E.user_stats->n_nbw += nbw;

@@ -59,7 +59,11 @@ def _caps(wl):
 def _alone(parent, wl, prec, steps):
     c = q.qed_ctx_share(parent)
     sim = q.Simulation(wl, prec=prec, ctx=c, **_caps(wl))
-    sim.run(steps, ALL)
+    processed = 0
+    for _ in range(steps):
+        processed += sim.e.count() + sim.pos.count() + sim.ph.count()
+        sim.run(1, ALL)
+    assert sim.counters()["n_processed"] == processed   # particle-steps counted on the device
     out = (sim.state(), sim.counters(), sim.t, sim.step_no)
     sim.close()
     q.qed_destroy(c)
