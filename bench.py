@@ -186,57 +186,61 @@ def c4_workload(seed=4):
     return wls
 
 
-def run_c4(q, torch, steps, warmup, seq_steps=5, tune_steps=2):
+def run_c4(q, torch, steps, warmup, tune_steps=2):
     """Batched ensembles: CUDA-graph replay of one batched step after the autotuner picked
-    the launch shape; then the same ensembles stepped one by one with qed_step."""
+    the launch shape.  For comparison the same ensembles, advanced to the same step on a
+    second copy (runs are deterministic), step one by one with qed_step over the same
+    segment of the trajectory."""
     wls = c4_workload()
     caps = []
     for wl in wls:
         n = len(wl["e"]["id"]) + len(wl["ph"]["id"])
         caps.append({"cap_e": n + n // 2 + 4096, "cap_p": n // 2 + 4096, "cap_ph": 24 * n + 4096})
     flags = q.QED_F_NCS | q.QED_F_NBW | q.QED_F_VB | q.QED_F_SPIN
-    b = q.Batch(wls, prec=q.QED_PREC_MIXED, flags=flags, caps=caps)
     n0 = sum(len(w["e"]["id"]) + len(w["ph"]["id"]) for w in wls)
-    b.run(C4_PRE)
-    cfg, tune_ms = q.qed_batch_tune(b.b, tune_steps)
-    b.run(warmup)
-    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def processed():
+    def processed(b):
         return int(torch.stack([s.stats for s in b.sims]).sum(0)[6].item())
 
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0 = processed()
+    b = q.Batch(wls, prec=q.QED_PREC_MIXED, flags=flags, caps=caps)
+    b.run(C4_PRE)
+    cfg, tune_rate = q.qed_batch_tune(b.b, tune_steps)
+    b.run(warmup)
+    torch.cuda.synchronize()
+    done = b.clocks()[0][1] - wls[0]["step0"]
+    p0 = processed(b)
     ev0.record()
     b.run(steps)
     ev1.record()
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
-    p1 = processed()
+    value = (processed(b) - p0) / (ms * 1e-3)
     status = q.qed_read_status(b.ctx)
-    # the same ensembles, one qed_step per ensemble per step
+    b.close()
+    # second copy, advanced to the same step, then one qed_step per ensemble per step
+    b = q.Batch(c4_workload(), prec=q.QED_PREC_MIXED, flags=flags, caps=caps)
+    b.run(done)
     for k, (t, st) in enumerate(b.clocks()):
         b.sims[k].t, b.sims[k].step_no = t, st
     torch.cuda.synchronize()
-    p2 = processed()
+    p0 = processed(b)
     ev0.record()
-    for _ in range(seq_steps):
+    for _ in range(steps):
         for s in b.sims:
             s.run(1, flags)
     ev1.record()
     ev1.synchronize()
     ms_seq = ev0.elapsed_time(ev1)
-    p3 = processed()
-    value = (p1 - p0) / (ms * 1e-3)
-    seq_value = (p3 - p2) / (ms_seq * 1e-3)
-    out = {"workload": "c4_64_ensembles_loguniform_1e3_1e6", "value": value, "unit": "particle-steps/s",
-           "ensembles": len(wls), "particles_at_start": n0, "pre_steps": C4_PRE, "steps": steps,
-           "ms_per_step": ms / steps, "launch": "cuda_graph", "tuned_config": cfg, "tune_best_ms": tune_ms,
-           "sequential_qed_step": {"value": seq_value, "steps": seq_steps, "ms_per_step": ms_seq / seq_steps},
-           "batched_over_sequential": value / seq_value, "status": status,
-           "l2": "not flushed: every step streams > 1 GB of particle state (L2 is 129 MB)"}
+    seq_value = (processed(b) - p0) / (ms_seq * 1e-3)
     b.close()
-    return out
+    return {"workload": "c4_64_ensembles_loguniform_1e3_1e6", "value": value, "unit": "particle-steps/s",
+            "ensembles": len(wls), "particles_at_start": n0, "steps_before_timing": done, "steps": steps,
+            "ms_per_step": ms / steps, "launch": "cuda_graph", "tuned_config": cfg, "tune_best_rate": tune_rate,
+            "sequential_qed_step": {"value": seq_value, "ms_per_step": ms_seq / steps,
+                                    "note": "same ensembles, same steps, 64 qed_step calls per step"},
+            "batched_over_sequential": value / seq_value, "status": status,
+            "l2": "not flushed: every step streams > 1 GB of particle state (L2 is 129 MB)"}
 
 
 def run_diag(q, torch, sim, reps=5):

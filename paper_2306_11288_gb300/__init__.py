@@ -187,11 +187,12 @@ def qed_batch_set_config(b, stream_blocks_per_sm, event_blocks_per_sm, smem_rate
 
 
 def qed_batch_tune(b, steps_per_candidate, stream=None):
-    c, ms = qed_batch_config(), C.c_double()
-    _check(lib().qed_batch_tune(b, int(steps_per_candidate), _stream(stream), C.byref(c), C.byref(ms)),
+    """(chosen launch shape, its particle-steps per second)"""
+    c, rate = qed_batch_config(), C.c_double()
+    _check(lib().qed_batch_tune(b, int(steps_per_candidate), _stream(stream), C.byref(c), C.byref(rate)),
            "qed_batch_tune")
     return {"stream_blocks_per_sm": c.stream_blocks_per_sm, "event_blocks_per_sm": c.event_blocks_per_sm,
-            "smem_rates": c.smem_rates}, float(ms.value)
+            "smem_rates": c.smem_rates}, float(rate.value)
 
 
 def qed_batch_destroy(b):

@@ -306,9 +306,12 @@ extern "C" qed_status qed_batch_create(qed_ctx* ctx, const qed_ensemble* ens, in
   return QED_OK;
 }
 
+#ifndef QED_BATCH_STEP_PDL
+#define QED_BATCH_STEP_PDL 1
+#endif
 extern "C" qed_status qed_batch_step(qed_batch* b, void* stream) {
   if (!b) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_step: batch is NULL");
-  return batch_launch(b, reinterpret_cast<cudaStream_t>(stream), true);
+  return batch_launch(b, reinterpret_cast<cudaStream_t>(stream), QED_BATCH_STEP_PDL);
 }
 
 // captures one step on the batch's capture stream (programmatic dependent launches if the
@@ -318,7 +321,10 @@ static qed_status batch_capture(qed_batch* b) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
-  for (int attempt = 0; attempt < 2; ++attempt) {
+#ifndef QED_BATCH_GRAPH_PDL
+#define QED_BATCH_GRAPH_PDL 1
+#endif
+  for (int attempt = QED_BATCH_GRAPH_PDL ? 0 : 1; attempt < 2; ++attempt) {
     const bool pdl = attempt == 0;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
@@ -386,13 +392,20 @@ extern "C" qed_status qed_batch_set_config(qed_batch* b, const qed_batch_config*
   return QED_OK;
 }
 
+static qed_status batch_processed(qed_batch* b, cudaStream_t s, unsigned long long* v) {
+  BCK(cudaMemcpyAsync(v, reinterpret_cast<char*>(b->gst) + offsetof(DevState, processed), sizeof(*v),
+                      cudaMemcpyDeviceToHost, s));
+  BCK(cudaStreamSynchronize(s));
+  return QED_OK;
+}
+
 extern "C" qed_status qed_batch_tune(qed_batch* b, uint32_t steps_per_candidate, void* stream, qed_batch_config* chosen,
-                                     double* ms_per_step) {
+                                     double* rate) {
   if (!b || steps_per_candidate < 1) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_tune: bad arguments");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int sblocks[4] = {1, 2, 3, 4}, eblocks[4] = {1, 2, 4, 8};
   qed_batch_config best = b->cfg;
-  double best_ms = 1e300;
+  double best_rate = -1.0;
   for (int sm = 1; sm >= 0; --sm) {
     const int occ_max = std::max(b->occ[sm][0], b->occ[sm][1]);
     for (int si = 0; si < 4; ++si) {
@@ -401,6 +414,8 @@ extern "C" qed_status qed_batch_tune(qed_batch* b, uint32_t steps_per_candidate,
         qed_batch_config c{sblocks[si], eblocks[ei], sm};
         qed_status r = qed_batch_set_config(b, &c);
         if (r == QED_OK) r = batch_launch(b, s, true);   // settle
+        unsigned long long p0 = 0, p1 = 0;
+        if (r == QED_OK) r = batch_processed(b, s, &p0);
         if (r != QED_OK) return r;
         BCK(cudaEventRecord(b->t0, s));
         for (uint32_t k = 0; k < steps_per_candidate && r == QED_OK; ++k) r = batch_launch(b, s, true);
@@ -409,9 +424,12 @@ extern "C" qed_status qed_batch_tune(qed_batch* b, uint32_t steps_per_candidate,
         BCK(cudaEventSynchronize(b->t1));
         float ms = 0;
         BCK(cudaEventElapsedTime(&ms, b->t0, b->t1));
-        const double per = ms / steps_per_candidate;
-        if (per < best_ms) {
-          best_ms = per;
+        r = batch_processed(b, s, &p1);
+        if (r != QED_OK) return r;
+        // the population changes from candidate to candidate: compare particle-steps per second
+        const double rt = ms > 0 ? (double)(p1 - p0) / (ms * 1e-3) : 0.0;
+        if (rt > best_rate) {
+          best_rate = rt;
           best = c;
         }
       }
@@ -420,7 +438,7 @@ extern "C" qed_status qed_batch_tune(qed_batch* b, uint32_t steps_per_candidate,
   const qed_status r = qed_batch_set_config(b, &best);
   if (r != QED_OK) return r;
   if (chosen) *chosen = best;
-  if (ms_per_step) *ms_per_step = best_ms;
+  if (rate) *rate = best_rate;
   return QED_OK;
 }
 

@@ -254,6 +254,7 @@ struct DevState {
   unsigned int done;                 // finished-block counter of the last kernel
   unsigned int epoch;                // stamp of this step's log entries
   unsigned int status;               // QED_STATUS_* bits (sticky)
+  unsigned long long processed;      // particle-steps of all ensembles stepped with this state (sticky)
   // batched steps: the ensemble's clock, advanced on the device by every step
   double t;
   unsigned int step;

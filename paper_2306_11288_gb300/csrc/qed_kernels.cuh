@@ -1049,6 +1049,7 @@ __global__ void __launch_bounds__(kTile) k_ncs_ev(const __grid_constant__ StepAr
       v->n_live[2] = nn > E.sp[2].cap ? E.sp[2].cap : nn;
     }
     v->next_id = v->next_id + 2ull * nbw + ncs;
+    atomicAdd(&gst->processed, processed);
     if (E.user_stats) {
       E.user_stats->n_processed += processed;
       E.user_stats->n_ncs[0] += v->ev[0];

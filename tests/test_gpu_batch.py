@@ -103,8 +103,8 @@ def test_graph_replay_and_every_tuned_shape_equal_alone(parent):
     wls = _ensembles(5, 2000, seed=43)
     b = q.Batch(wls, prec=q.QED_PREC_MIXED, ctx=parent, caps=[_caps(w) for w in wls])
     b.run(12)                                  # CUDA graph of one step, replayed
-    cfg, ms = q.qed_batch_tune(b.b, 1)         # every candidate shape steps the batch
-    assert ms > 0 and 1 <= cfg["stream_blocks_per_sm"] <= 4
+    cfg, rate = q.qed_batch_tune(b.b, 1)       # every candidate shape steps the batch
+    assert rate > 0 and 1 <= cfg["stream_blocks_per_sm"] <= 4
     b.run(5)                                   # graph recaptured for the chosen shape
     clocks = b.clocks()
     for k, wl in enumerate(wls):
