@@ -306,12 +306,9 @@ extern "C" qed_status qed_batch_create(qed_ctx* ctx, const qed_ensemble* ens, in
   return QED_OK;
 }
 
-#ifndef QED_BATCH_STEP_PDL
-#define QED_BATCH_STEP_PDL 1
-#endif
 extern "C" qed_status qed_batch_step(qed_batch* b, void* stream) {
   if (!b) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_step: batch is NULL");
-  return batch_launch(b, reinterpret_cast<cudaStream_t>(stream), QED_BATCH_STEP_PDL);
+  return batch_launch(b, reinterpret_cast<cudaStream_t>(stream), true);
 }
 
 // captures one step on the batch's capture stream (programmatic dependent launches if the
@@ -321,10 +318,7 @@ static qed_status batch_capture(qed_batch* b) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
-#ifndef QED_BATCH_GRAPH_PDL
-#define QED_BATCH_GRAPH_PDL 1
-#endif
-  for (int attempt = QED_BATCH_GRAPH_PDL ? 0 : 1; attempt < 2; ++attempt) {
+  for (int attempt = 0; attempt < 2; ++attempt) {
     const bool pdl = attempt == 0;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
