@@ -62,6 +62,8 @@ typedef enum { QED_PREC_F64 = 0, QED_PREC_MIXED = 1 } qed_precision;
 #define QED_F_SPIN 8u          /* T-BMT spin precession (Sec. III B, Eq. bmteqn)             */
 #define QED_F_NO_RECOIL 16u    /* test mode: emission changes the spin only, no photon born   */
 #define QED_F_DROP_PHOTONS 32u /* emitted photons are not stored (recoil is applied)          */
+#define QED_F_MLP 64u          /* NCS photon energy from the learned sampler (mixed path only;
+                                  the context or its owner must hold parameters: qed_mlp_*)  */
 
 /* Structure-of-arrays view of one species, caller-owned device memory.  Element i of
  * every array describes particle i.  Element types follow qed_precision (above):
@@ -346,6 +348,30 @@ qed_status qed_batch_tune(qed_batch *b, uint32_t steps_per_candidate, void *stre
                           double *rate);
 
 qed_status qed_batch_destroy(qed_batch *b);
+
+/* ---- Learned photon-energy sampler of the NCS events -----------------------------------
+ * A 3 -> 64 -> 64 -> 1 GELU network maps (ln chi_e, s = S.zeta, one uniform r) to ln u,
+ * u = omega/(gamma - omega), in place of the two-component inverse-CDF table lookup (the
+ * spin mixture of Eq. Wspin2, inverted as one monotone map of r).  Its 64 x 64 layer runs on
+ * the tensor cores in BF16 with FP32 accumulation; the rest in FP32.  The paper has no
+ * counterpart: this is an alternative sampler, judged against the table sampler.
+ * Parameters live on the context that owns the tables (a shared context uses its owner's).
+ * Parameter vector (4481 floats): w1[64][3], b1[64], w2[64][64], b2[64], w3[64], b3. */
+
+/* Trains on n_samples samples produced by the table sampler itself (ln chi_e uniform in
+ * [ln 1e-3, ln 10], s uniform in [-1, 1], r uniform; target its mixture inverse CDF from the
+ * FP32 tables), in batches of `batch`, with Adam and a cosine learning rate, from an
+ * initialisation seeded by `seed`.  Syncs.  Errors: QED_ERR_INVALID_ARG (64 <= batch <=
+ * 2^22, batch <= n_samples), QED_ERR_CUDA. */
+qed_status qed_mlp_train(qed_ctx *ctx, uint64_t n_samples, uint32_t batch, uint64_t seed, void *stream);
+/* Copy the parameter vector in or out (host, 4481 floats; syncs). */
+qed_status qed_mlp_set_params(qed_ctx *ctx, const float *host, void *stream);
+qed_status qed_mlp_get_params(qed_ctx *ctx, float *host, void *stream);
+/* ln u of the learned sampler (tensor cores) and of the table sampler's mixture inverse for
+ * n device rows (ln chi_e, s, r) -> dev_out[n] (async).  Errors: QED_ERR_NOT_INITIALIZED (no
+ * parameters, for qed_mlp_eval), QED_ERR_INVALID_ARG. */
+qed_status qed_mlp_eval(qed_ctx *ctx, const float *dev_in, float *dev_out, uint64_t n, void *stream);
+qed_status qed_mlp_target(qed_ctx *ctx, const float *dev_in, float *dev_out, uint64_t n, void *stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *qed_last_error(void);

@@ -21,6 +21,7 @@ QED_ERR_NOT_INITIALIZED, QED_ERR_TIMEOUT, QED_WARN_TABLE_RANGE = 4, 5, 6
 QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
 QED_PREC_F64, QED_PREC_MIXED = 0, 1
 QED_F_NCS, QED_F_NBW, QED_F_VB, QED_F_SPIN, QED_F_NO_RECOIL, QED_F_DROP_PHOTONS = 1, 2, 4, 8, 16, 32
+QED_F_MLP = 64
 QED_STATUS_CAPACITY, QED_STATUS_TIMEOUT, QED_STATUS_TABLE_RANGE = 1, 2, 4
 FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
 
@@ -29,7 +30,9 @@ ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particle
                  "qed_step", "qed_step_host", "qed_step_static", "qed_read_status", "qed_copy_table",
                  "qed_set_timing", "qed_get_timing", "qed_diag", "qed_ctx_share", "qed_batch_create",
                  "qed_batch_step", "qed_batch_run", "qed_batch_clock", "qed_batch_get_config",
-                 "qed_batch_set_config", "qed_batch_tune", "qed_batch_destroy", "qed_last_error")
+                 "qed_batch_set_config", "qed_batch_tune", "qed_batch_destroy", "qed_mlp_train",
+                 "qed_mlp_set_params", "qed_mlp_get_params", "qed_mlp_eval", "qed_mlp_target", "qed_last_error")
+MLP_PARAMS = 4481
 QED_DIAG_SPECTRUM, QED_DIAG_DETECTOR = 0, 1
 
 
@@ -109,6 +112,11 @@ def lib():
         L.qed_batch_set_config.argtypes = [vp, C.POINTER(qed_batch_config)]
         L.qed_batch_tune.argtypes = [vp, u32, vp, C.POINTER(qed_batch_config), C.POINTER(d)]
         L.qed_batch_destroy.argtypes = [vp]
+        L.qed_mlp_train.argtypes = [vp, u64, u32, u64, vp]
+        L.qed_mlp_set_params.argtypes = [vp, C.POINTER(C.c_float), vp]
+        L.qed_mlp_get_params.argtypes = [vp, C.POINTER(C.c_float), vp]
+        L.qed_mlp_eval.argtypes = [vp, vp, vp, u64, vp]
+        L.qed_mlp_target.argtypes = [vp, vp, vp, u64, vp]
         L.qed_last_error.restype = C.c_char_p
         for name in ABI_FUNCTIONS:
             if name != "qed_last_error":
@@ -193,6 +201,45 @@ def qed_batch_tune(b, steps_per_candidate, stream=None):
            "qed_batch_tune")
     return {"stream_blocks_per_sm": c.stream_blocks_per_sm, "event_blocks_per_sm": c.event_blocks_per_sm,
             "smem_rates": c.smem_rates}, float(rate.value)
+
+
+def qed_mlp_train(ctx, n_samples, batch=16384, seed=1, stream=None):
+    _check(lib().qed_mlp_train(ctx, int(n_samples), int(batch), int(seed), _stream(stream)), "qed_mlp_train")
+
+
+def qed_mlp_set_params(ctx, params, stream=None):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != MLP_PARAMS:
+        raise ValueError(f"expected {MLP_PARAMS} parameters")
+    _check(lib().qed_mlp_set_params(ctx, a.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)),
+           "qed_mlp_set_params")
+
+
+def qed_mlp_get_params(ctx, stream=None) -> np.ndarray:
+    a = np.zeros(MLP_PARAMS, dtype=np.float32)
+    _check(lib().qed_mlp_get_params(ctx, a.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)),
+           "qed_mlp_get_params")
+    return a
+
+
+def qed_mlp_eval(ctx, dev_in_ptr, dev_out_ptr, n, stream=None):
+    _check(lib().qed_mlp_eval(ctx, C.c_void_p(dev_in_ptr), C.c_void_p(dev_out_ptr), int(n), _stream(stream)),
+           "qed_mlp_eval")
+
+
+def qed_mlp_target(ctx, dev_in_ptr, dev_out_ptr, n, stream=None):
+    _check(lib().qed_mlp_target(ctx, C.c_void_p(dev_in_ptr), C.c_void_p(dev_out_ptr), int(n), _stream(stream)),
+           "qed_mlp_target")
+
+
+def mlp_apply(ctx, rows: np.ndarray, which="eval") -> np.ndarray:
+    """ln u for host rows (ln chi_e, s, r) [n, 3] via the learned sampler ("eval") or the
+    table sampler's mixture inverse ("target")."""
+    import torch
+    x = torch.as_tensor(np.ascontiguousarray(rows, dtype=np.float32), device="cuda")
+    y = torch.empty(len(rows), dtype=torch.float32, device="cuda")
+    (qed_mlp_eval if which == "eval" else qed_mlp_target)(ctx, x.data_ptr(), y.data_ptr(), len(rows))
+    return y.cpu().numpy().astype(np.float64)
 
 
 def qed_batch_destroy(b):

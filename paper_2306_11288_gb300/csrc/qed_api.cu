@@ -92,6 +92,7 @@ extern "C" qed_status qed_ctx_share(qed_ctx* parent, void* stream, qed_ctx** out
   c->tab64 = parent->tab64;
   c->tab32 = parent->tab32;
   c->shared = 1;
+  c->owner = parent;
   memcpy(c->nblk, parent->nblk, sizeof(c->nblk));
   cudaError_t e = cudaMalloc(&c->st, sizeof(DevState));
   DevState h;
@@ -119,6 +120,7 @@ extern "C" qed_status qed_destroy(qed_ctx* c) {
   if (!c->shared) {
     cudaFree(c->tab64);
     cudaFree(c->tab32);
+    cudaFree(c->mlp);
   }
   cudaFree(c->st);
   for (int k = 0; k < 2; ++k) {
@@ -316,6 +318,14 @@ void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos,
 }  // namespace qedk
 
 namespace qedk {
+qed_status check_mlp_flag(const qed_ctx* c, uint32_t flags, qed_precision prec, const char* who) {
+  if (!(flags & QED_F_MLP)) return QED_OK;
+  if (prec != QED_PREC_MIXED) FAIL(QED_ERR_INVALID_ARG, "%s: the learned sampler runs on the mixed path only", who);
+  const qed_ctx* o = c->owner ? c->owner : c;
+  if (!o->mlp_ready) FAIL(QED_ERR_NOT_INITIALIZED, "%s: the learned sampler has no parameters (qed_mlp_train)", who);
+  return QED_OK;
+}
+
 qed_status check_fields(const qed_fields* f, const char* who) {
   switch (f->kind) {
     case QED_FIELD_NONE:
@@ -344,7 +354,7 @@ static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos
   if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_step: invalid context");
   if (!f) FAIL(QED_ERR_INVALID_ARG, "qed_step: fields is NULL");
   if (!(dt > 0.0) || !std::isfinite(dt)) FAIL(QED_ERR_INVALID_ARG, "qed_step: dt must be positive and finite");
-  if (flags & ~63u) FAIL(QED_ERR_INVALID_ARG, "qed_step: unknown flag bits 0x%x", flags & ~63u);
+  if (flags & ~127u) FAIL(QED_ERR_INVALID_ARG, "qed_step: unknown flag bits 0x%x", flags & ~127u);
   const qed_particles* all[3] = {e, pos, ph};
   const qed_species want[3] = {QED_ELECTRON, QED_POSITRON, QED_PHOTON};
   int have = -1;
@@ -357,7 +367,8 @@ static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos
   }
   *prec = have < 0 ? QED_PREC_F64 : (qed_precision)have;
   if ((flags & QED_F_NBW) && (!e || !pos)) FAIL(QED_ERR_INVALID_ARG, "qed_step: NBW needs e- and e+ sets");
-  qed_status r_;
+  qed_status r_ = check_mlp_flag(c, flags, *prec, "qed_step");
+  if (r_ != QED_OK) return r_;
   r_ = check_fields(f, "qed_step");
   if (r_ != QED_OK) return r_;
   const unsigned long long tp = ph ? tiles_of(ph->cap) : 0;
@@ -380,6 +391,7 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
   a.fdt = (float)dt;
   a.flags = flags;
   a.tables = prec == QED_PREC_F64 ? (const void*)c->tab64 : (const void*)c->tab32;
+  a.mlp = (c->owner ? c->owner : c)->mlp;
   a.st = c->st;
   for (int k = 0; k < 2; ++k) {
     a.tile_cnt[k] = c->tile_cnt[k];

@@ -83,7 +83,12 @@ static void launch_batch_t(const StepArgs& a, const int* nb, cudaStream_t s, cud
   launch_k(k_fill<R, true>, nb[2], kTile, s, pdl, a);
   cudaStreamWaitEvent(s, join, 0);
   k_scan<true><<<1, kScanThreads, 0, s>>>(a, 1);
-  launch_k(k_ncs_ev<R, true>, nb[2], kTile, s, pdl, a);
+  if constexpr (sizeof(R) == 4) {
+    if (a.flags & QED_F_MLP) launch_k(k_ncs_ev_mlp<true>, nb[2] * 2, kMlpRows, s, pdl, a);
+    else launch_k(k_ncs_ev<R, true>, nb[2], kTile, s, pdl, a);
+  } else {
+    launch_k(k_ncs_ev<R, true>, nb[2], kTile, s, pdl, a);
+  }
 }
 
 template <typename R, bool kSm>
@@ -163,6 +168,7 @@ static StepArgs batch_args(const qed_batch* b) {
   a.fdt = (float)b->dt;
   a.flags = b->flags;
   a.tables = b->prec == QED_PREC_F64 ? (const void*)b->ctx->tab64 : (const void*)b->ctx->tab32;
+  a.mlp = (b->ctx->owner ? b->ctx->owner : b->ctx)->mlp;
   a.st = b->gst;
   for (int k = 0; k < 2; ++k) {
     a.tile_cnt[k] = b->tile_cnt[k];
@@ -202,7 +208,7 @@ extern "C" qed_status qed_batch_create(qed_ctx* ctx, const qed_ensemble* ens, in
   if (!ctx || !ctx->alive) BFAIL(QED_ERR_NOT_INITIALIZED, "qed_batch_create: invalid context");
   if (!ens || n_ens < 1 || n_ens > kMaxEns) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: n_ens must be in [1, %d]", kMaxEns);
   if (!(dt > 0.0) || !std::isfinite(dt)) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: dt must be positive and finite");
-  if (flags & ~63u) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: unknown flag bits 0x%x", flags & ~63u);
+  if (flags & ~127u) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: unknown flag bits 0x%x", flags & ~127u);
   int prec = -1;
   unsigned long long tp = 1, tl = 1, cap_ph = 0, cap_l = 0;
   for (int i = 0; i < n_ens; ++i) {
@@ -230,6 +236,10 @@ extern "C" qed_status qed_batch_create(qed_ctx* ctx, const qed_ensemble* ens, in
     cap_l += (E.e ? E.e->cap : 0) + (E.pos ? E.pos->cap : 0);
   }
   if (tp >= (1ull << 31) || tl >= (1ull << 31)) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: batch too large");
+  {
+    const qed_status rm = check_mlp_flag(ctx, flags, prec < 0 ? QED_PREC_F64 : (qed_precision)prec, "qed_batch_create");
+    if (rm != QED_OK) return rm;
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   qed_batch* b = new qed_batch();
   memset(b, 0, sizeof(*b));

@@ -63,6 +63,7 @@ struct StepArgs {
   float fdt;
   unsigned int flags;
   const void* tables;                // double* or float* depending on precision
+  const void* mlp;                   // learned sampler parameters (QED_F_MLP)
   DevState* st;                      // log cursors, epoch, finished-block counter, status
   unsigned int* tile_cnt[2];         // events per tile: photon tiles, lepton tiles
   unsigned int* tile_pre[2];         // their exclusive prefixes
@@ -90,6 +91,11 @@ void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos,
 void step_time_floats(double t, double phi0, float* t_rel, float* t_mod);
 // host validation of a field descriptor (message prefixed by who)
 qed_status check_fields(const qed_fields* f, const char* who);
+}  // namespace qedk
+struct qed_ctx;
+namespace qedk {
+// QED_F_MLP needs the mixed path and trained (or set) sampler parameters
+qed_status check_mlp_flag(const qed_ctx* c, uint32_t flags, qed_precision prec, const char* who);
 // occupancy-derived persistent grid sizes
 qed_status step_grid_sizes(qed_precision prec, int* nblk);
 size_t nbw_rec_bytes(qed_precision p);
@@ -102,6 +108,9 @@ constexpr int kTile = 256;   // particles per tile (= threads per block, one par
 struct qed_ctx {
   int device;
   int shared;                         // tables belong to another context (qed_ctx_share)
+  qed_ctx* owner;                     // that context (NULL for an owner)
+  void* mlp;                          // learned sampler parameters (owner only)
+  int mlp_ready;
   double* tab64;
   float* tab32;
   qedk::DevState* st;

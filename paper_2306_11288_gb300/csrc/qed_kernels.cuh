@@ -29,6 +29,7 @@
 // the single-ensemble kernels, qed_batch.cu the batched ones.
 #include "qed_common.cuh"
 #include "qed_internal.h"
+#include "qed_mlp.cuh"
 
 namespace qedk {
 
@@ -911,10 +912,76 @@ __global__ void __launch_bounds__(kTile) k_fill(const __grid_constant__ StepArgs
 // spin collapse along the SQA of Eq. F0, photon pure state from Eqs. F1-F3, photon birth
 // at x^{n+1}; the last block to finish closes the step.
 // ======================================================================================
+// The last block of the final event kernel closes the step: counts, id counters,
+// statistics, clocks (batched), resets.  Called by every block of that kernel.
+template <bool kB>
+__device__ __forceinline__ void close_step(const StepArgs& a, bool births) {
+  DevState* gst = a.st;
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int d = atomicAdd(&gst->done, 1u);
+    s_last = d == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int ne = kB ? a.n_ens : 1;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const EnsArgs& E = ens_of<kB>(a, e);
+    volatile DevState* v = E.st;
+    const unsigned long long nbw = v->n_nbw, ncs = births ? v->n_ncs_tot : 0ull, surv = v->n_surv;
+    const unsigned long long processed = (E.sp[0].present ? v->n_live[0] : 0ull) +   // step-start counts
+                                         (E.sp[1].present ? v->n_live[1] : 0ull) +
+                                         (E.sp[2].present ? v->n_live[2] : 0ull);
+    for (int s = 0; s < 2; ++s) {
+      if (!E.sp[s].present) continue;
+      const unsigned long long nn = v->n_live[s] + nbw;
+      v->n_live[s] = nn > E.sp[s].cap ? E.sp[s].cap : nn;
+    }
+    if (E.sp[2].present) {
+      const unsigned long long nn = surv + ncs;
+      v->n_live[2] = nn > E.sp[2].cap ? E.sp[2].cap : nn;
+    }
+    v->next_id = v->next_id + 2ull * nbw + ncs;
+    atomicAdd(&gst->processed, processed);
+    if (E.user_stats) {
+      E.user_stats->n_processed += processed;
+      E.user_stats->n_ncs[0] += v->ev[0];
+      E.user_stats->n_ncs[1] += v->ev[1];
+      E.user_stats->n_nbw += nbw;
+      E.user_stats->n_range += v->ev[3];
+      E.user_stats->n_drop += v->ev[4];
+      E.user_stats->n_steps += 1;
+    }
+    if (v->ev[3]) atomicOr(&gst->status, QED_STATUS_TABLE_RANGE);
+    for (int q = 0; q < 6; ++q) v->ev[q] = 0;
+    v->n_nbw = 0; v->n_surv = 0; v->n_ncs_tot = 0;
+    if constexpr (kB) {
+      // the ensemble's clock: the same operations as the host forms of a single step
+      const double t = v->t + a.dt;
+      v->t = t;
+      v->step = v->step + 1;
+      v->t_rel = (float)(t - E.f.phi0);
+      v->t_mod = (float)fma(-kTwoPi, floor(t / kTwoPi), t);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile DevState* g = gst;
+    g->cursor[0] = 0; g->cursor[1] = 0;
+    g->done = 0;
+    g->epoch = g->epoch + 1;
+    __threadfence();
+  }
+}
+
 // One emission (the body of k_ncs_ev), not inlined for the same reason as nbw_event.
 template <typename R>
 __device__ __noinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
-                                       unsigned long long rank, bool births, unsigned int flags, DevState* gst) {
+                                       unsigned long long rank, bool births, unsigned int flags, DevState* gst,
+                                       bool learned, float lnu_learned) {
   DevState* st = E.st;
   const SpeciesArgs& G = E.sp[2];
   const unsigned long long nsurv = st->n_surv;
@@ -936,14 +1003,19 @@ __device__ __noinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E, c
   const R s = dot(S, zeta);
   const Uni2 um = uniforms(E.seed, id, step, 1u);
   const Uni2 us = uniforms(E.seed, id, step, 2u);
-  const R wplus = R(0.5) * (R(1) + s) * (A - B);
-  const int comp = ((R)um.u0 * (A - s * B) < wplus) ? 0 : 1;
-  const double l = um.u1;
-  R tt;
-  if (sizeof(R) == 8) tt = (R)(log(l) - log1p(-l));
-  else tt = m_log((R)l) - m_log((R)(1.0 - l));
-  tt = tt < R(kCTLo) ? R(kCTLo) : (tt > R(kCTHi) ? R(kCTHi) : tt);
-  const R uu = m_exp(tb.ncs_inv(comp, chi, tt));
+  R uu;
+  if (learned) {
+    uu = (R)expf(lnu_learned);   // the learned sampler's ln u (one uniform, um.u1)
+  } else {
+    const R wplus = R(0.5) * (R(1) + s) * (A - B);
+    const int comp = ((R)um.u0 * (A - s * B) < wplus) ? 0 : 1;
+    const double l = um.u1;
+    R tt;
+    if (sizeof(R) == 8) tt = (R)(log(l) - log1p(-l));
+    else tt = m_log((R)l) - m_log((R)(1.0 - l));
+    tt = tt < R(kCTLo) ? R(kCTLo) : (tt > R(kCTHi) ? R(kCTHi) : tt);
+    uu = m_exp(tb.ncs_inv(comp, chi, tt));
+  }
   const R omr = R(1) / (R(1) + uu), rr = uu * omr;
   const R om = rr * g1;
   R k13, k23, ik;
@@ -1017,68 +1089,73 @@ __global__ void __launch_bounds__(kTile) k_ncs_ev(const __grid_constant__ StepAr
     const EnsTime tm = time_of<kB>(E);
     const unsigned long long grank = (unsigned long long)a.tile_pre[1][rec.tile] + rec.r_in;
     const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
-    ncs_event<R>(rec, E, tb, tm.step, rank, births, a.flags, gst);
+    ncs_event<R>(rec, E, tb, tm.step, rank, births, a.flags, gst, false, 0.0f);
   }
-  // the last block to finish closes the step: counts, id counters, statistics, clocks
-  // (batched), resets
-  __shared__ int s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int d = atomicAdd(&gst->done, 1u);
-    s_last = d == gridDim.x - 1;
+  close_step<kB>(a, births);
+}
+
+
+// ======================================================================================
+// NCS events with the learned energy sampler (mixed path): a block of 128 threads takes
+// 128 logged emissions at a time, evaluates the network for all of them on the tensor
+// cores (qed_mlp.cuh), then completes each event as k_ncs_ev does.
+// ======================================================================================
+template <bool kB>
+__global__ void __launch_bounds__(kMlpRows) k_ncs_ev_mlp(const __grid_constant__ StepArgs a) {
+  pdl_wait();
+  __shared__ MlpSmem sm;
+  DevState* gst = a.st;
+  const Tabs<float> tb{reinterpret_cast<const float*>(a.tables), reinterpret_cast<const float*>(a.tables) + kOffRA};
+  const unsigned long long nrec = min(gst->cursor[1], a.rec_cap[1]);
+  const unsigned int epoch = gst->epoch;
+  const NcsRec<float>* evlog = reinterpret_cast<const NcsRec<float>*>(a.rec[1]);
+  const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
+  mlp_setup(sm, static_cast<const MlpParams*>(a.mlp));
+  unsigned int phase = 0;
+  const unsigned long long nchunk = (nrec + kMlpRows - 1) / kMlpRows;
+  for (unsigned long long c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const unsigned long long kk = c * kMlpRows + threadIdx.x;
+    NcsRec<float> rec;
+    bool valid = kk < nrec;
+    if (valid) {
+      rec = evlog[kk];
+      valid = rec.stamp == epoch && a.tile_cnt[1][rec.tile] != 0;
+    }
+    const int ens = valid && kB ? (int)(rec.species >> 1) : 0;
+    const EnsArgs& E = ens_of<kB>(a, ens);
+    const EnsTime tm = time_of<kB>(E);
+    float x[3] = {0.0f, 0.0f, 0.0f}, lnchi = 0.0f, t = 0.0f;
+    if (valid) {
+      // the network's inputs: ln chi_e, s = S.zeta, logit of the level uniform
+      const SpeciesArgs& L = E.sp[rec.species & 1u];
+      const unsigned long long i = rec.i;
+      const V3<float> pn = mk<float>(ld<float>(L.px, i), ld<float>(L.py, i), ld<float>(L.pz, i));
+      const V3<float> S = mk<float>(ld<float>(L.s1, i), ld<float>(L.s2, i), ld<float>(L.s3, i));
+      float pmag = norm(pn);
+      pmag = pmag > 0.0f ? pmag : 1e-30f;
+      const V3<float> nn = (1.0f / pmag) * pn;
+      const V3<float> zeta = cross(nn, mk<float>(rec.ax, rec.ay, rec.az));
+      const Uni2 um = uniforms(E.seed, L.id[i], tm.step, 1u);
+      double td = log(um.u1) - log1p(-um.u1);
+      td = td < kCTLo ? kCTLo : (td > kCTHi ? kCTHi : td);
+      t = (float)td;
+      lnchi = logf(rec.chi);
+      mlp_features(lnchi, dot(S, zeta), t, x);
+    }
+    bool ok;
+    const float y = mlp_rows(sm, x, phase, &ok);
+    if (!ok) {
+      if (threadIdx.x == 0) atomicOr(&gst->status, QED_STATUS_TIMEOUT);
+      break;
+    }
+    if (valid) {
+      const unsigned long long grank = (unsigned long long)a.tile_pre[1][rec.tile] + rec.r_in;
+      const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
+      ncs_event<float>(rec, E, tb, tm.step, rank, births, a.flags, gst, true, mlp_base(lnchi, t) + 8.0f * y);
+    }
   }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const int ne = kB ? a.n_ens : 1;
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    const EnsArgs& E = ens_of<kB>(a, e);
-    volatile DevState* v = E.st;
-    const unsigned long long nbw = v->n_nbw, ncs = births ? v->n_ncs_tot : 0ull, surv = v->n_surv;
-    const unsigned long long processed = (E.sp[0].present ? v->n_live[0] : 0ull) +   // step-start counts
-                                         (E.sp[1].present ? v->n_live[1] : 0ull) +
-                                         (E.sp[2].present ? v->n_live[2] : 0ull);
-    for (int s = 0; s < 2; ++s) {
-      if (!E.sp[s].present) continue;
-      const unsigned long long nn = v->n_live[s] + nbw;
-      v->n_live[s] = nn > E.sp[s].cap ? E.sp[s].cap : nn;
-    }
-    if (E.sp[2].present) {
-      const unsigned long long nn = surv + ncs;
-      v->n_live[2] = nn > E.sp[2].cap ? E.sp[2].cap : nn;
-    }
-    v->next_id = v->next_id + 2ull * nbw + ncs;
-    atomicAdd(&gst->processed, processed);
-    if (E.user_stats) {
-      E.user_stats->n_processed += processed;
-      E.user_stats->n_ncs[0] += v->ev[0];
-      E.user_stats->n_ncs[1] += v->ev[1];
-      E.user_stats->n_nbw += nbw;
-      E.user_stats->n_range += v->ev[3];
-      E.user_stats->n_drop += v->ev[4];
-      E.user_stats->n_steps += 1;
-    }
-    if (v->ev[3]) atomicOr(&gst->status, QED_STATUS_TABLE_RANGE);
-    for (int q = 0; q < 6; ++q) v->ev[q] = 0;
-    v->n_nbw = 0; v->n_surv = 0; v->n_ncs_tot = 0;
-    if constexpr (kB) {
-      // the ensemble's clock: the same operations as the host forms of a single step
-      const double t = v->t + a.dt;
-      v->t = t;
-      v->step = v->step + 1;
-      v->t_rel = (float)(t - E.f.phi0);
-      v->t_mod = (float)fma(-kTwoPi, floor(t / kTwoPi), t);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile DevState* g = gst;
-    g->cursor[0] = 0; g->cursor[1] = 0;
-    g->done = 0;
-    g->epoch = g->epoch + 1;
-    __threadfence();
-  }
+  mlp_teardown(sm);
+  close_step<kB>(a, births);
 }
 
 // launch with the programmatic-dependent-launch attribute when pdl is set

@@ -86,8 +86,8 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
     set_error("qed_step_static: dt must be positive and finite");
     return QED_ERR_INVALID_ARG;
   }
-  if (flags & ~63u) {
-    set_error("qed_step_static: unknown flag bits 0x%x", flags & ~63u);
+  if (flags & ~127u) {
+    set_error("qed_step_static: unknown flag bits 0x%x", flags & ~127u);
     return QED_ERR_INVALID_ARG;
   }
   const qed_particles* all[3] = {e, pos, ph};
@@ -123,6 +123,10 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
     return QED_ERR_INVALID_ARG;
   }
   const qed_precision pr = prec < 0 ? QED_PREC_F64 : (qed_precision)prec;
+  {
+    const qed_status rm = check_mlp_flag(c, flags, pr, "qed_step_static");
+    if (rm != QED_OK) return rm;
+  }
   if (nbw_rec_bytes(pr) > kNbwRecMax || ncs_rec_bytes(pr) > kNcsRecMax) {
     set_error("qed_step_static: event record larger than the static layout assumes");
     return QED_ERR_INVALID_ARG;
@@ -146,6 +150,7 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
   a.fdt = (float)dt;
   a.flags = flags;
   a.tables = pr == QED_PREC_F64 ? (const void*)c->tab64 : (const void*)c->tab32;
+  a.mlp = (c->owner ? c->owner : c)->mlp;
   a.st = c->st;
   a.tile_cnt[0] = reinterpret_cast<unsigned int*>(b + kSoCntPh);
   a.tile_pre[0] = reinterpret_cast<unsigned int*>(b + kSoPrePh);

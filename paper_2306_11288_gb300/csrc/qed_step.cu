@@ -37,7 +37,12 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     if (ss.tev) cudaEventRecord(ss.tev[5], s);
   }
   k_scan<false><<<1, kScanThreads, 0, s>>>(a, 1);
-  launch_k(k_ncs_ev<R, false>, nb[2], kTile, s, pdl, a);
+  if constexpr (sizeof(R) == 4) {
+    if (a.flags & QED_F_MLP) launch_k(k_ncs_ev_mlp<false>, nb[2] * 2, kMlpRows, s, pdl, a);
+    else launch_k(k_ncs_ev<R, false>, nb[2], kTile, s, pdl, a);
+  } else {
+    launch_k(k_ncs_ev<R, false>, nb[2], kTile, s, pdl, a);
+  }
   if (ss.tev) cudaEventRecord(ss.tev[3], s);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
