@@ -243,6 +243,88 @@ def run_c4(q, torch, steps, warmup, tune_steps=2):
             "l2": "not flushed: every step streams > 1 GB of particle state (L2 is 129 MB)"}
 
 
+def _photon_spectrum(q, sp, nbins=48):
+    """photon dN/d(ln omega) and <xi> in the (x, y) detection basis, via qed_diag"""
+    import numpy as np
+    d = q.diag(sp, q.diag_spec(q.QED_DIAG_SPECTRUM, nbins, 1, 1.0, 3e4))
+    b = d["bins"][0]
+    return b[:, 0], b[:, 1:4] / np.maximum(b[:, :1], 1e-300), b[:, 4]
+
+
+def run_c5(q, torch, steps, n_train=100_000_000):
+    """Learned sampler: training on table-sampled rows, its ln u error against the table
+    sampler on held-out rows, the tensor-core evaluation rate, then the 1e6-electron
+    workload stepped with it and with the table path (same seeds): throughput of both and
+    the photon spectrum / polarisation of the learned run as pulls against the table run
+    (the comparison with the oracle is in the GPU tests)."""
+    import numpy as np
+    ctx = q.qed_init_tables()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    q.qed_mlp_train(ctx, n_train, 16384, seed=5)
+    train_s = time.time() - t0
+    rng = np.random.default_rng(77)
+    nr = 1_000_000
+    rows = np.stack([rng.uniform(math.log(1e-3), math.log(10.0), nr), rng.uniform(-1, 1, nr),
+                     rng.uniform(1e-7, 1 - 1e-7, nr)], 1).astype(np.float32)
+    x = torch.as_tensor(rows, device="cuda")
+    y_m = torch.empty(nr, device="cuda")
+    y_t = torch.empty(nr, device="cuda")
+    q.qed_mlp_target(ctx, x.data_ptr(), y_t.data_ptr(), nr)
+    q.qed_mlp_eval(ctx, x.data_ptr(), y_m.data_ptr(), nr)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(10):
+        q.qed_mlp_eval(ctx, x.data_ptr(), y_m.data_ptr(), nr)
+    ev1.record()
+    ev1.synchronize()
+    eval_rate = 10 * nr / (ev0.elapsed_time(ev1) * 1e-3)
+    err = (y_m - y_t).abs().cpu().numpy()
+    # the 1e6-electron workload with each sampler
+    flags = q.QED_F_NCS | q.QED_F_NBW | q.QED_F_VB | q.QED_F_SPIN
+    n = 1_000_000
+    res = {}
+    for name, extra in (("table", 0), ("learned", q.QED_F_MLP)):
+        sctx = q.qed_ctx_share(ctx)
+        sim = q.Simulation(c2_workload(n, 2), prec=q.QED_PREC_MIXED, ctx=sctx, cap_e=n + 4_000_000,
+                           cap_p=4_000_000, cap_ph=40 * n)
+        sim.run(PRE_STEPS, flags | extra)
+        torch.cuda.synchronize()
+        p0 = int(sim.stats[6].item())
+        ev0.record()
+        sim.run(steps, flags | extra)
+        ev1.record()
+        ev1.synchronize()
+        rate = (int(sim.stats[6].item()) - p0) / (ev0.elapsed_time(ev1) * 1e-3)
+        h, xi, cnt = _photon_spectrum(q, sim.ph)
+        res[name] = {"rate": rate, "h": h, "xi": xi, "cnt": cnt, "status": sim.status(),
+                     "counts": (sim.e.count(), sim.pos.count(), sim.ph.count())}
+        sim.close()
+        q.qed_destroy(sctx)
+    q.qed_destroy(ctx)
+    ht, hm = res["table"]["h"], res["learned"]["h"]
+    ok = (ht > 100) & (hm > 100)
+    pull_h = (hm - ht)[ok] / np.sqrt(hm + ht)[ok]
+    rel_h = np.abs(hm - ht)[ok] / ht[ok]
+    sig_xi = np.sqrt(1.0 / ht[ok] + 1.0 / hm[ok])
+    pull_xi = (res["learned"]["xi"][ok] - res["table"]["xi"][ok]) / sig_xi[:, None]
+    return {"train": {"samples": n_train, "batch": 16384, "seconds": train_s},
+            "ln_u_error_vs_table": {"rows": nr, "median": float(np.median(err)),
+                                    "p99": float(np.quantile(err, 0.99)), "max": float(err.max())},
+            "eval_rows_per_s": eval_rate,
+            "workload": "c2_focused_cp_a100_g2e4, 1e6 electrons", "steps": steps,
+            "rate_learned": res["learned"]["rate"], "rate_table": res["table"]["rate"],
+            "counts_learned": res["learned"]["counts"], "counts_table": res["table"]["counts"],
+            "photon_spectrum_pull_vs_table": {"bins": int(ok.sum()), "rms": float(np.sqrt(np.mean(pull_h ** 2))),
+                                              "max_abs": float(np.abs(pull_h).max()),
+                                              "max_rel_diff": float(rel_h.max()), "median_rel_diff": float(np.median(rel_h)),
+                                              "note": "same seeds: the two runs are correlated, pulls use independent errors"},
+            "stokes_pull_vs_table": {"rms": [float(v) for v in np.sqrt(np.mean(pull_xi ** 2, 0))],
+                                     "max_abs": [float(v) for v in np.abs(pull_xi).max(0)]},
+            "status": [res["table"]["status"], res["learned"]["status"]]}
+
+
 def run_diag(q, torch, sim, reps=5):
     """End-of-run observables on the final state: photon spectrum with the Stokes parameters
     in the (x, y) detection basis, electron spectrum with the mean spin (mixed layout reads
@@ -326,6 +408,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=20_000)
     ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--c5-steps", type=int, default=50,
+                    help="timed steps of the learned-sampler leg (0: skip)")
     ap.add_argument("--c4-steps", type=int, default=100,
                     help="timed steps of the 64-ensemble batch (0: skip)")
     ap.add_argument("--kernel-steps", type=int, default=20,
@@ -385,6 +469,7 @@ def main():
         sim64.close()
     diag = run_diag(q, torch, sim)
     c4 = run_c4(q, torch, args.c4_steps, args.warmup) if args.c4_steps > 0 else None
+    c5 = run_c5(q, torch, args.c5_steps) if args.c5_steps > 0 else None
     e2e = run_e2e(q, torch, sim, q.QED_PREC_MIXED, args.e2e_steps, flags)
 
     ms, parts = info["ms"], info["particles"]
@@ -437,6 +522,7 @@ def main():
         "e2e": e2e,
         "diag": diag,
         "c4": c4,
+        "c5": c5,
         "gpu_launches": 7 * args.steps,   # headline loop; per step: photon, lepton, 2 scans, pairs, refill, NCS
         "clocks": clk.summary(),
         "counts_after": {"e": info["final_counts"][0], "pos": info["final_counts"][1],

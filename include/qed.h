@@ -63,7 +63,8 @@ typedef enum { QED_PREC_F64 = 0, QED_PREC_MIXED = 1 } qed_precision;
 #define QED_F_NO_RECOIL 16u    /* test mode: emission changes the spin only, no photon born   */
 #define QED_F_DROP_PHOTONS 32u /* emitted photons are not stored (recoil is applied)          */
 #define QED_F_MLP 64u          /* NCS photon energy from the learned sampler (mixed path only;
-                                  the context or its owner must hold parameters: qed_mlp_*)  */
+                                  the context or its owner must hold parameters: qed_mlp_*);
+                                  events with chi_e outside [1e-3, 10] use the table sampler */
 
 /* Structure-of-arrays view of one species, caller-owned device memory.  Element i of
  * every array describes particle i.  Element types follow qed_precision (above):
@@ -359,7 +360,8 @@ qed_status qed_batch_destroy(qed_batch *b);
  * Parameter vector (4481 floats): w1[64][3], b1[64], w2[64][64], b2[64], w3[64], b3. */
 
 /* Trains on n_samples samples produced by the table sampler itself (ln chi_e uniform in
- * [ln 1e-3, ln 10], s uniform in [-1, 1], r uniform; target its mixture inverse CDF from the
+ * [ln 1e-3, ln 10], s uniform in [-1, 1], r uniform -- for 1/16 of the samples
+ * logit(r) uniform in [-38, 38] to cover the tails; target its mixture inverse CDF from the
  * FP32 tables), in batches of `batch`, with Adam and a cosine learning rate, from an
  * initialisation seeded by `seed`.  Syncs.  Errors: QED_ERR_INVALID_ARG (64 <= batch <=
  * 2^22, batch <= n_samples), QED_ERR_CUDA. */

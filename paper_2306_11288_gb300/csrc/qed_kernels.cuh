@@ -1110,9 +1110,10 @@ __global__ void __launch_bounds__(kMlpRows) k_ncs_ev_mlp(const __grid_constant__
   const unsigned int epoch = gst->epoch;
   const NcsRec<float>* evlog = reinterpret_cast<const NcsRec<float>*>(a.rec[1]);
   const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
+  const unsigned long long nchunk = (nrec + kMlpRows - 1) / kMlpRows;
+  if (blockIdx.x < nchunk) {   // blocks without events skip the tensor-core set-up
   mlp_setup(sm, static_cast<const MlpParams*>(a.mlp));
   unsigned int phase = 0;
-  const unsigned long long nchunk = (nrec + kMlpRows - 1) / kMlpRows;
   for (unsigned long long c = blockIdx.x; c < nchunk; c += gridDim.x) {
     const unsigned long long kk = c * kMlpRows + threadIdx.x;
     NcsRec<float> rec;
@@ -1151,10 +1152,13 @@ __global__ void __launch_bounds__(kMlpRows) k_ncs_ev_mlp(const __grid_constant__
     if (valid) {
       const unsigned long long grank = (unsigned long long)a.tile_pre[1][rec.tile] + rec.r_in;
       const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
-      ncs_event<float>(rec, E, tb, tm.step, rank, births, a.flags, gst, true, mlp_base(lnchi, t) + 8.0f * y);
+      // outside the trained chi_e range the table sampler (the fallback) draws the energy
+      const bool learned = rec.chi >= kMlpChiLo && rec.chi <= kMlpChiHi;
+      ncs_event<float>(rec, E, tb, tm.step, rank, births, a.flags, gst, learned, mlp_base(lnchi, t) + 8.0f * y);
     }
   }
   mlp_teardown(sm);
+  }
   close_step<kB>(a, births);
 }
 

@@ -1,7 +1,9 @@
 // qed_mlp.cu -- training and evaluation of the learned NCS photon-energy sampler.
 //
 // Training data: the table sampler itself.  A sample is (ln chi_e ~ U(ln 1e-3, ln 10),
-// s ~ U(-1, 1), r ~ U(0, 1)) with the target ln u = F^{-1}(r) of the spin mixture of
+// s ~ U(-1, 1), r ~ U(0, 1); for 1/16 of the samples the logit of r is drawn uniformly
+// over [-38, 38] instead, so that the rarely visited tails are fitted) with the
+// target ln u = F^{-1}(r) of the spin mixture of
 // Eq. Wspin2: F(y) = [w+ F+(y) + w- F-(y)] / (w+ + w-), w+- = (1 +- s)(A -+ B)/2, where
 // F+-(y) is the level at which the component's inverse-CDF table reaches y.  F+- and F^{-1}
 // are found by bisection on the tables (FP32).
@@ -61,7 +63,12 @@ __global__ void k_mlp_gen(const float* tables, unsigned long long seed, unsigned
     const float lnchi = kMlpLnChiLo + (kMlpLnChiHi - kMlpLnChiLo) * ((float)(o.c >> 8) * 0x1p-24f);
     const float s = 2.0f * ((float)(o.d >> 8) * 0x1p-24f) - 1.0f;
     const double r = ((double)(((uint64_t)(o.a >> 5) << 26) | (uint64_t)(o.b >> 6)) + 0.5) * 0x1p-53;
-    double td = log(r) - log1p(-r);
+    double td;
+    if ((o.c & 0xFFu) < 16u) {
+      td = kCTLo + (kCTHi - kCTLo) * r;   // 1/16 of the rows: the logit uniform over its range (tails)
+    } else {
+      td = log(r) - log1p(-r);            // the rest: the logit of a uniform level
+    }
     td = td < kCTLo ? kCTLo : (td > kCTHi ? kCTHi : td);
     const float t = (float)td;
     float x[3];

@@ -33,6 +33,7 @@ struct MlpParams {
 // input features and output transform (shared by training and inference)
 constexpr float kMlpLnChiLo = -6.907755279f;   // ln 1e-3
 constexpr float kMlpLnChiHi = 2.302585093f;    // ln 10
+constexpr float kMlpChiLo = 1e-3f, kMlpChiHi = 10.0f;   // trained range of chi_e
 __device__ __forceinline__ void mlp_features(float lnchi, float s, float t, float x[3]) {
   x[0] = (2.0f * lnchi - (kMlpLnChiLo + kMlpLnChiHi)) / (kMlpLnChiHi - kMlpLnChiLo);
   x[1] = s;

@@ -61,7 +61,7 @@ def test_tensor_core_eval_matches_numpy_network(ctx):
 
 
 def test_training_learns_the_table_sampler(ctx):
-    q.qed_mlp_train(ctx, 4_000_000, 8192, seed=3)
+    q.qed_mlp_train(ctx, 20_000_000, 16384, seed=3)
     rows = _rows(20000, 11)
     got = q.mlp_apply(ctx, rows, "eval")
     tgt = q.mlp_apply(ctx, rows, "target")
@@ -76,7 +76,7 @@ def _spectrum(ph, bins):
     return h, h3
 
 
-def test_step_with_learned_sampler(ctx):
+def test_step_with_learned_sampler(ctx, orc):
     # needs the parameters of the previous test (module order)
     n = 8000
     out = {}
@@ -97,3 +97,13 @@ def test_step_with_learned_sampler(ctx):
     m = (ht > 300) & (hm > 300)
     xt, xm = h3t[m] / ht[m], h3m[m] / hm[m]
     assert np.all(np.abs(xt - xm) <= 4.0 * np.sqrt(1.0 / ht[m] + 1.0 / hm[m]) + 0.02)
+    # against the FP64 oracle (independent seed): the same bounds
+    import oracle
+    wl = workloads.c1(n=n, seed=22)
+    osim = oracle.Sim(orc, wl)
+    osim.run(450, q.QED_F_NCS | q.QED_F_SPIN)
+    ho, h3o = _spectrum(osim.state()["ph"], bins)
+    sig = np.sqrt(ho + hm + 1e-9)
+    assert np.all(np.abs(ho - hm) <= 4.0 * sig + 0.03 * ho + 2), (ho, hm)
+    m = (ho > 300) & (hm > 300)
+    assert np.all(np.abs(h3o[m] / ho[m] - h3m[m] / hm[m]) <= 4.0 * np.sqrt(1.0 / ho[m] + 1.0 / hm[m]) + 0.02)
