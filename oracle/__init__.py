@@ -25,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 F_NCS, F_NBW, F_VB, F_SPIN, F_NO_RECOIL, F_DROP_PHOTONS = 1, 2, 4, 8, 16, 32
+F_LL, F_MLL, F_MBMT = 128, 256, 512   # radiative pusher: LL, quantum-corrected LL, radiative T-BMT
 FIELD_NONE, FIELD_UNIFORM, FIELD_PLANE, FIELD_GAUSS, FIELD_GRID2D = 0, 1, 2, 3, 4
 
 
@@ -89,6 +90,7 @@ def lib():
             L.or_nbw_invcdf.argtypes = [C.c_void_p, C.c_int, d, d]
             L.or_nbw_invcdf.restype = d
             L.or_vb_m.argtypes = [C.c_void_p, d, pd]
+            L.or_rr_funcs.argtypes = [C.c_void_p, d, pd]
             L.or_scorer_gi_prime.argtypes = [d]
             L.or_scorer_gi_prime.restype = d
             L.or_field.argtypes = [C.POINTER(Fields), d, d, d, d, pd, pd]
@@ -230,6 +232,12 @@ class Oracle:
     def vb_m(self, chig):
         o = np.zeros(2)
         self.L.or_vb_m(self.ctx, float(chig), _dp(o))
+        return o
+
+    def rr_funcs(self, chi):
+        """q(chi), psi1, psi2, psi3 of the radiative pusher (Sec. III A, B)"""
+        o = np.zeros(4)
+        self.L.or_rr_funcs(self.ctx, float(chi), _dp(o))
         return o
 
     def ncs_F(self, u, chi, n, a, Si, Sf):

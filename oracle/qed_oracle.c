@@ -67,6 +67,7 @@ struct or_ctx {
   double t0s[NBX], t3s[NBX];                    /* T0, T3 times exp(8/(3chi_g))   */
   double by[2][NBX][NBT], bd[2][NBX][NBT];      /* NBW half inverse CDF: ln delta */
   double mpar[NV], mperp[NV];                   /* VB M_par, M_perp               */
+  double rr[4][NR];                             /* q, psi1/chi^3, psi2/chi^3, psi3/chi^3 */
   uint64_t next_id;
   uint64_t nlog, logcap;
   uint64_t *log_id; uint32_t *log_step; double *log_margin;
@@ -389,6 +390,35 @@ static void or_build_ncs(or_ctx *c) {
       A += sa * NCS_H * 0.5; B += sb * NCS_H * 0.5;
     }
     c->ra[i] = A / chi; c->rb[i] = B / chi;
+    /* radiative pusher functions on the same nodes (Sec. III A, B):
+     *   q(chi) = I_QED / I_C, the quantum radiated power over the classical one,
+     *     I_QED = alpha/(sqrt3 pi xi_L) int du u/(1+u) [(2+2u+u^2)K23 - (1+u)IntK13]/(1+u)^3
+     *     (photon energy omega = gamma u/(1+u) times the rate of Eq. Wspin2, spin-averaged),
+     *     I_C = (2/3) alpha chi^2 / xi_L  =>  q = sqrt3/(2 pi chi^2) int du (...);
+     *   psi1 = int du u'' K23(u'), psi3 = int du u'' K13(u'),
+     *   psi2 = int du u'' IntK13(u') - psi1,  u'' = u^2/(1+u)^3  (Eq. spin1's legend).
+     * Below v0 every density is O(u'^{4/3}) or smaller: no tail term. */
+    double I[4] = {0, 0, 0, 0};
+    for (int p = 0; p < NCS_NP; ++p) {
+      double s4[4] = {0, 0, 0, 0};
+      for (int k = 0; k < 8; ++k) {
+        const double *kk = ks + (size_t)(p * 8 + k) * 3;
+        double upk = up[p * 8 + k], u = 1.5 * chi * upk, em = exp(-upk), qq = 1.0 + u;
+        double jac = 1.5 * chi * upk, upp = u * u / (qq * qq * qq);
+        double fa, fb;
+        or_ncs_density(chi, upk, kk, &fa, &fb);
+        s4[0] += GL8W[k] * fa * u / qq;
+        s4[1] += GL8W[k] * jac * upp * kk[1] * em;
+        s4[2] += GL8W[k] * jac * upp * kk[2] * em;
+        s4[3] += GL8W[k] * jac * upp * kk[0] * em;
+      }
+      for (int j = 0; j < 4; ++j) I[j] += s4[j] * NCS_H * 0.5;
+    }
+    double chi3 = chi * chi * chi;
+    c->rr[0][i] = sqrt(3.0) / (2.0 * OR_PI * chi * chi) * I[0];
+    c->rr[1][i] = I[1] / chi3;
+    c->rr[2][i] = (I[2] - I[1]) / chi3;
+    c->rr[3][i] = I[3] / chi3;
   }
 
   /* inverse CDF tables: component 0 = spin projection s=+1 (a-b), 1 = s=-1 (a+b) */
@@ -612,6 +642,7 @@ const double *or_table(const or_ctx *c, int which, uint64_t *len) {
     case 3: *len = 2 * NBX; return c->t0s;
     case 4: *len = 4 * NBX * NBT; return &c->by[0][0][0];
     case 5: *len = 2 * NV; return c->mpar;
+    case 6: *len = 4 * NR; return &c->rr[0][0];
   }
   *len = 0;
   return NULL;
@@ -638,6 +669,16 @@ double or_nbw_invcdf(const or_ctx *c, int comp, double chig, double t) {
   double ht = (BT_HI - BT_LO) / (NBT - 1);
   return or_table2d(&c->by[comp][0][0], &c->bd[comp][0][0], NBX, NBT, X, (t - BT_LO) / ht, ht);
 }
+/* q and psi1..3 at chi from the tables (4-point Lagrange in ln chi).  Below chi_min:
+ * q = 1 (its classical limit) and psi_i = chi^3 times the first node's psi_i/chi^3
+ * (the psi's go as chi^3 for chi -> 0); above chi_max the caller clamps chi. */
+void or_rr_funcs(const or_ctx *c, double chi, double out[4]) {
+  double X = (log(chi) - R_LO) / ((R_HI - R_LO) / (NR - 1));
+  double chi3 = chi * chi * chi;
+  out[0] = chi < OR_CHI_MIN ? 1.0 : or_lagrange4(c->rr[0], NR, X);
+  for (int j = 1; j < 4; ++j) out[j] = chi3 * or_lagrange4(c->rr[j], NR, X);
+}
+
 void or_vb_m(const or_ctx *c, double chig, double out[2]) {
   if (chig < OR_VB_MIN) { out[0] = 4.0; out[1] = 7.0; return; }
   double X = (log(chig) - V_LO) / ((V_HI - V_LO) / (NV - 1));
@@ -974,6 +1015,63 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
   cross3(pp, sig, ppxs);
   double pn[3];
   for (int k = 0; k < 3; ++k) pn[k] = pm[k] + ppxs[k] + hq * E[k];
+  /* Radiative pusher (Sec. III A "Algorithms of the Radiative Pusher" and Sec. III B
+   * radiative T-BMT).  Readings: the radiation force and the radiative spin term are
+   * evaluated once, at time n, with the fields at x^n and the time-centred momentum
+   * pb = (p^{n-1/2} + p_L^{n+1/2})/2 of the Boris step; the LL force keeps the second and
+   * third terms of Eq. eq1-1 (the field-derivative term is dropped: the paper notes the
+   * last two dominate in ultra-intense fields) with 1/gamma restored on E(p.E) as in
+   * Eq. eq1; the third term is written through chi: gamma p[(E+beta x B)^2-(beta.E)^2] =
+   * chi^2 beta / xi_L^2; n_B = beta x a is taken as the unit vector n x a. */
+  double rs_P = 0, rs_psi[3] = {0, 0, 0}, rs_be[3] = {0, 0, 0}, rs_z[3] = {0, 0, 0};
+  int rs_on = 0;
+  if (flags & (OR_F_LL | OR_F_MLL | OR_F_MBMT)) {
+    double pb[3] = {0.5 * (p0[0] + pn[0]), 0.5 * (p0[1] + pn[1]), 0.5 * (p0[2] + pn[2])};
+    double gb = sqrt(1.0 + dot3(pb, pb));
+    double pbm = norm3(pb);
+    double be[3] = {pb[0] / gb, pb[1] / gb, pb[2] / gb};
+    double chi = 0.0, v[3] = {0, 0, 0}, vm = 0.0, nb[3] = {0, 0, 0};
+    if (pbm > 0.0) {
+      for (int k = 0; k < 3; ++k) nb[k] = pb[k] / pbm;
+      double nE = dot3(nb, E), pxB[3];
+      cross3(pb, B, pxB);
+      for (int k = 0; k < 3; ++k) v[k] = gb * (E[k] - nb[k] * nE) + pxB[k];
+      vm = norm3(v);
+      chi = OR_XIL * sqrt(vm * vm + nE * nE);
+    }
+    double chit = chi;
+    if (chit > OR_CHI_MAX) { chit = OR_CHI_MAX; if (st) st->n_range++; }
+    double fn[4] = {1.0, 0, 0, 0};
+    if (chit > 0.0) or_rr_funcs(c, chit, fn);
+    if (flags & (OR_F_LL | OR_F_MLL)) {
+      double qf = (flags & OR_F_MLL) ? fn[0] : 1.0;
+      double ExB[3], Bxp[3], BxBxp[3];
+      cross3(E, B, ExB);
+      cross3(B, pb, Bxp);
+      cross3(B, Bxp, BxBxp);
+      double pE = dot3(pb, E);
+      double c2 = 2.0 / 3.0 * OR_ALPHA * OR_XIL, c3 = 2.0 / 3.0 * OR_ALPHA / OR_XIL * chi * chi;
+      for (int k = 0; k < 3; ++k) {
+        double F = qf * (c2 * (ExB[k] + BxBxp[k] / gb + E[k] * pE / gb) - c3 * be[k]);
+        pn[k] += F * dt;
+      }
+    }
+    if ((flags & OR_F_MBMT) && vm > 0.0 && chi > 0.0) {
+      double sq = q > 0 ? 1.0 : -1.0;
+      double a[3] = {sq * v[0] / vm, sq * v[1] / vm, sq * v[2] / vm};
+      cross3(nb, a, rs_z);
+      rs_P = OR_ALPHA / (sqrt(3.0) * OR_PI * gb * OR_XIL);
+      for (int k = 0; k < 3; ++k) { rs_psi[k] = fn[k + 1]; rs_be[k] = be[k]; }
+      rs_on = 1;
+    }
+  }
+  /* radiative T-BMT half kick: S += dt/2 (dS/dt)_R, (dS/dt)_R = -P[psi1 S + psi2 (S.beta)
+   * beta + psi3 n_B] (Eq. spin1) */
+  if (rs_on) {
+    double sb = dot3(S, rs_be);
+    for (int k = 0; k < 3; ++k)
+      S[k] += 0.5 * dt * (-rs_P * (rs_psi[0] * S[k] + rs_psi[1] * sb * rs_be[k] + rs_psi[2] * rs_z[k]));
+  }
   /* T-BMT (reading: beta, gamma from the mean of p^{n-1/2}, p^{n+1/2};
      dS/dt = q S x Omega as implied by t = q dt Omega / 2) */
   if (flags & OR_F_SPIN) {
@@ -996,7 +1094,12 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
     cross3(S1, ov, s1xo);
     for (int k = 0; k < 3; ++k) S[k] += s1xo[k];
   }
-  /* position with the pre-QED p^{n+1/2} */
+  if (rs_on) {
+    double sb = dot3(S, rs_be);
+    for (int k = 0; k < 3; ++k)
+      S[k] += 0.5 * dt * (-rs_P * (rs_psi[0] * S[k] + rs_psi[1] * sb * rs_be[k] + rs_psi[2] * rs_z[k]));
+  }
+  /* position with the pre-QED p^{n+1/2} (after the radiation force when it is on) */
   double g1 = sqrt(1.0 + dot3(pn, pn));
   for (int k = 0; k < 3; ++k) x[k] += dt * pn[k] / g1;
   int emitted = 0;

@@ -28,6 +28,9 @@ extern "C" {
 #define OR_F_SPIN       8u   /* T-BMT precession (Sec. III B, Eq. bmteqn)       */
 #define OR_F_NO_RECOIL 16u   /* test mode: emission leaves p unchanged, no photon */
 #define OR_F_DROP_PHOTONS 32u /* emitted photons are not stored (recoil kept)  */
+#define OR_F_LL       128u   /* classical Landau-Lifshitz radiation reaction (Eq. eq1-1) */
+#define OR_F_MLL      256u   /* quantum-corrected LL: q(chi) F_RR,classical (Sec. III A) */
+#define OR_F_MBMT     512u   /* radiative T-BMT (Eq. spin1); needs OR_F_SPIN        */
 
 /* --- particle arrays (structure of arrays, caller-owned) -------------------- */
 typedef struct {
@@ -90,6 +93,8 @@ double or_ncs_invcdf(const or_ctx *c, int comp, double chi, double t); /* ln u *
 void or_nbw_rates(const or_ctx *c, double chig, double out[2]);     /* T0, T3   */
 double or_nbw_invcdf(const or_ctx *c, int comp, double chig, double t); /* ln d */
 void or_vb_m(const or_ctx *c, double chig, double out[2]);          /* M_par, M_perp */
+/* radiative pusher functions at chi (Sec. III A, B): out = {q, psi1, psi2, psi3} */
+void or_rr_funcs(const or_ctx *c, double chi, double out[4]);
 double or_scorer_gi_prime(double y);
 void or_field(const or_fields *f, double x, double y, double z, double t,
               double E[3], double B[3]);
@@ -101,7 +106,7 @@ void or_nbw_G(const or_ctx *c, double delta, double omega, double chig,
               const double ap[3], const double bp[3], const double vp[3],
               const double Sp[3], const double Sm[3], double G[4]);
 /* raw table access for pins: which = 0 K, 1 ncs rate, 2 ncs inv, 3 nbw rate,
-   4 nbw inv, 5 vb */
+   4 nbw inv, 5 vb, 6 radiative pusher (q, psi1/chi^3, psi2/chi^3, psi3/chi^3) */
 const double *or_table(const or_ctx *c, int which, uint64_t *len);
 
 #ifdef __cplusplus
