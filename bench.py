@@ -120,14 +120,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def run_gpu_path(q, torch, wl, prec, steps, warmup, flush, flags, kernel_steps):
+def run_gpu_path(q, torch, wl, prec, steps, warmup, flush, flags, kernel_steps, pre=PRE_STEPS, caps=None):
     """Pre-run, warm up, time `steps` steps (the headline), then `kernel_steps` more steps
     with the library's per-kernel timing on (kernels serialised, event records and a sync
     inside every step, so they are kept out of the headline loop)."""
     n = len(wl["e"]["id"])
-    sim = q.Simulation(wl, prec=prec, cap_e=n + 4_000_000, cap_p=4_000_000, cap_ph=40 * n)
+    caps = caps or {"cap_e": n + 4_000_000, "cap_p": 4_000_000, "cap_ph": 40 * n}
+    sim = q.Simulation(wl, prec=prec, **caps)
     stream = torch.cuda.current_stream()
-    sim.run(PRE_STEPS, flags)
+    sim.run(pre, flags)
     sim.run(warmup, flags)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -166,6 +167,73 @@ def run_gpu_path(q, torch, wl, prec, steps, warmup, flush, flags, kernel_steps):
     kinfo.update({"kernel_ms": kms, "kernel_steps": ksteps})
     info["kern"] = kinfo
     return sim, info
+
+
+C3_N, C3_PRE = 30_000_000, 20
+C3_GRID_BYTES = 6 * 4096 * 2048 * 4   # the six FP32 Yee components
+
+
+def run_c3(q, torch, steps, warmup, flush, f64_steps, kernel_steps):
+    """Grid-gathered fields: 3e7 electrons (gamma0 = 4000, tile-sorted) in a 4096 x 2048
+    FP32 Yee snapshot of an a0 = 150 pulse reflected off a dense slab, TSC gather, NCS + NBW
+    with spins; dt = T0/64.  C3_PRE untimed steps populate photons, then the same timing as
+    the headline (L2 flushed before every step; the grid alone is 201 MB > L2)."""
+    import workloads
+    wl = workloads.c3(n=C3_N, seed=3)
+    flags = q.QED_F_NCS | q.QED_F_NBW | q.QED_F_VB | q.QED_F_SPIN
+    caps = {"cap_e": C3_N + 4_000_000, "cap_p": 4_000_000, "cap_ph": 60_000_000}
+    out = {"workload": "c3_grid_4096x2048_yee_tsc_a150_g4000", "electrons": C3_N, "pre_steps": C3_PRE,
+           "unit": "particle-steps/s"}
+    b = BYTES["mixed"]
+    for name, prec, nsteps in (("mixed", q.QED_PREC_MIXED, steps), ("f64", q.QED_PREC_F64, f64_steps)):
+        if nsteps <= 0:
+            continue
+        sim, info = run_gpu_path(q, torch, wl, prec, nsteps, warmup, flush, flags,
+                                 kernel_steps if name == "mixed" else 0, pre=C3_PRE, caps=caps)
+        v = info["particles"] / (info["ms"] * 1e-3)
+        r = {"value": v, "ms_per_step": info["ms"] / nsteps, "steps": nsteps, "status": info["status"],
+             "counts_after": info["final_counts"]}
+        kn = info["kern"]
+        if name == "mixed" and kn["kernel_steps"]:
+            ks = kn["kernel_steps"]
+            k_ph_ms, k_lep_ms, k_ev_ms = kn["kernel_ms"]
+            lep_bytes = kn["lep_units"] * b["lep"] + kn["ncs_births"] * b["ncs_birth"] + ks * C3_GRID_BYTES
+            ph_bytes = kn["ph_units"] * b["ph"] + kn["nbw_births"] * b["nbw_birth"]
+            r["kernels"] = {"steps": ks, "k_lepton_ms": k_lep_ms / ks, "k_photon_ms": k_ph_ms / ks,
+                            "event_kernels_ms": k_ev_ms / ks,
+                            "k_lepton_GBs": lep_bytes / (k_lep_ms * 1e-3) / 1e9 if k_lep_ms else None,
+                            "k_photon_GBs": ph_bytes / (k_ph_ms * 1e-3) / 1e9 if k_ph_ms else None,
+                            "leptons_per_launch": kn["lep_units"] / ks, "photons_per_launch": kn["ph_units"] / ks,
+                            "bytes_note": "k_lepton counts 104 B per lepton plus the whole 201 MB grid once"}
+        out[name] = r
+        sim.close()
+    if "mixed" in out and "f64" in out:
+        out["speedup_mixed"] = out["mixed"]["value"] / out["f64"]["value"]
+    return out
+
+
+def run_rr(q, torch, steps, warmup, flush, kernel_steps):
+    """Radiative pusher (deterministic radiation reaction instead of the NCS Monte Carlo):
+    the 1e6-electron focused-pulse workload with the quantum-corrected LL force and the
+    radiative T-BMT (QED_F_MLL | QED_F_MBMT | QED_F_SPIN), mixed and FP64 paths; only
+    electrons stream (104 B / 152 B per particle-step)."""
+    flags = q.QED_F_MLL | q.QED_F_MBMT | q.QED_F_SPIN
+    n = 1_000_000
+    caps = {"cap_e": n, "cap_p": 16, "cap_ph": 16}
+    out = {"workload": "c2_focused_cp_a100_g2e4, 1e6 electrons, MLL + radiative T-BMT", "unit": "particle-steps/s"}
+    for name, prec, nst, bpp in (("mixed", q.QED_PREC_MIXED, steps, 104), ("f64", q.QED_PREC_F64, steps, 152)):
+        sim, info = run_gpu_path(q, torch, c2_workload(n, 2), prec, nst, warmup, flush, flags, kernel_steps,
+                                 caps=caps)
+        kn = info["kern"]
+        ks = max(kn["kernel_steps"], 1)
+        k_lep_ms = kn["kernel_ms"][1]
+        out[name] = {"value": info["particles"] / (info["ms"] * 1e-3), "ms_per_step": info["ms"] / nst,
+                     "k_lepton_ms": k_lep_ms / ks,
+                     "k_lepton_GBs": kn["lep_units"] * bpp / (k_lep_ms * 1e-3) / 1e9 if k_lep_ms else None,
+                     "status": info["status"]}
+        sim.close()
+    out["speedup_mixed"] = out["mixed"]["value"] / out["f64"]["value"]
+    return out
 
 
 C4_PRE = 150   # the ensembles start 150 steps before the beam centres reach the focus
@@ -412,6 +480,12 @@ def main():
                     help="timed steps of the learned-sampler leg (0: skip)")
     ap.add_argument("--c4-steps", type=int, default=100,
                     help="timed steps of the 64-ensemble batch (0: skip)")
+    ap.add_argument("--c3-steps", type=int, default=50,
+                    help="timed steps of the 3e7-electron grid workload (0: skip)")
+    ap.add_argument("--c3-f64-steps", type=int, default=10,
+                    help="timed steps of the grid workload on the FP64 path (0: skip)")
+    ap.add_argument("--rr-steps", type=int, default=50,
+                    help="timed steps of the radiative-pusher leg (0: skip)")
     ap.add_argument("--kernel-steps", type=int, default=20,
                     help="steps after the timed ones with per-kernel timing (roofline)")
     args = ap.parse_args()
@@ -468,6 +542,9 @@ def main():
                                   args.warmup, flush, flags, min(args.kernel_steps, args.steps))
         sim64.close()
     diag = run_diag(q, torch, sim)
+    c3 = (run_c3(q, torch, args.c3_steps, args.warmup, flush, args.c3_f64_steps, min(args.kernel_steps, 10))
+          if args.c3_steps > 0 else None)
+    rr = run_rr(q, torch, args.rr_steps, args.warmup, flush, min(args.kernel_steps, 10)) if args.rr_steps > 0 else None
     c4 = run_c4(q, torch, args.c4_steps, args.warmup) if args.c4_steps > 0 else None
     c5 = run_c5(q, torch, args.c5_steps) if args.c5_steps > 0 else None
     e2e = run_e2e(q, torch, sim, q.QED_PREC_MIXED, args.e2e_steps, flags)
@@ -521,7 +598,9 @@ def main():
                                    f"{PRE_STEPS} untimed"},
         "e2e": e2e,
         "diag": diag,
+        "c3": c3,
         "c4": c4,
+        "radiative_pusher": rr,
         "c5": c5,
         "gpu_launches": 7 * args.steps,   # headline loop; per step: photon, lepton, 2 scans, pairs, refill, NCS
         "clocks": clk.summary(),

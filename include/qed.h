@@ -65,6 +65,24 @@ typedef enum { QED_PREC_F64 = 0, QED_PREC_MIXED = 1 } qed_precision;
 #define QED_F_MLP 64u          /* NCS photon energy from the learned sampler (mixed path only;
                                   the context or its owner must hold parameters: qed_mlp_*);
                                   events with chi_e outside [1e-3, 10] use the table sampler */
+/* Radiative pusher (Sec. III A "Algorithms of the Radiative Pusher", Sec. III B radiative
+ * T-BMT): deterministic radiation reaction in place of the NCS Monte Carlo, for the regime
+ * where stochasticity does not matter (the paper disables it when NCS is on; combining
+ * either with QED_F_NCS is rejected).  Evaluated once per step at the time-centred
+ * momentum (p^{n-1/2} + p_L^{n+1/2})/2 of the Boris step and the fields at x^n:
+ *   QED_F_LL   : p^{n+1/2} = p_L^{n+1/2} + F_RR dt with the Landau-Lifshitz force of Eq.
+ *                eq1-1 (its second and third terms; the field-derivative term is dropped,
+ *                the paper notes the last two dominate in ultra-intense fields);
+ *   QED_F_MLL  : the same with q(chi) F_RR, q = I_QED/I_C the quantum/classical radiated
+ *                power ratio (tabulated from the NCS spectrum; q = 1 below chi = 1e-4);
+ *   QED_F_MBMT : half kicks S += dt/2 (dS/dt)_R before and after the T-BMT rotation,
+ *                (dS/dt)_R = -P[psi1 S + psi2 (S.beta) beta + psi3 n_B] (Eq. spin1),
+ *                n_B = n x a_hat; with QED_F_SPIN this is the paper's M-BMT, alone it is
+ *                the radiative term without precession.  S is then a mean polarisation
+ *                (|S| <= 1), not a unit vector. */
+#define QED_F_LL 128u
+#define QED_F_MLL 256u
+#define QED_F_MBMT 512u
 
 /* Structure-of-arrays view of one species, caller-owned device memory.  Element i of
  * every array describes particle i.  Element types follow qed_precision (above):
@@ -185,9 +203,12 @@ qed_status qed_get_next_id(qed_ctx *ctx, uint64_t *next_id, void *stream);
  * and counter = (id_lo, id_hi, step, stream index).
  * e, pos, ph may be NULL (an absent species); all given sets share one precision.
  * dev_stats (device memory, optional) accumulates counters.
+ *   with QED_F_LL / QED_F_MLL / QED_F_MBMT the radiative pusher (see the flags) acts
+ *     between the Boris push and the position update, and NCS is off.
  * Errors: QED_ERR_INVALID_ARG (dt <= 0 or not finite, precision mismatch, unknown
- * field kind, NULL grid arrays, NBW without lepton arrays), QED_ERR_NOT_INITIALIZED,
- * QED_ERR_CUDA (launch failure). */
+ * field kind, NULL grid arrays, NBW without lepton arrays, unknown flag bits, the
+ * radiative pusher together with QED_F_NCS, QED_F_LL with QED_F_MLL),
+ * QED_ERR_NOT_INITIALIZED, QED_ERR_CUDA (launch failure). */
 qed_status qed_step(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed_particles *ph,
                     const qed_fields *f, double t, double dt, uint64_t seed, uint32_t step,
                     uint32_t flags, qed_step_stats *dev_stats, void *stream);
@@ -246,7 +267,9 @@ qed_status qed_get_timing(qed_ctx *ctx, double ms[3], uint64_t *steps);
  *          [ln 1e-2, ln 1e3];
  *        4 NBW half inverse CDF: ln delta then d(ln delta)/dt, [2][2 xi3' = +1,-1][256 chi_g]
  *          [256 t], t = ln(level of the half distribution) in [-38, 0];
- *        5 VB M_par then M_perp, [2][1024] on ln chi_g in [ln 1e-3, ln 1e3].
+ *        5 VB M_par then M_perp, [2][1024] on ln chi_g in [ln 1e-3, ln 1e3];
+ *        6 radiative pusher q(chi), psi1/chi^3, psi2/chi^3, psi3/chi^3, [4][512] on the
+ *          grid of 1.
  * *len receives the element count; host may be NULL to query it; otherwise cap must be
  * >= the count.  Errors: QED_ERR_INVALID_ARG (bad which, cap too small). */
 qed_status qed_copy_table(qed_ctx *ctx, int which, double *host, uint64_t cap, uint64_t *len, void *stream);

@@ -20,6 +20,9 @@
  *   Boris ................. |p| conserved in pure B; plane-wave invariants
  *   T-BMT ................. g-2 precession closed form
  *   spin MC ............... mean one-step drift = radiative T-BMT (Eq. spin1)
+ *   radiative pusher ...... q, psi1..3 vs scipy quadrature and Mellin small-chi forms;
+ *                           one LL step radiates the Larmor power; Sokolov-Ternov
+ *                           build-up; MC mean = MLL + radiative T-BMT (Sec. III C)
  *   field models .......... Maxwell-like checks of the analytic fields (B = k x E)
  * parity unpinned: the exact shape of the paraxial Gaussian (a synthetic input model;
  * both sides implement the same first-order formula).

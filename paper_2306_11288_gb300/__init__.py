@@ -22,6 +22,7 @@ QED_ELECTRON, QED_POSITRON, QED_PHOTON = 0, 1, 2
 QED_PREC_F64, QED_PREC_MIXED = 0, 1
 QED_F_NCS, QED_F_NBW, QED_F_VB, QED_F_SPIN, QED_F_NO_RECOIL, QED_F_DROP_PHOTONS = 1, 2, 4, 8, 16, 32
 QED_F_MLP = 64
+QED_F_LL, QED_F_MLL, QED_F_MBMT = 128, 256, 512
 QED_STATUS_CAPACITY, QED_STATUS_TIMEOUT, QED_STATUS_TABLE_RANGE = 1, 2, 4
 FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
 

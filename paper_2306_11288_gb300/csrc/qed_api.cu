@@ -314,10 +314,25 @@ void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos,
   E.ff.zr = (float)(0.5 * f->w0 * f->w0);
   E.ff.inv_zr = f->w0 > 0.0 ? (float)(2.0 / (f->w0 * f->w0)) : 0.0f;
   E.ff.inv_w02 = f->w0 > 0.0 ? (float)(1.0 / (f->w0 * f->w0)) : 0.0f;
+  if (f->kind == QED_FIELD_GRID2D && f->dx > 0.0 && f->dy > 0.0) {
+    E.ff.gix = (float)(1.0 / f->dx);
+    E.ff.giy = (float)(1.0 / f->dy);
+    E.ff.gox = (float)(f->x0 / f->dx);
+    E.ff.goy = (float)(f->y0 / f->dy);
+  }
 }
 }  // namespace qedk
 
 namespace qedk {
+qed_status check_flag_bits(uint32_t flags, const char* who) {
+  if (flags & ~kAllFlags) FAIL(QED_ERR_INVALID_ARG, "%s: unknown flag bits 0x%x", who, flags & ~kAllFlags);
+  if ((flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT)) && (flags & QED_F_NCS))
+    FAIL(QED_ERR_INVALID_ARG, "%s: the radiative pusher (LL, MLL, MBMT) and the NCS Monte Carlo count the same "
+         "radiation: choose one", who);
+  if ((flags & QED_F_LL) && (flags & QED_F_MLL)) FAIL(QED_ERR_INVALID_ARG, "%s: QED_F_LL and QED_F_MLL exclude each other", who);
+  return QED_OK;
+}
+
 qed_status check_mlp_flag(const qed_ctx* c, uint32_t flags, qed_precision prec, const char* who) {
   if (!(flags & QED_F_MLP)) return QED_OK;
   if (prec != QED_PREC_MIXED) FAIL(QED_ERR_INVALID_ARG, "%s: the learned sampler runs on the mixed path only", who);
@@ -327,6 +342,17 @@ qed_status check_mlp_flag(const qed_ctx* c, uint32_t flags, qed_precision prec, 
 }
 
 qed_status check_fields(const qed_fields* f, const char* who) {
+  // every parameter the kind uses must be finite: a NaN or inf here would reach every
+  // particle of the step
+  bool finite = true;
+  if (f->kind == QED_FIELD_UNIFORM)
+    for (int k = 0; k < 3; ++k) finite = finite && std::isfinite(f->E[k]) && std::isfinite(f->B[k]);
+  if (f->kind == QED_FIELD_PLANE || f->kind == QED_FIELD_GAUSS)
+    finite = std::isfinite(f->a0) && std::isfinite(f->phi0) && std::isfinite(f->len) &&
+             (f->kind == QED_FIELD_PLANE || (std::isfinite(f->w0) && std::isfinite(f->zf)));
+  if (f->kind == QED_FIELD_GRID2D)
+    finite = std::isfinite(f->dx) && std::isfinite(f->dy) && std::isfinite(f->x0) && std::isfinite(f->y0);
+  if (!finite) FAIL(QED_ERR_INVALID_ARG, "%s: non-finite field parameter", who);
   switch (f->kind) {
     case QED_FIELD_NONE:
     case QED_FIELD_UNIFORM:
@@ -354,7 +380,10 @@ static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos
   if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_step: invalid context");
   if (!f) FAIL(QED_ERR_INVALID_ARG, "qed_step: fields is NULL");
   if (!(dt > 0.0) || !std::isfinite(dt)) FAIL(QED_ERR_INVALID_ARG, "qed_step: dt must be positive and finite");
-  if (flags & ~127u) FAIL(QED_ERR_INVALID_ARG, "qed_step: unknown flag bits 0x%x", flags & ~127u);
+  {
+    const qed_status rf = check_flag_bits(flags, "qed_step");
+    if (rf != QED_OK) return rf;
+  }
   const qed_particles* all[3] = {e, pos, ph};
   const qed_species want[3] = {QED_ELECTRON, QED_POSITRON, QED_PHOTON};
   int have = -1;
@@ -504,7 +533,8 @@ extern "C" qed_status qed_copy_table(qed_ctx* c, int which, double* host, uint64
     case 3: off = kOffT0; n = 2 * (size_t)kNBX; break;
     case 4: off = kOffBY; n = 4 * (size_t)kNBX * kNBT; break;
     case 5: off = kOffMP; n = 2 * (size_t)kNV; break;
-    default: FAIL(QED_ERR_INVALID_ARG, "qed_copy_table: which must be 0..5");
+    case 6: off = kOffRR; n = 4 * (size_t)kNR; break;
+    default: FAIL(QED_ERR_INVALID_ARG, "qed_copy_table: which must be 0..6");
   }
   *len = n;
   if (!host) return QED_OK;

@@ -75,7 +75,8 @@ static void launch_batch_t(const StepArgs& a, const int* nb, cudaStream_t s, cud
   k_bmap<<<1, kMapThreads, 0, s>>>(a);
   cudaEventRecord(fork, s);
   cudaStreamWaitEvent(side, fork, 0);
-  k_lepton<R, true, kSm><<<nb[1], kTile, 0, side>>>(a);
+  if (a.flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT)) k_lepton<R, true, kSm, true><<<nb[1], kTile, 0, side>>>(a);
+  else k_lepton<R, true, kSm><<<nb[1], kTile, 0, side>>>(a);
   cudaEventRecord(join, side);
   k_photon<R, true, kSm><<<nb[0], kTile, 0, s>>>(a);
   launch_k(k_scan<true>, 1, kScanThreads, s, pdl, a, 0);
@@ -208,7 +209,10 @@ extern "C" qed_status qed_batch_create(qed_ctx* ctx, const qed_ensemble* ens, in
   if (!ctx || !ctx->alive) BFAIL(QED_ERR_NOT_INITIALIZED, "qed_batch_create: invalid context");
   if (!ens || n_ens < 1 || n_ens > kMaxEns) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: n_ens must be in [1, %d]", kMaxEns);
   if (!(dt > 0.0) || !std::isfinite(dt)) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: dt must be positive and finite");
-  if (flags & ~127u) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: unknown flag bits 0x%x", flags & ~127u);
+  {
+    const qed_status rf = check_flag_bits(flags, "qed_batch_create");
+    if (rf != QED_OK) return rf;
+  }
   int prec = -1;
   unsigned long long tp = 1, tl = 1, cap_ph = 0, cap_l = 0;
   for (int i = 0; i < n_ens; ++i) {

@@ -46,7 +46,8 @@ constexpr size_t kOffCY = kOffMQ + kNV;                        // [2][kNCX][kNCT
 constexpr size_t kOffCD = kOffCY + 2 * (size_t)kNCX * kNCT;
 constexpr size_t kOffBY = kOffCD + 2 * (size_t)kNCX * kNCT;    // [2][kNBX][kNBT]
 constexpr size_t kOffBD = kOffBY + 2 * (size_t)kNBX * kNBT;
-constexpr size_t kTableLen = kOffBD + 2 * (size_t)kNBX * kNBT;
+constexpr size_t kOffRR = kOffBD + 2 * (size_t)kNBX * kNBT;    // [4][kNR] q, psi1..3 / chi^3
+constexpr size_t kTableLen = kOffRR + 4 * (size_t)kNR;
 // the 1-D rate tables are contiguous [kOffRA, kOffCY): staged to shared memory
 constexpr size_t kSmemRateLen = kOffCY - kOffRA;
 

@@ -28,6 +28,7 @@ struct SpeciesArgs {
 // float copies of per-step constants for the mixed path (no FP64 arithmetic in kernels)
 struct FloatConsts {
   float dt, inv_len, t_rel, t_mod, a0, w0, zf, zr, inv_zr, inv_w02;
+  float gix, giy, gox, goy;           // grid: 1/dx, 1/dy, x0/dx, y0/dy
 };
 
 // the arguments of one ensemble (a set of e-, e+, photons in one field)
@@ -95,6 +96,9 @@ qed_status check_fields(const qed_fields* f, const char* who);
 struct qed_ctx;
 namespace qedk {
 // QED_F_MLP needs the mixed path and trained (or set) sampler parameters
+// every flag bit the step kernels know; validation of flag combinations
+constexpr uint32_t kAllFlags = 1023u;
+qed_status check_flag_bits(uint32_t flags, const char* who);
 qed_status check_mlp_flag(const qed_ctx* c, uint32_t flags, qed_precision prec, const char* who);
 // occupancy-derived persistent grid sizes
 qed_status step_grid_sizes(qed_precision prec, int* nblk);

@@ -79,6 +79,48 @@ __device__ __forceinline__ R tsc_gather(const float* g, int nx, int ny, double X
   return acc;
 }
 
+// Mixed path: the same TSC gather with the cell coordinates in float (no FP64 arithmetic).
+// The cell coordinate carries an absolute error of about 2^-24 of its value (below 3e-4
+// of a cell on a 4096-cell axis); the TSC shape is continuous with a continuous slope
+// across cell boundaries, so this moves the gathered field by that much times its
+// gradient, whichever stencil the rounding selects.
+__device__ __forceinline__ int tsc_axis(float X, float w[3]) {
+  const float f = floorf(X + 0.5f);
+  const float d = X - f;
+  const float lo = 0.5f - d, hi = 0.5f + d;
+  w[0] = 0.5f * lo * lo;
+  w[1] = 0.75f - d * d;
+  w[2] = 0.5f * hi * hi;
+  return (int)f - 1;
+}
+__device__ __forceinline__ float tsc_sum(const float* g, int nx, int ny, int i0, int j0, const float* wx,
+                                         const float* wy) {
+  float acc = 0.0f;
+  if (i0 >= 0 && j0 >= 0 && i0 + 2 < nx && j0 + 2 < ny) {   // interior: the whole stencil is on the grid
+    const float* r = g + (size_t)j0 * nx + i0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      acc += wy[b] * (wx[0] * __ldg(r) + wx[1] * __ldg(r + 1) + wx[2] * __ldg(r + 2));
+      r += nx;
+    }
+    return acc;
+  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const int j = j0 + b;
+    if (j < 0 || j >= ny) continue;
+    float row = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int i = i0 + c;
+      if (i < 0 || i >= nx) continue;
+      row += wx[c] * __ldg(g + (size_t)j * nx + i);
+    }
+    acc += wy[b] * row;
+  }
+  return acc;
+}
+
 // ---- ensembles ------------------------------------------------------------------------
 // A launch steps one ensemble (kB = false: its arguments are the launch parameters a.e0)
 // or a batch of ensembles (kB = true: a.ens[e] in device memory, the clock of each in its
@@ -168,6 +210,17 @@ __device__ __forceinline__ EB<R> gather(const EnsArgs& E, const EnsTime& tm, dou
     r.E.y = f.circular ? g * sp : R(0);
     r.B.x = r.E.y;
     r.B.y = -r.E.x;
+  } else if (f.kind == QED_FIELD_GRID2D && sizeof(R) == 4) {
+    const float X = d2f_bits(x) * E.ff.gix - E.ff.gox, Y = d2f_bits(y) * E.ff.giy - E.ff.goy;
+    float wx0[3], wx1[3], wy0[3], wy1[3];
+    const int i0 = tsc_axis(X, wx0), ih = tsc_axis(X - 0.5f, wx1);
+    const int j0 = tsc_axis(Y, wy0), jh = tsc_axis(Y - 0.5f, wy1);
+    r.E.x = (R)tsc_sum(f.gEx, f.nx, f.ny, ih, j0, wx1, wy0);
+    r.E.y = (R)tsc_sum(f.gEy, f.nx, f.ny, i0, jh, wx0, wy1);
+    r.E.z = (R)tsc_sum(f.gEz, f.nx, f.ny, i0, j0, wx0, wy0);
+    r.B.x = (R)tsc_sum(f.gBx, f.nx, f.ny, i0, jh, wx0, wy1);
+    r.B.y = (R)tsc_sum(f.gBy, f.nx, f.ny, ih, j0, wx1, wy0);
+    r.B.z = (R)tsc_sum(f.gBz, f.nx, f.ny, ih, jh, wx1, wy1);
   } else if (f.kind == QED_FIELD_GRID2D) {
     const double X = (x - f.x0) / f.dx, Y = (y - f.y0) / f.dy;
     r.E.x = tsc_gather<R>(f.gEx, f.nx, f.ny, X - 0.5, Y);
@@ -251,7 +304,98 @@ struct Tabs {
     mq = lagrange4(s + (kOffMQ - kOffRA), kNV, X);
   }
   __device__ __forceinline__ void k(R x, R& k13, R& k23, R& ik) const { kfun(g, x, k13, k23, ik); }
+  // radiative pusher functions (read through L1/L2: used only with the radiative flags):
+  // q(chi) (1 below chi_min) and psi1..3 = chi^3 times the tabulated psi/chi^3
+  __device__ __forceinline__ void rr_funcs(R chi, R& qf, R& p1, R& p2, R& p3) const {
+    const R X = (f_log(chi) - R(kRLo)) * R((kNR - 1) / (kRHi - kRLo));
+    const R chi3 = chi * chi * chi;
+    qf = chi < R(kChiMin) ? R(1) : lagrange4(g + kOffRR, kNR, X);
+    p1 = chi3 * lagrange4(g + kOffRR + kNR, kNR, X);
+    p2 = chi3 * lagrange4(g + kOffRR + 2 * kNR, kNR, X);
+    p3 = chi3 * lagrange4(g + kOffRR + 3 * kNR, kNR, X);
+  }
 };
+
+// ---- radiative pusher (Sec. III A "Algorithms of the Radiative Pusher"; Sec. III B) ----
+// Evaluated once per step at the time-centred momentum pb = (p^{n-1/2} + p_L^{n+1/2})/2 of
+// the Boris step and the fields at x^n.  The LL force keeps the second and third terms of
+// Eq. eq1-1 (the field-derivative term is dropped), with 1/gamma on E(p.E) as in Eq. eq1;
+// its third term is written through chi: gamma p [(E + beta x B)^2 - (beta.E)^2] =
+// chi^2 beta / xi_L^2.  The radiative T-BMT term -P[psi1 S + psi2 (S.beta) beta + psi3 n_B]
+// (Eq. spin1), n_B = n x a_hat, is applied as two half kicks around the T-BMT rotation.
+template <typename R>
+struct RadSpin {
+  R P, p1, p2, p3;
+  V3<R> be, zeta;
+  bool on;
+};
+
+template <typename R>
+__device__ __forceinline__ void rad_push(const Tabs<R>& tb, uint32_t flags, R q, R dt, const EB<R>& f,
+                                         const V3<R>& p0, V3<R>& pn, RadSpin<R>& rs, bool& range) {
+  rs.on = false;
+  const V3<R> pb = R(0.5) * (p0 + pn);
+  const R pm2 = dot(pb, pb);
+  const R gb2 = R(1) + pm2;
+  const R inv_gb = f_rsqrt(gb2);
+  const R gb = gb2 * inv_gb;
+  const V3<R> be = inv_gb * pb;
+  R chi = R(0), vm2 = R(0);
+  V3<R> v = mk<R>(0, 0, 0), nb = mk<R>(0, 0, 0);
+  if (pm2 > R(0)) {
+    nb = f_rsqrt(pm2) * pb;
+    const R nE = dot(nb, f.E);
+    v = gb * (f.E - nE * nb) + cross(pb, f.B);
+    vm2 = dot(v, v);
+    if (sizeof(R) == 4) {
+      // FP64 island: gamma E_perp and p x B cancel (co-propagation)
+      const V3<R> a1 = gb * (f.E - nE * nb), a2 = cross(pb, f.B);
+      if (vm2 < R(1e-4) * (dot(a1, a1) + dot(a2, a2))) {
+        const double px = pb.x, py = pb.y, pz = pb.z;
+        const double G1 = sqrt(1.0 + px * px + py * py + pz * pz), pmd = sqrt(px * px + py * py + pz * pz);
+        const double nx = px / pmd, ny = py / pmd, nz = pz / pmd;
+        const double Ex = f.E.x, Ey = f.E.y, Ez = f.E.z, Bx = f.B.x, By = f.B.y, Bz = f.B.z;
+        const double ne = nx * Ex + ny * Ey + nz * Ez;
+        const double vx = G1 * (Ex - ne * nx) + (py * Bz - pz * By);
+        const double vy = G1 * (Ey - ne * ny) + (pz * Bx - px * Bz);
+        const double vz = G1 * (Ez - ne * nz) + (px * By - py * Bx);
+        v = mk<R>((R)vx, (R)vy, (R)vz);
+        vm2 = (R)(vx * vx + vy * vy + vz * vz);
+      }
+    }
+    const R c2 = vm2 + nE * nE;
+    chi = c2 > R(0) ? R(kXiL) * c2 * f_rsqrt(c2) : R(0);
+  }
+  R chit = chi;
+  if (chit > R(kChiMax)) { chit = R(kChiMax); range = true; }
+  R qf = R(1), p1 = R(0), p2 = R(0), p3 = R(0);
+  if (chit > R(0)) tb.rr_funcs(chit, qf, p1, p2, p3);
+  if (flags & (QED_F_LL | QED_F_MLL)) {
+    const R qq = (flags & QED_F_MLL) ? qf : R(1);
+    const V3<R> ExB = cross(f.E, f.B);
+    const V3<R> BxBxp = cross(f.B, cross(f.B, pb));
+    const R pE = dot(pb, f.E);
+    const R c2 = R(2.0 / 3.0 * kAlpha * kXiL), c3 = R(2.0 / 3.0 * kAlpha / kXiL) * chi * chi;
+    const V3<R> F = qq * (c2 * (ExB + inv_gb * BxBxp + (inv_gb * pE) * f.E) - c3 * be);
+    pn = pn + dt * F;
+  }
+  if ((flags & QED_F_MBMT) && vm2 > R(0) && chi > R(0)) {
+    const V3<R> av = (q * f_rsqrt(vm2)) * v;
+    rs.zeta = cross(nb, av);
+    rs.P = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) * inv_gb;
+    rs.p1 = p1; rs.p2 = p2; rs.p3 = p3;
+    rs.be = be;
+    rs.on = true;
+  }
+}
+
+// S += dt/2 (dS/dt)_R
+template <typename R>
+__device__ __forceinline__ void rad_spin_half(const RadSpin<R>& rs, R dt, V3<R>& S) {
+  const R sb = dot(S, rs.be);
+  const R h = R(-0.5) * dt * rs.P;
+  S = S + h * (rs.p1 * S + (rs.p2 * sb) * rs.be + rs.p3 * rs.zeta);
+}
 
 template <typename R>
 __device__ __forceinline__ void stage_rates(const R* g, R* s) {
@@ -330,6 +474,8 @@ __device__ __forceinline__ unsigned long long tile_log(bool flag, unsigned int t
 }
 
 template <typename R> struct Occ { static constexpr int v = sizeof(R) == 4 ? 4 : 2; };
+// the photon pass holds a second tile's records in registers
+template <typename R> struct OccPh { static constexpr int v = sizeof(R) == 4 ? 3 : 2; };
 
 // ---- programmatic dependent launch ------------------------------------------------------
 // The event kernels are launched as programmatic dependents of the kernel before them on
@@ -342,8 +488,60 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // ======================================================================================
 // photon streaming pass
 // ======================================================================================
+// A photon's input record.  The pass loads the next tile's records before it computes the
+// current tile (register double buffering), so the loads of one tile are in flight while
+// the previous one is computed: the pass's own loads hide behind its arithmetic instead of
+// stalling every warp of the block at the top of each tile.
+template <typename R>
+struct PhIn {
+  double x, y, z;
+  V3<R> k, xi;
+  R th;
+  uint64_t id;
+};
+
+template <typename R>
+__device__ __forceinline__ void ph_load(const SpeciesArgs& P, unsigned int i, bool live, PhIn<R>& v) {
+  if (live) {
+    v.x = P.x[i]; v.y = P.y[i]; v.z = P.z[i];
+    v.k = mk<R>(ld<R>(P.px, i), ld<R>(P.py, i), ld<R>(P.pz, i));
+    v.xi = mk<R>(ld<R>(P.s1, i), ld<R>(P.s2, i), ld<R>(P.s3, i));
+    v.th = ld<R>(P.theta, i);
+    v.id = P.id[i];
+  } else {
+    v.x = 0; v.y = 0; v.z = 0;
+    v.k = mk<R>(1, 0, 0);
+    v.xi = mk<R>(0, 0, 0);
+    v.th = 0;
+    v.id = 0;
+  }
+}
+
+// where a tile's photons are: ensemble, first slot of the thread, live flag
+struct PhTile {
+  int ens;
+  unsigned int i;
+  bool live;
+};
+
+template <bool kB>
+__device__ __forceinline__ PhTile ph_tile(const StepArgs& a, const unsigned int* s_off, unsigned long long n_one,
+                                          unsigned int tile) {
+  PhTile t;
+  t.ens = kB ? find_ens(s_off, a.n_ens, tile) : 0;
+  const EnsArgs& E = ens_of<kB>(a, t.ens);
+  const SpeciesArgs& P = E.sp[2];
+  const unsigned long long n = kB ? (P.present ? E.st->n_live[2] : 0ull) : n_one;
+  t.i = (tile - (kB ? s_off[t.ens] : 0u)) * kTile + threadIdx.x;   // capacity <= 2^32 - 256
+  t.live = t.i < (unsigned int)n;
+  return t;
+}
+
 template <typename R, bool kB, bool kSm>
-__global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(const __grid_constant__ StepArgs a) {
+  // single-ensemble launches double-buffer the records in registers; batched launches
+  // (whose tile-to-ensemble search needs the registers) load each tile at its top
+  constexpr bool kPf = !kB;
   pdl_trigger();
   __shared__ R s_rates[kSm ? kSmemRateLen : 1];
   __shared__ TileShared s_tile;
@@ -365,26 +563,37 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(const __grid_consta
   const unsigned int epoch = gst->epoch;
   const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.fdt;
   NbwRec<R>* evlog = reinterpret_cast<NbwRec<R>*>(a.rec[0]);
+  PhTile cur{0, 0u, false};
+  PhIn<R> in;
+  if (kPf && blockIdx.x < ntiles) {
+    cur = ph_tile<kB>(a, s_off, n_one, blockIdx.x);
+    ph_load<R>(ens_of<kB>(a, cur.ens).sp[2], cur.i, cur.live, in);
+  }
   for (unsigned int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int ens = kB ? find_ens(s_off, a.n_ens, tile) : 0;
+    PhTile nxt{0, 0u, false};
+    PhIn<R> in_n;
+    if constexpr (kPf) {
+      // the next tile's records, in flight while this tile is computed
+      const unsigned int tile_n = tile + gridDim.x;
+      if (tile_n < ntiles) nxt = ph_tile<kB>(a, s_off, n_one, tile_n);
+      ph_load<R>(ens_of<kB>(a, nxt.ens).sp[2], nxt.i, nxt.live, in_n);
+    } else {
+      cur = ph_tile<kB>(a, s_off, n_one, tile);
+      ph_load<R>(ens_of<kB>(a, cur.ens).sp[2], cur.i, cur.live, in);
+    }
+
+    const int ens = cur.ens;
     const EnsArgs& E = ens_of<kB>(a, ens);
     const EnsTime tm = time_of<kB>(E);
     DevState* st = E.st;
     const SpeciesArgs& P = E.sp[2];
-    const unsigned long long n = kB ? (P.present ? st->n_live[2] : 0ull) : n_one;
-    const unsigned int i = (tile - (kB ? s_off[ens] : 0u)) * kTile + threadIdx.x;   // capacity <= 2^32 - 256
-    const bool live = i < (unsigned int)n;
-    double x = 0, y = 0, z = 0;
-    V3<R> k = mk<R>(1, 0, 0), xi = mk<R>(0, 0, 0);
-    R th = 0;
-    uint64_t id = 0;
-    if (live) {
-      x = P.x[i]; y = P.y[i]; z = P.z[i];
-      k = mk<R>(ld<R>(P.px, i), ld<R>(P.py, i), ld<R>(P.pz, i));
-      xi = mk<R>(ld<R>(P.s1, i), ld<R>(P.s2, i), ld<R>(P.s3, i));
-      th = ld<R>(P.theta, i);
-      id = P.id[i];
-    }
+    const unsigned int i = cur.i;
+    const bool live = cur.live;
+    const double x = in.x, y = in.y, z = in.z;
+    const V3<R> k = in.k;
+    V3<R> xi = in.xi;
+    R th = in.th;
+    const uint64_t id = in.id;
     bool decay = false, range = false;
     const R om2 = dot(k, k);
     const R inv_om = f_rsqrt(om2);
@@ -452,14 +661,18 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_photon(const __grid_consta
       rec.chig = chig; rec.rmix = rmix; rec.p1x = P1.x; rec.p1y = P1.y; rec.p1z = P1.z;
       evlog[slot] = rec;
     }
+    if constexpr (kPf) {
+      cur = nxt;
+      in = in_n;
+    }
   }
 }
 
 // ======================================================================================
 // lepton streaming pass
 // ======================================================================================
-template <typename R, bool kB, bool kSm>
-__global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(const __grid_constant__ StepArgs a) {
+template <typename R, bool kB, bool kSm, bool kRad = false>
+__global__ void __launch_bounds__(kTile, kRad ? OccPh<R>::v : Occ<R>::v) k_lepton(const __grid_constant__ StepArgs a) {
   __shared__ R s_rates[kSm ? kSmemRateLen : 1];
   __shared__ TileShared s_tile;
   __shared__ unsigned int s_off[kB ? kMaxEns + 1 : 1];
@@ -514,7 +727,13 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(const __grid_consta
       const V3<R> tau = (hq * f_rsqrt(R(1) + dot(pm, pm))) * f.B;
       const V3<R> pp = pm + cross(pm, tau);
       const V3<R> sig = (R(2) * f_rcp(R(1) + dot(tau, tau))) * tau;
-      const V3<R> pn = pm + cross(pp, sig) + hq * f.E;
+      V3<R> pn = pm + cross(pp, sig) + hq * f.E;
+      RadSpin<R> rs;
+      rs.on = false;
+      if constexpr (kRad) {
+        rad_push<R>(tb, a.flags, q, dt, f, p, pn, rs, range);
+        if (rs.on) rad_spin_half<R>(rs, dt, S);
+      }
       // T-BMT with beta, gamma of the mean of p^{n-1/2} and p^{n+1/2}
       if (a.flags & QED_F_SPIN) {
         const V3<R> pa = R(0.5) * (p + pn);
@@ -530,6 +749,9 @@ __global__ void __launch_bounds__(kTile, Occ<R>::v) k_lepton(const __grid_consta
         const V3<R> ov = (R(2) * f_rcp(R(1) + dot(tv, tv))) * tv;
         const V3<R> S1 = S + cross(S, tv);
         S = S + cross(S1, ov);
+      }
+      if constexpr (kRad) {
+        if (rs.on) rad_spin_half<R>(rs, dt, S);
       }
       const R g12 = R(1) + dot(pn, pn);
       const R inv_g1 = f_rsqrt(g12);

@@ -86,9 +86,9 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
     set_error("qed_step_static: dt must be positive and finite");
     return QED_ERR_INVALID_ARG;
   }
-  if (flags & ~127u) {
-    set_error("qed_step_static: unknown flag bits 0x%x", flags & ~127u);
-    return QED_ERR_INVALID_ARG;
+  {
+    const qed_status rf = check_flag_bits(flags, "qed_step_static");
+    if (rf != QED_OK) return rf;
   }
   const qed_particles* all[3] = {e, pos, ph};
   const qed_species want[3] = {QED_ELECTRON, QED_POSITRON, QED_PHOTON};
@@ -114,13 +114,9 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
     set_error("qed_step_static: NBW needs e- and e+ sets");
     return QED_ERR_INVALID_ARG;
   }
-  if (f->kind < QED_FIELD_NONE || f->kind > QED_FIELD_GRID2D ||
-      ((f->kind == QED_FIELD_PLANE || f->kind == QED_FIELD_GAUSS) && !(f->len > 0.0)) ||
-      (f->kind == QED_FIELD_GAUSS && !(f->w0 > 0.0)) ||
-      (f->kind == QED_FIELD_GRID2D && (!f->gEx || !f->gEy || !f->gEz || !f->gBx || !f->gBy || !f->gBz ||
-                                       f->nx < 1 || f->ny < 1 || !(f->dx > 0) || !(f->dy > 0)))) {
-    set_error("qed_step_static: invalid field descriptor");
-    return QED_ERR_INVALID_ARG;
+  {
+    const qed_status rf = check_fields(f, "qed_step_static");
+    if (rf != QED_OK) return rf;
   }
   const qed_precision pr = prec < 0 ? QED_PREC_F64 : (qed_precision)prec;
   {

@@ -11,6 +11,13 @@ size_t ncs_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NcsRec
 // (forked after all earlier work on the caller's stream, joined before the lepton scan):
 // the lepton pass reads only particles below the counts of the step start, the pair
 // births of k_nbw_ev go above them, so the two chains are independent until k_ncs_ev.
+// the lepton pass: with the radiative pusher flags its kRad instantiation
+template <typename R>
+static void launch_lepton(const StepArgs& a, int grid, cudaStream_t s) {
+  if (a.flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT)) k_lepton<R, false, true, true><<<grid, kTile, 0, s>>>(a);
+  else k_lepton<R, false, true><<<grid, kTile, 0, s>>>(a);
+}
+
 template <typename R>
 static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, const StreamSet& ss) {
   const bool fork = ss.side != nullptr;
@@ -20,7 +27,7 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     cudaEventRecord(ss.fork, s);
     cudaStreamWaitEvent(ss.side, ss.fork, 0);
     if (ss.tev) cudaEventRecord(ss.tev[4], ss.side);
-    k_lepton<R, false, true><<<nb[1], kTile, 0, ss.side>>>(a);
+    launch_lepton<R>(a, nb[1], ss.side);
     if (ss.tev) cudaEventRecord(ss.tev[5], ss.side);
     cudaEventRecord(ss.join, ss.side);
   }
@@ -33,7 +40,7 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     cudaStreamWaitEvent(s, ss.join, 0);
   } else {
     if (ss.tev) cudaEventRecord(ss.tev[4], s);
-    k_lepton<R, false, true><<<nb[1], kTile, 0, s>>>(a);
+    launch_lepton<R>(a, nb[1], s);
     if (ss.tev) cudaEventRecord(ss.tev[5], s);
   }
   k_scan<false><<<1, kScanThreads, 0, s>>>(a, 1);

@@ -166,6 +166,32 @@ __global__ void k_ncs_rates(const Kv* kn, double* tab) {
     tab[kOffRA + i] = A / chi;
     tab[kOffRB + i] = B / chi;
   }
+  // Radiative pusher functions on the same nodes (Sec. III A, B):
+  //   q = I_QED / I_C: the spin-averaged radiated power (photon energy gamma u/(1+u) times
+  //   the A-density of Eq. Wspin2) over (2/3) alpha chi^2/xi_L, i.e. sqrt3/(2 pi chi^2)
+  //   int du u/(1+u) [(2+2u+u^2)K23 - (1+u)IntK13]/(1+u)^3;
+  //   psi1 = int du u'' K23(u'), psi3 = int du u'' K13(u'), psi2 = int du u'' IntK13(u') -
+  //   psi1 with u'' = u^2/(1+u)^3 (Eq. spin1's legend).  No tail below v0 (O(u'^{4/3})).
+  double s4[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int n = threadIdx.x; n < kVN; n += blockDim.x) {
+    const double up = exp(vnode(n)), u = 1.5 * chi * up, q = 1.0 + u, em = exp(-up);
+    const double wj = c_gl16w[n & 15] * 1.5 * chi * up * em * u * u / (q * q * q);
+    double fa, fb;
+    ncs_dens(chi, up, kn[n], fa, fb);
+    s4[0] += c_gl16w[n & 15] * fa * u / q;
+    s4[1] += wj * kn[n].k23;
+    s4[2] += wj * kn[n].ik;
+    s4[3] += wj * kn[n].k13;
+  }
+  double I[4];
+  for (int j = 0; j < 4; ++j) I[j] = block_sum(s4[j], sh) * 0.5 * kVH;
+  if (threadIdx.x == 0) {
+    const double chi3 = chi * chi * chi;
+    tab[kOffRR + i] = 1.7320508075688772935 / (2.0 * kPi * chi * chi) * I[0];
+    tab[kOffRR + kNR + i] = I[1] / chi3;
+    tab[kOffRR + 2 * kNR + i] = (I[2] - I[1]) / chi3;
+    tab[kOffRR + 3 * kNR + i] = I[3] / chi3;
+  }
 }
 
 // one block per (comp, chi row): node densities, panel integrals, cumulative sums,

@@ -9,7 +9,10 @@
    only on its id, the step and the seed) and compared one by one.  FP64 path: decisions
    exact except the oracle's logged near-ties, values within 1e-10.  Mixed path: values
    within 2e-5; decisions may differ only where float rounding moves the threshold,
-   bounded at 0.5 % of the sample."""
+   bounded at 0.5 % of the sample.
+3. The grid workload at its full size (3e7 electrons, 4096 x 2048 FP32 Yee grid, TSC
+   gather): the same sampled comparison, 12 steps in, drawn mostly from the particles
+   inside the reflected pulse."""
 import math
 
 import numpy as np
@@ -112,6 +115,7 @@ def test_many_tiles_per_block_mixed_is_deterministic(ctx):
 
 # ---------------------------------------------------------------------------------------
 N_BENCH, PRE_STEPS, T_SHIFT = 1_000_000, 150, 8.5 * math.pi   # the benchmark's workload
+N_GRID, PRE_GRID = 30_000_000, 12                             # the grid workload at size
 
 
 def _bench_workload():
@@ -131,38 +135,63 @@ def _take(d, ids):
     return {k: v[idx] for k, v in d.items()}, found
 
 
-def _sample_step(orc, ctx, prec, tol, max_mismatch):
-    wl = _bench_workload()
-    sim = q.Simulation(wl, prec=prec, ctx=ctx, cap_e=N_BENCH + 2_000_000, cap_p=2_000_000, cap_ph=10_000_000)
-    sim.run(PRE_STEPS, ALL)
-    pre = sim.state()
-    t, step = sim.t, sim.step_no
-    sim.run(1, ALL)
-    post = sim.state()
-    assert sim.status() == 0
-    sim.close()
-    assert len(pre["ph"]["id"]) > N_BENCH and len(pre["pos"]["id"]) > N_BENCH // 1000
+def _rows_at(sp, idx):
+    """rows `idx` (device index tensor) of one species, copied to the host"""
+    out = {}
+    for k, v in sp.t.items():
+        a = v[idx].cpu().numpy()
+        out[k] = a.view(np.uint64) if k == "id" else a.astype(np.float64)
+    return out
 
-    rng = np.random.default_rng(5)
-    pick = {sp: np.sort(rng.choice(pre[sp]["id"], size=min(n, len(pre[sp]["id"])), replace=False))
-            for sp, n in (("e", 4000), ("pos", 2000), ("ph", 6000))}
+
+def _rows_of_ids(sp, ids):
+    """the live rows whose id is in `ids` (selected on the device: no full-state copy)"""
+    n = sp.count()
+    want = torch.as_tensor(np.asarray(ids, dtype=np.uint64).view(np.int64), device="cuda")
+    idx = torch.nonzero(torch.isin(sp.t["id"][:n], want)).flatten()
+    return _rows_at(sp, idx)
+
+
+def _pick(sp, k, rng, cand=None):
+    """k random live rows of a species (from the candidate index tensor if given)"""
+    n = sp.count()
+    if cand is None:
+        cand = torch.arange(n, device="cuda")
+    m = int(cand.numel())
+    sel = np.sort(rng.choice(m, size=min(k, m), replace=False)).astype(np.int64)
+    return _rows_at(sp, cand[torch.as_tensor(sel, device="cuda")])
+
+
+def _sample_parity(orc, sim, wl, pre, tol, max_mismatch):
+    """Step the GPU set once more; step the sampled pre-step rows `pre` once with the
+    oracle from the same state; compare the sampled particles one by one."""
+    t, step = sim.t, sim.step_no
+    qed_next_id = q.qed_get_next_id(sim.ctx)
+    sim.run(1, ALL)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    pick = {sp: np.sort(pre[sp]["id"]) for sp in ("e", "pos", "ph")}
+    post = {sp: _rows_of_ids(getattr(sim, sp), pick[sp]) for sp in ("e", "pos", "ph")}
     owl = {"field": wl["field"], "dt": wl["dt"], "seed": wl["seed"], "t0": t, "step0": step,
-           "next_id": int(pre["next_id"])}
+           "next_id": int(qed_next_id)}
+    if "grid" in wl:
+        owl["grid"] = wl["grid"]
     for sp in ("e", "pos", "ph"):
-        owl[sp], found = _take(pre[sp], pick[sp])
-        assert found.all()
+        owl[sp] = pre[sp]
     n_near0 = len(orc.near_log()[0])
     osim = oracle.Sim(orc, owl)
-    osim.run(1, ALL)
+    ost = osim.run(1, ALL)
     near_ids, near_steps, _ = orc.near_log()
     near = set(int(i) for i, s in zip(near_ids[n_near0:], near_steps[n_near0:]) if s == step)
-    ost = osim.state()
+    ostate = osim.state()
 
     mism = 0
     total = 0
     for sp in ("e", "pos", "ph"):
+        if not len(pick[sp]):
+            continue
         g, gf = _take(post[sp], pick[sp])
-        o, of = _take(ost[sp], pick[sp])
+        o, of = _take(ostate[sp], pick[sp])
         if sp != "ph":
             assert gf.all() and of.all()
         ok = gf & of
@@ -181,6 +210,20 @@ def _sample_step(orc, ctx, prec, tol, max_mismatch):
         assert good.sum() > 0.9 * len(pick[sp]), sp
         assert np.array_equal(g["w"][good], o["w"][good])
     assert mism <= max_mismatch * total, f"{mism} of {total} sampled particles differ"
+    return ost
+
+
+def _sample_step(orc, ctx, prec, tol, max_mismatch):
+    wl = _bench_workload()
+    sim = q.Simulation(wl, prec=prec, ctx=ctx, cap_e=N_BENCH + 2_000_000, cap_p=2_000_000, cap_ph=10_000_000)
+    sim.run(PRE_STEPS, ALL)
+    torch.cuda.synchronize()
+    assert sim.ph.count() > N_BENCH and sim.pos.count() > N_BENCH // 1000
+    rng = np.random.default_rng(5)
+    pre = {sp: _pick(getattr(sim, sp), n, rng) for sp, n in (("e", 4000), ("pos", 2000), ("ph", 6000))}
+    ost = _sample_parity(orc, sim, wl, pre, tol, max_mismatch)
+    assert ost["n_ncs_e"] > 0 and ost["n_nbw"] > 0
+    sim.close()
 
 
 def test_bench_workload_sampled_parity_fp64(orc, ctx):
@@ -189,3 +232,42 @@ def test_bench_workload_sampled_parity_fp64(orc, ctx):
 
 def test_bench_workload_sampled_parity_mixed(orc, ctx):
     _sample_step(orc, ctx, q.QED_PREC_MIXED, 2e-5, 0.005)
+
+
+@pytest.fixture(scope="module")
+def grid_wl():
+    return workloads.c3(n=N_GRID, seed=3)
+
+
+def _grid_sample_step(orc, ctx, wl, prec, tol, max_mismatch):
+    """Config 3 at full size: 3e7 electrons on the 4096 x 2048 Yee grid (TSC gather),
+    12 steps in (photons and pairs exist); the sample is drawn mostly from particles
+    inside the reflected pulse, where every process is active."""
+    sim = q.Simulation(wl, prec=prec, ctx=ctx, cap_e=N_GRID + 2_000_000, cap_p=2_000_000, cap_ph=20_000_000)
+    sim.run(PRE_GRID, ALL)
+    torch.cuda.synchronize()
+    assert sim.ph.count() > 10_000
+    rng = np.random.default_rng(6)
+    x_lo = wl["grid"]["xs"] - 4.5 * 2 * math.pi   # the pulse reaches 4 wavelengths in front of the slab
+    pre = {}
+    for sp, n_in, n_any in (("e", 4000, 1000), ("pos", 1000, 0), ("ph", 4000, 1000)):
+        s = getattr(sim, sp)
+        n = s.count()
+        hot = torch.nonzero(s.t["x"][:n] > x_lo).flatten()
+        a = _pick(s, n_in, rng, hot)
+        if n_any:
+            b = _pick(s, n_any, rng)
+            keep = ~np.isin(b["id"], a["id"])
+            a = {k: np.concatenate([a[k], b[k][keep]]) for k in a}
+        pre[sp] = a
+    ost = _sample_parity(orc, sim, wl, pre, tol, max_mismatch)
+    assert ost["n_ncs_e"] > 0
+    sim.close()
+
+
+def test_grid_workload_sampled_parity_fp64(orc, ctx, grid_wl):
+    _grid_sample_step(orc, ctx, grid_wl, q.QED_PREC_F64, 1e-10, 0.0)
+
+
+def test_grid_workload_sampled_parity_mixed(orc, ctx, grid_wl):
+    _grid_sample_step(orc, ctx, grid_wl, q.QED_PREC_MIXED, 2e-5, 0.005)

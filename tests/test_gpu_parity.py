@@ -81,7 +81,7 @@ def _compare_all(sim, osim, tol, pos_tol):
 # ---------------------------------------------------------------------------------------
 def test_tables_match_oracle(orc, ctx):
     """Each side builds its tables with its own quadrature; they agree to rounding."""
-    names = {0: "K", 1: "ncs rate", 2: "ncs invcdf", 3: "nbw rate", 4: "nbw invcdf", 5: "vb"}
+    names = {0: "K", 1: "ncs rate", 2: "ncs invcdf", 3: "nbw rate", 4: "nbw invcdf", 5: "vb", 6: "radiative pusher"}
     for w, name in names.items():
         g = q.qed_copy_table(ctx, w)
         o = orc.table(w)
