@@ -26,6 +26,7 @@ _lib = None
 
 F_NCS, F_NBW, F_VB, F_SPIN, F_NO_RECOIL, F_DROP_PHOTONS = 1, 2, 4, 8, 16, 32
 F_LL, F_MLL, F_MBMT = 128, 256, 512   # radiative pusher: LL, quantum-corrected LL, radiative T-BMT
+F_DEPOSIT = 1024                      # leptons deposit their current (Esirkepov)
 FIELD_NONE, FIELD_UNIFORM, FIELD_PLANE, FIELD_GAUSS, FIELD_GRID2D = 0, 1, 2, 3, 4
 
 
@@ -56,7 +57,13 @@ class Fields(C.Structure):
                 ("gEz", C.POINTER(C.c_float)), ("gBx", C.POINTER(C.c_float)),
                 ("gBy", C.POINTER(C.c_float)), ("gBz", C.POINTER(C.c_float)),
                 ("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double),
-                ("x0", C.c_double), ("y0", C.c_double)]
+                ("x0", C.c_double), ("y0", C.c_double), ("periodic", C.c_int),
+                ("gJx", C.POINTER(C.c_double)), ("gJy", C.POINTER(C.c_double)), ("gJz", C.POINTER(C.c_double))]
+
+
+class Grid(C.Structure):
+    _fields_ = [(n, C.POINTER(C.c_double)) for n in ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")] + [
+        ("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double), ("periodic", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -96,6 +103,9 @@ def lib():
             L.or_field.argtypes = [C.POINTER(Fields), d, d, d, d, pd, pd]
             L.or_ncs_F.argtypes = [C.c_void_p, d, d, pd, pd, pd, pd, pd]
             L.or_nbw_G.argtypes = [C.c_void_p, d, d, d, pd, pd, pd, pd, pd, pd]
+            L.or_fdtd_b.argtypes = [C.POINTER(Grid), d]
+            L.or_fdtd_e.argtypes = [C.POINTER(Grid), d]
+            L.or_charge_tsc.argtypes = [C.POINTER(Grid), d, d, pd, pd, pd, u64, pd]
             L.or_table.argtypes = [C.c_void_p, C.c_int, C.POINTER(u64)]
             L.or_table.restype = pd
             _lib = L
@@ -165,6 +175,7 @@ def make_fields(kind=FIELD_NONE, circular=0, a0=0.0, phi0=0.0, length=1.0, w0=1.
             setattr(f, name, a.ctypes.data_as(C.POINTER(C.c_float)))
         f.ny, f.nx = comps[0].shape
         f.dx, f.dy, f.x0, f.y0 = grid["dx"], grid["dy"], grid.get("x0", 0.0), grid.get("y0", 0.0)
+        f.periodic = int(grid.get("periodic", 0))
     return f
 
 
@@ -333,3 +344,93 @@ class Sim:
     def state(self):
         return {"e": self.e.view(), "pos": self.pos.view(), "ph": self.ph.view(),
                 "next_id": self.o.next_id()}
+
+
+# ---------------------------------------------------------------------------------
+# Self-consistent 2D3V PIC around the step (Secs. II B, II C, II F): Yee solver and
+# Esirkepov deposition of the oracle, driven in the paper's leapfrog order.
+# ---------------------------------------------------------------------------------
+class YeeGrid:
+    """Double-precision Yee arrays [ny][nx] (E, B, J) with the oracle's solver."""
+
+    NAMES = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
+
+    def __init__(self, nx, ny, dx, dy, periodic=1, fields=None):
+        self.a = {k: np.zeros((ny, nx)) for k in self.NAMES}
+        if fields:
+            for k, v in fields.items():
+                self.a[k][...] = v
+        self.g = Grid()
+        for k in self.NAMES:
+            setattr(self.g, k, _dp(self.a[k]))
+        self.g.nx, self.g.ny, self.g.dx, self.g.dy, self.g.periodic = nx, ny, dx, dy, periodic
+        self.L = lib()
+
+    def advance_b(self, dt):
+        self.L.or_fdtd_b(C.byref(self.g), float(dt))
+
+    def advance_e(self, dt):
+        self.L.or_fdtd_e(C.byref(self.g), float(dt))
+
+    def charge(self, x, y, qw, x0=0.0, y0=0.0):
+        rho = np.zeros((self.g.ny, self.g.nx))
+        x, y, qw = map(_vec, (x, y, qw))
+        self.L.or_charge_tsc(C.byref(self.g), float(x0), float(y0), _dp(x), _dp(y), _dp(qw), len(x), _dp(rho))
+        return rho
+
+    def div_e(self):
+        a, g = self.a, self.g
+        # div E at the nodes (i, j): Ex(i+1/2) - Ex(i-1/2), Ey(j+1/2) - Ey(j-1/2)
+        ex, ey = a["Ex"], a["Ey"]
+        if g.periodic:
+            return (ex - np.roll(ex, 1, 1)) / g.dx + (ey - np.roll(ey, 1, 0)) / g.dy
+        d = ex.copy() / g.dx
+        d[:, 1:] -= ex[:, :-1] / g.dx
+        d += ey / g.dy
+        d[1:, :] -= ey[:-1, :] / g.dy
+        return d
+
+
+class PicSim(Sim):
+    """The QED step inside the PIC loop of Fig. fig-loop, leapfrog of Sec. II F:
+    E^n, B^{n-1/2} stored; B -> B^n by half a curl step; the step gathers (E^n, B^n),
+    pushes, runs the QED processes and deposits J^{n+1/2} from x^n -> x^{n+1}; B -> B^{n+1/2}
+    by the second half; E -> E^{n+1} with curl B^{n+1/2} - J^{n+1/2}.  The gather reads a
+    float copy of the fields, as the grid is FP32 by specification."""
+
+    def __init__(self, orc, wl, grid: YeeGrid, x0=0.0, y0=0.0, **caps):
+        g = grid.g
+        spec = {"Ex": np.zeros((g.ny, g.nx), np.float32), "dx": g.dx, "dy": g.dy, "x0": x0, "y0": y0,
+                "periodic": g.periodic}
+        for k in ("Ey", "Ez", "Bx", "By", "Bz"):
+            spec[k] = np.zeros((g.ny, g.nx), np.float32)
+        wl = dict(wl)
+        wl["field"] = {"kind": "grid2d"}
+        wl["grid"] = spec
+        super().__init__(orc, wl, **caps)
+        self.grid = grid
+        f = self.fields
+        for name, k in (("gJx", "Jx"), ("gJy", "Jy"), ("gJz", "Jz")):
+            setattr(f, name, _dp(grid.a[k]))
+        self._f32 = f._keep   # the float copies the gather reads (Ex..Bz)
+
+    def _refresh(self):
+        for arr, k in zip(self._f32, ("Ex", "Ey", "Ez", "Bx", "By", "Bz")):
+            arr[...] = self.grid.a[k]
+
+    def run(self, nsteps, flags):
+        tot = {}
+        for _ in range(nsteps):
+            self.grid.advance_b(0.5 * self.dt)
+            self._refresh()
+            for k in ("Jx", "Jy", "Jz"):
+                self.grid.a[k][...] = 0.0
+            s = self.o.step(self.e, self.pos, self.ph, self.fields, self.t, self.dt, self.seed, self.step_no,
+                            flags | F_DEPOSIT)
+            for k, v in s.items():
+                tot[k] = tot.get(k, 0) + v
+            self.grid.advance_b(0.5 * self.dt)
+            self.grid.advance_e(self.dt)
+            self.t += self.dt
+            self.step_no += 1
+        return tot

@@ -727,7 +727,13 @@ static void or_tsc(double d, double w[3]) {
   w[2] = 0.5 * (0.5 + d) * (0.5 + d);
 }
 
-static double or_gather(const float *g, int nx, int ny, double xs, double ys, int hx, int hy) {
+/* node index on a grid axis of n nodes: wrapped (periodic) or -1 when outside */
+static int or_node(int i, int n, int periodic) {
+  if (periodic) { i %= n; return i < 0 ? i + n : i; }
+  return (i < 0 || i >= n) ? -1 : i;
+}
+
+static double or_gather(const float *g, int nx, int ny, int periodic, double xs, double ys, int hx, int hy) {
   /* hx, hy: 1 if the component sits on the half grid along that axis */
   double X = hx ? xs - 0.5 : xs, Y = hy ? ys - 0.5 : ys;
   int ig = (int)floor(X + 0.5), jg = (int)floor(Y + 0.5);
@@ -736,15 +742,142 @@ static double or_gather(const float *g, int nx, int ny, double xs, double ys, in
   or_tsc(Y - jg, wy);
   double acc = 0;
   for (int b = 0; b < 3; ++b) {
-    int j = jg - 1 + b;
-    if (j < 0 || j >= ny) continue;
+    int j = or_node(jg - 1 + b, ny, periodic);
+    if (j < 0) continue;
     for (int a = 0; a < 3; ++a) {
-      int i = ig - 1 + a;
-      if (i < 0 || i >= nx) continue;
+      int i = or_node(ig - 1 + a, nx, periodic);
+      if (i < 0) continue;
       acc += wx[a] * wy[b] * (double)g[(size_t)j * nx + i];
     }
   }
   return acc;
+}
+
+/* ======================================================================= *
+ *  Esirkepov current deposition (Sec. II C, Esirkepov 2001) with the TSC  *
+ *  shape of Sec. II E, 2D3V.  The particle moves from (X0, Y0) to (X1, Y1) *
+ *  in cell units during dt (less than half a cell per axis, the CFL of    *
+ *  the field solver).  Shapes S0, S1 on the 5 nodes around the old       *
+ *  nearest node; DS = S1 - S0;                                            *
+ *    Wx = DS_x (S0_y + DS_y/2), Wy = DS_y (S0_x + DS_x/2),                 *
+ *    Wz = S0_x S0_y + DS_x S0_y/2 + S0_x DS_y/2 + DS_x DS_y/3;             *
+ *  Jx(i+1/2,j) = -(q w/(dy dt)) sum_{i'<=i} Wx(i',j),                      *
+ *  Jy(i,j+1/2) = -(q w/(dx dt)) sum_{j'<=j} Wy(i,j'),                      *
+ *  Jz(i,j) = q w vz Wz(i,j)/(dx dy),                                       *
+ *  which makes (rho^{n+1} - rho^n)/dt + div J = 0 on the grid exactly.     *
+ * ======================================================================= */
+static void or_deposit(const or_fields *f, double qw, const double xo[3], const double xn[3], double vz,
+                       double dt) {
+  double X0 = (xo[0] - f->x0) / f->dx, Y0 = (xo[1] - f->y0) / f->dy;
+  double X1 = (xn[0] - f->x0) / f->dx, Y1 = (xn[1] - f->y0) / f->dy;
+  int i0 = (int)floor(X0 + 0.5), j0 = (int)floor(Y0 + 0.5);
+  int i1 = (int)floor(X1 + 0.5), j1 = (int)floor(Y1 + 0.5);
+  double S0x[5] = {0}, S1x[5] = {0}, S0y[5] = {0}, S1y[5] = {0}, w[3];
+  int di = i1 - i0, dj = j1 - j0;
+  if (di < -1 || di > 1 || dj < -1 || dj > 1) return;   /* beyond the solver's CFL: not deposited */
+  or_tsc(X0 - i0, w);
+  for (int k = 0; k < 3; ++k) S0x[1 + k] = w[k];
+  or_tsc(X1 - i1, w);
+  for (int k = 0; k < 3; ++k) S1x[1 + di + k] = w[k];
+  or_tsc(Y0 - j0, w);
+  for (int k = 0; k < 3; ++k) S0y[1 + k] = w[k];
+  or_tsc(Y1 - j1, w);
+  for (int k = 0; k < 3; ++k) S1y[1 + dj + k] = w[k];
+  const double cx = -qw / (f->dy * dt), cy = -qw / (f->dx * dt), cz = qw * vz / (f->dx * f->dy);
+  for (int b = 0; b < 5; ++b) {
+    int j = or_node(j0 - 2 + b, f->ny, f->periodic);
+    double acc = 0.0;
+    for (int a = 0; a < 5; ++a) {
+      double dsx = S1x[a] - S0x[a], dsy = S1y[b] - S0y[b];
+      double Wx = dsx * (S0y[b] + 0.5 * dsy);
+      double Wz = S0x[a] * S0y[b] + 0.5 * dsx * S0y[b] + 0.5 * S0x[a] * dsy + dsx * dsy / 3.0;
+      acc += Wx;
+      int i = or_node(i0 - 2 + a, f->nx, f->periodic);
+      if (i < 0 || j < 0) continue;
+      if (a < 4) f->gJx[(size_t)j * f->nx + i] += cx * acc;
+      f->gJz[(size_t)j * f->nx + i] += cz * Wz;
+    }
+  }
+  for (int a = 0; a < 5; ++a) {
+    int i = or_node(i0 - 2 + a, f->nx, f->periodic);
+    double acc = 0.0;
+    for (int b = 0; b < 5; ++b) {
+      double dsx = S1x[a] - S0x[a], dsy = S1y[b] - S0y[b];
+      acc += dsy * (S0x[a] + 0.5 * dsx);
+      int j = or_node(j0 - 2 + b, f->ny, f->periodic);
+      if (i < 0 || j < 0 || b == 4) continue;
+      f->gJy[(size_t)j * f->nx + i] += cy * acc;
+    }
+  }
+}
+
+/* ======================================================================= *
+ *  Yee field solver (Sec. II B), 2D (z squeezed), the curl equations only *
+ *  (Gauss's law is kept by the charge-conserving deposition).  Neighbours *
+ *  outside the grid are zero, or wrap when periodic.                       *
+ * ======================================================================= */
+static double or_at(const double *a, const or_grid *g, int i, int j) {
+  i = or_node(i, g->nx, g->periodic);
+  j = or_node(j, g->ny, g->periodic);
+  return (i < 0 || j < 0) ? 0.0 : a[(size_t)j * g->nx + i];
+}
+
+void or_fdtd_b(const or_grid *g, double dt) {
+  const int nx = g->nx, ny = g->ny;
+  double *nbx = (double *)malloc(sizeof(double) * nx * ny), *nby = (double *)malloc(sizeof(double) * nx * ny);
+  double *nbz = (double *)malloc(sizeof(double) * nx * ny);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t k = (size_t)j * nx + i;
+      /* Bx(i,j+1/2): -dEz/dy;  By(i+1/2,j): +dEz/dx;  Bz(i+1/2,j+1/2): -(dEy/dx - dEx/dy) */
+      nbx[k] = g->Bx[k] - dt * (or_at(g->Ez, g, i, j + 1) - or_at(g->Ez, g, i, j)) / g->dy;
+      nby[k] = g->By[k] + dt * (or_at(g->Ez, g, i + 1, j) - or_at(g->Ez, g, i, j)) / g->dx;
+      nbz[k] = g->Bz[k] - dt * ((or_at(g->Ey, g, i + 1, j) - or_at(g->Ey, g, i, j)) / g->dx -
+                                (or_at(g->Ex, g, i, j + 1) - or_at(g->Ex, g, i, j)) / g->dy);
+    }
+  memcpy(g->Bx, nbx, sizeof(double) * nx * ny);
+  memcpy(g->By, nby, sizeof(double) * nx * ny);
+  memcpy(g->Bz, nbz, sizeof(double) * nx * ny);
+  free(nbx); free(nby); free(nbz);
+}
+
+void or_fdtd_e(const or_grid *g, double dt) {
+  const int nx = g->nx, ny = g->ny;
+  double *nex = (double *)malloc(sizeof(double) * nx * ny), *ney = (double *)malloc(sizeof(double) * nx * ny);
+  double *nez = (double *)malloc(sizeof(double) * nx * ny);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t k = (size_t)j * nx + i;
+      /* Ex(i+1/2,j): dBz/dy - Jx;  Ey(i,j+1/2): -dBz/dx - Jy;  Ez(i,j): dBy/dx - dBx/dy - Jz */
+      nex[k] = g->Ex[k] + dt * ((or_at(g->Bz, g, i, j) - or_at(g->Bz, g, i, j - 1)) / g->dy - g->Jx[k]);
+      ney[k] = g->Ey[k] + dt * (-(or_at(g->Bz, g, i, j) - or_at(g->Bz, g, i - 1, j)) / g->dx - g->Jy[k]);
+      nez[k] = g->Ez[k] + dt * ((or_at(g->By, g, i, j) - or_at(g->By, g, i - 1, j)) / g->dx -
+                                (or_at(g->Bx, g, i, j) - or_at(g->Bx, g, i, j - 1)) / g->dy - g->Jz[k]);
+    }
+  memcpy(g->Ex, nex, sizeof(double) * nx * ny);
+  memcpy(g->Ey, ney, sizeof(double) * nx * ny);
+  memcpy(g->Ez, nez, sizeof(double) * nx * ny);
+  free(nex); free(ney); free(nez);
+}
+
+void or_charge_tsc(const or_grid *g, double x0, double y0, const double *x, const double *y, const double *qw,
+                   uint64_t n, double *rho) {
+  for (uint64_t p = 0; p < n; ++p) {
+    double X = (x[p] - x0) / g->dx, Y = (y[p] - y0) / g->dy;
+    int ig = (int)floor(X + 0.5), jg = (int)floor(Y + 0.5);
+    double wx[3], wy[3];
+    or_tsc(X - ig, wx);
+    or_tsc(Y - jg, wy);
+    for (int b = 0; b < 3; ++b) {
+      int j = or_node(jg - 1 + b, g->ny, g->periodic);
+      if (j < 0) continue;
+      for (int a = 0; a < 3; ++a) {
+        int i = or_node(ig - 1 + a, g->nx, g->periodic);
+        if (i < 0) continue;
+        rho[(size_t)j * g->nx + i] += qw[p] * wx[a] * wy[b] / (g->dx * g->dy);
+      }
+    }
+  }
 }
 
 void or_field(const or_fields *f, double x, double y, double z, double t, double E[3], double B[3]) {
@@ -779,12 +912,12 @@ void or_field(const or_fields *f, double x, double y, double z, double t, double
     /* 2D Yee staggering (z squeezed): Ex(i+1/2,j) Ey(i,j+1/2) Ez(i,j)
        Bx(i,j+1/2) By(i+1/2,j) Bz(i+1/2,j+1/2) */
     double xs = (x - f->x0) / f->dx, ys = (y - f->y0) / f->dy;
-    E[0] = or_gather(f->gEx, f->nx, f->ny, xs, ys, 1, 0);
-    E[1] = or_gather(f->gEy, f->nx, f->ny, xs, ys, 0, 1);
-    E[2] = or_gather(f->gEz, f->nx, f->ny, xs, ys, 0, 0);
-    B[0] = or_gather(f->gBx, f->nx, f->ny, xs, ys, 0, 1);
-    B[1] = or_gather(f->gBy, f->nx, f->ny, xs, ys, 1, 0);
-    B[2] = or_gather(f->gBz, f->nx, f->ny, xs, ys, 1, 1);
+    E[0] = or_gather(f->gEx, f->nx, f->ny, f->periodic, xs, ys, 1, 0);
+    E[1] = or_gather(f->gEy, f->nx, f->ny, f->periodic, xs, ys, 0, 1);
+    E[2] = or_gather(f->gEz, f->nx, f->ny, f->periodic, xs, ys, 0, 0);
+    B[0] = or_gather(f->gBx, f->nx, f->ny, f->periodic, xs, ys, 0, 1);
+    B[1] = or_gather(f->gBy, f->nx, f->ny, f->periodic, xs, ys, 1, 0);
+    B[2] = or_gather(f->gBz, f->nx, f->ny, f->periodic, xs, ys, 1, 1);
   }
 }
 
@@ -1104,7 +1237,11 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
   }
   /* position with the pre-QED p^{n+1/2} (after the radiation force when it is on) */
   double g1 = sqrt(1.0 + dot3(pn, pn));
+  double xo[3] = {x[0], x[1], x[2]};
   for (int k = 0; k < 3; ++k) x[k] += dt * pn[k] / g1;
+  /* current of the move x^n -> x^{n+1} (Sec. II C), with v_z of the same p^{n+1/2} */
+  if ((flags & OR_F_DEPOSIT) && f->kind == OR_FIELD_GRID2D && f->gJx)
+    or_deposit(f, q * L->w[i], xo, x, pn[2] / g1, dt);
   int emitted = 0;
   if (flags & OR_F_NCS) {
     double pmag = norm3(pn);

@@ -31,6 +31,7 @@ extern "C" {
 #define OR_F_LL       128u   /* classical Landau-Lifshitz radiation reaction (Eq. eq1-1) */
 #define OR_F_MLL      256u   /* quantum-corrected LL: q(chi) F_RR,classical (Sec. III A) */
 #define OR_F_MBMT     512u   /* radiative T-BMT (Eq. spin1); needs OR_F_SPIN        */
+#define OR_F_DEPOSIT 1024u   /* leptons deposit their current (Esirkepov, Sec. II C)  */
 
 /* --- particle arrays (structure of arrays, caller-owned) -------------------- */
 typedef struct {
@@ -59,7 +60,22 @@ typedef struct {
   const float *gEx, *gEy, *gEz, *gBx, *gBy, *gBz;
   int nx, ny;
   double dx, dy, x0, y0;
+  int periodic;            /* grid: 1 periodic in x and y, 0 nodes outside are zero */
+  double *gJx, *gJy, *gJz; /* grid current (OR_F_DEPOSIT adds to it), [ny][nx] with
+                              Jx(i+1/2,j) Jy(i,j+1/2) Jz(i,j)                       */
 } or_fields;
+
+/* --- 2D3V Yee grid of the field solver (Sec. II B), double, [ny][nx] ----------
+ * Ex(i+1/2,j) Ey(i,j+1/2) Ez(i,j) Bx(i,j+1/2) By(i+1/2,j) Bz(i+1/2,j+1/2), currents on
+ * the E positions; node (i,j) at (x0 + i dx, y0 + j dy).  Normalised units: c = 1,
+ * E, B in m c omega/e, rho in e n_c, J in e n_c c, so that div E = rho and
+ * curl B = dE/dt + J.  A macro-particle of weight w carries density w/(dx dy) n_c. */
+typedef struct {
+  double *Ex, *Ey, *Ez, *Bx, *By, *Bz, *Jx, *Jy, *Jz;
+  int nx, ny;
+  double dx, dy;
+  int periodic;
+} or_grid;
 
 typedef struct {
   uint64_t n_ncs[2];       /* emissions by e-, e+                             */
@@ -82,6 +98,13 @@ void or_near_log(or_ctx *c, uint64_t *ids, uint32_t *steps, double *margins, uin
 int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph,
             const or_fields *f, double t, double dt, uint64_t seed, uint32_t step,
             uint32_t flags, or_stats *st);
+
+/* Yee leapfrog halves (Sec. II B): B -= dt curl E;  E += dt (curl B - J) */
+void or_fdtd_b(const or_grid *g, double dt);
+void or_fdtd_e(const or_grid *g, double dt);
+/* TSC charge density of n particles (charge*weight qw) on the nodes: rho += ... */
+void or_charge_tsc(const or_grid *g, double x0, double y0, const double *x, const double *y,
+                   const double *qw, uint64_t n, double *rho);
 
 /* --- pieces exposed for the oracle's own pins ------------------------------- */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
