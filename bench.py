@@ -65,7 +65,7 @@ BYTES = {
 # by the particles it processed) from the ncu capture summarised in
 # profiles/k_photon_k_lepton_c2_1e6_traffic.md; scaled to a launch by its particle count.
 # Must be re-captured whenever either streaming kernel changes.
-TRAFFIC_PER_UNIT = {}   # the streaming kernels changed after the last capture
+TRAFFIC_PER_UNIT = {"k_photon": 87.19, "k_lepton": 62.97}
 
 
 class ClockSampler:
@@ -209,6 +209,50 @@ def run_c3(q, torch, steps, warmup, flush, f64_steps, kernel_steps):
         sim.close()
     if "mixed" in out and "f64" in out:
         out["speedup_mixed"] = out["mixed"]["value"] / out["f64"]["value"]
+    return out
+
+
+def run_pic(q, torch, steps, warmup):
+    """Self-consistent PIC around the step: the 3e7-electron grid workload (4096 x 2048
+    cells, fields evolved by the Yee solver from the reflected-pulse snapshot, bounded
+    grid) with Esirkepov deposition of every lepton move, NCS + NBW + VB + T-BMT, mixed
+    path.  Per step: FDTD_B(dt/2), qed_step(... | QED_F_DEPOSIT), FDTD_B(dt/2), FDTD_E(dt).
+    Macro-particle weight 0.01 (about 1 n_c).  The field solver's own rate is timed apart:
+    132 B per cell and step (two B halves of 36 B, one E update of 60 B incl. J)."""
+    import numpy as np
+    import workloads
+    wl = workloads.c3(n=C3_N, seed=3)
+    g = wl["grid"]
+    ny, nx = g["Ey"].shape
+    wl["e"]["w"] = np.full(C3_N, 0.01)
+    flags = q.QED_F_NCS | q.QED_F_NBW | q.QED_F_VB | q.QED_F_SPIN
+    sim = q.PicSimulation(wl, nx, ny, g["dx"], g["dy"], periodic=0,
+                          fields={k: g[k] for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")}, prec=q.QED_PREC_MIXED,
+                          cap_e=C3_N + 4_000_000, cap_p=4_000_000, cap_ph=60_000_000)
+    sim.run(C3_PRE + warmup, flags)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0 = int(sim.stats[6].item())
+    ev0.record()
+    sim.run(steps, flags)
+    ev1.record()
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    parts = int(sim.stats[6].item()) - p0
+    reps = 20
+    ev0.record()
+    for _ in range(reps):
+        q.qed_fdtd_advance(sim.g, q.QED_FDTD_B, 0.5 * sim.dt)
+        q.qed_fdtd_advance(sim.g, q.QED_FDTD_B, 0.5 * sim.dt)
+        q.qed_fdtd_advance(sim.g, q.QED_FDTD_E, sim.dt)
+    ev1.record()
+    ev1.synchronize()
+    fd_ms = ev0.elapsed_time(ev1) / reps
+    out = {"workload": "c3 grid 4096x2048 + Yee solver + Esirkepov deposition, 3e7 electrons",
+           "value": parts / (ms * 1e-3), "unit": "particle-steps/s", "ms_per_step": ms / steps, "steps": steps,
+           "fdtd_ms_per_step": fd_ms, "fdtd_GBs": 132.0 * nx * ny / (fd_ms * 1e-3) / 1e9,
+           "counts_after": (sim.e.count(), sim.pos.count(), sim.ph.count()), "status": sim.status()}
+    sim.close()
     return out
 
 
@@ -484,6 +528,8 @@ def main():
                     help="timed steps of the 3e7-electron grid workload (0: skip)")
     ap.add_argument("--c3-f64-steps", type=int, default=10,
                     help="timed steps of the grid workload on the FP64 path (0: skip)")
+    ap.add_argument("--pic-steps", type=int, default=20,
+                    help="timed steps of the self-consistent PIC leg (0: skip)")
     ap.add_argument("--rr-steps", type=int, default=50,
                     help="timed steps of the radiative-pusher leg (0: skip)")
     ap.add_argument("--kernel-steps", type=int, default=20,
@@ -545,6 +591,7 @@ def main():
     c3 = (run_c3(q, torch, args.c3_steps, args.warmup, flush, args.c3_f64_steps, min(args.kernel_steps, 10))
           if args.c3_steps > 0 else None)
     rr = run_rr(q, torch, args.rr_steps, args.warmup, flush, min(args.kernel_steps, 10)) if args.rr_steps > 0 else None
+    pic = run_pic(q, torch, args.pic_steps, args.warmup) if args.pic_steps > 0 else None
     c4 = run_c4(q, torch, args.c4_steps, args.warmup) if args.c4_steps > 0 else None
     c5 = run_c5(q, torch, args.c5_steps) if args.c5_steps > 0 else None
     e2e = run_e2e(q, torch, sim, q.QED_PREC_MIXED, args.e2e_steps, flags)
@@ -601,6 +648,7 @@ def main():
         "c3": c3,
         "c4": c4,
         "radiative_pusher": rr,
+        "pic": pic,
         "c5": c5,
         "gpu_launches": 7 * args.steps,   # headline loop; per step: photon, lepton, 2 scans, pairs, refill, NCS
         "clocks": clk.summary(),

@@ -83,6 +83,13 @@ typedef enum { QED_PREC_F64 = 0, QED_PREC_MIXED = 1 } qed_precision;
 #define QED_F_LL 128u
 #define QED_F_MLL 256u
 #define QED_F_MBMT 512u
+/* Current deposition (Sec. II C, Esirkepov's charge-conserving scheme with the TSC shape of
+ * Sec. II E): every lepton adds the current of its move x^n -> x^{n+1} (charge q w, v_z of
+ * p^{n+1/2}) to gJx, gJy, gJz of a QED_FIELD_GRID2D field, so that (rho^{n+1} - rho^n)/dt +
+ * div J = 0 on the grid.  Moves of more than one cell per axis (beyond the solver's CFL)
+ * are not deposited.  Float atomics: the summation order, and so the last bits of J, vary
+ * from run to run.  Single-ensemble steps only (qed_batch_create rejects it). */
+#define QED_F_DEPOSIT 1024u
 
 /* Structure-of-arrays view of one species, caller-owned device memory.  Element i of
  * every array describes particle i.  Element types follow qed_precision (above):
@@ -130,7 +137,25 @@ typedef struct {
   const float *gEx, *gEy, *gEz, *gBx, *gBy, *gBz;
   int nx, ny;
   double dx, dy, x0, y0;
+  int periodic;              /* grid: 1 = periodic in x and y (gather and deposit wrap),
+                                0 = nodes outside the grid are zero                      */
+  float *gJx, *gJy, *gJz;    /* grid: current density for QED_F_DEPOSIT, [ny][nx] with
+                                Jx(i+1/2,j), Jy(i,j+1/2), Jz(i,j) (the E positions); may
+                                be NULL otherwise                                         */
 } qed_fields;
+
+/* The 2D3V Yee grid of the field solver (paper Sec. II B, Fig. "yeegrid" (b), z squeezed):
+ * nine float arrays [ny][nx] in device memory, caller-owned, with the staggering of
+ * QED_FIELD_GRID2D (Ex(i+1/2,j), Ey(i,j+1/2), Ez(i,j), Bx(i,j+1/2), By(i+1/2,j),
+ * Bz(i+1/2,j+1/2)) and the current on the E positions.  Normalised units: c = 1, E and B
+ * in m c omega/e, J in e n_c c, so that curl B = dE/dt + J and div E = rho (rho in e n_c);
+ * a macro-particle of weight w stands for a density w/(dx dy) n_c spread over one cell. */
+typedef struct {
+  float *Ex, *Ey, *Ez, *Bx, *By, *Bz, *Jx, *Jy, *Jz;
+  int nx, ny;
+  double dx, dy;
+  int periodic;              /* 1 periodic, 0 neighbours outside the grid are zero */
+} qed_grid2d;
 
 /* Per-step event counters accumulated on the device (add-only). */
 typedef struct {
@@ -212,6 +237,20 @@ qed_status qed_get_next_id(qed_ctx *ctx, uint64_t *next_id, void *stream);
 qed_status qed_step(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed_particles *ph,
                     const qed_fields *f, double t, double dt, uint64_t seed, uint32_t step,
                     uint32_t flags, qed_step_stats *dev_stats, void *stream);
+
+/* Field solver (Sec. II B): one half of the Yee leapfrog on a 2D3V grid (async).
+ *   which = QED_FDTD_B: B -= dt curl E   (Faraday);
+ *   which = QED_FDTD_E: E += dt (curl B - J) (Ampere), and J is then set to zero, ready
+ *                       for the next step's deposition.
+ * Only the curl equations are solved: with the charge-conserving deposition Gauss's law
+ * is kept (Sec. II B).  The PIC loop of Sec. II F around qed_step, with E^n and B^{n-1/2}
+ * stored: FDTD_B(dt/2); qed_step(... | QED_F_DEPOSIT) gathers E^n, B^n and deposits
+ * J^{n+1/2}; FDTD_B(dt/2); FDTD_E(dt).  The explicit scheme needs dt below the 2D Courant
+ * limit 1/sqrt(1/dx^2 + 1/dy^2).  Errors: QED_ERR_INVALID_ARG (NULL arrays, nx or ny < 2,
+ * ny > 65535, dx, dy or dt not positive and finite, unknown which), QED_ERR_CUDA. */
+#define QED_FDTD_B 0
+#define QED_FDTD_E 1
+qed_status qed_fdtd_advance(const qed_grid2d *g, int which, double dt, void *stream);
 
 /* End-to-end form of qed_step for callers whose particles live in host memory: copies
  * the live part of each given host SoA (same layout and precision as the device set,

@@ -23,6 +23,8 @@ QED_PREC_F64, QED_PREC_MIXED = 0, 1
 QED_F_NCS, QED_F_NBW, QED_F_VB, QED_F_SPIN, QED_F_NO_RECOIL, QED_F_DROP_PHOTONS = 1, 2, 4, 8, 16, 32
 QED_F_MLP = 64
 QED_F_LL, QED_F_MLL, QED_F_MBMT = 128, 256, 512
+QED_F_DEPOSIT = 1024
+QED_FDTD_B, QED_FDTD_E = 0, 1
 QED_STATUS_CAPACITY, QED_STATUS_TIMEOUT, QED_STATUS_TABLE_RANGE = 1, 2, 4
 FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
 
@@ -32,7 +34,8 @@ ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particle
                  "qed_set_timing", "qed_get_timing", "qed_diag", "qed_ctx_share", "qed_batch_create",
                  "qed_batch_step", "qed_batch_run", "qed_batch_clock", "qed_batch_get_config",
                  "qed_batch_set_config", "qed_batch_tune", "qed_batch_destroy", "qed_mlp_train",
-                 "qed_mlp_set_params", "qed_mlp_get_params", "qed_mlp_eval", "qed_mlp_target", "qed_last_error")
+                 "qed_mlp_set_params", "qed_mlp_get_params", "qed_mlp_eval", "qed_mlp_target", "qed_fdtd_advance",
+                 "qed_last_error")
 MLP_PARAMS = 4481
 QED_DIAG_SPECTRUM, QED_DIAG_DETECTOR = 0, 1
 
@@ -48,7 +51,13 @@ class qed_fields(C.Structure):
                 ("B", C.c_double * 3), ("gEx", C.c_void_p), ("gEy", C.c_void_p), ("gEz", C.c_void_p),
                 ("gBx", C.c_void_p), ("gBy", C.c_void_p), ("gBz", C.c_void_p), ("nx", C.c_int),
                 ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double), ("x0", C.c_double),
-                ("y0", C.c_double)]
+                ("y0", C.c_double), ("periodic", C.c_int), ("gJx", C.c_void_p), ("gJy", C.c_void_p),
+                ("gJz", C.c_void_p)]
+
+
+class qed_grid2d(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")] + [
+        ("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double), ("periodic", C.c_int)]
 
 
 class qed_step_stats(C.Structure):
@@ -118,6 +127,7 @@ def lib():
         L.qed_mlp_get_params.argtypes = [vp, C.POINTER(C.c_float), vp]
         L.qed_mlp_eval.argtypes = [vp, vp, vp, u64, vp]
         L.qed_mlp_target.argtypes = [vp, vp, vp, u64, vp]
+        L.qed_fdtd_advance.argtypes = [C.POINTER(qed_grid2d), C.c_int, d, vp]
         L.qed_last_error.restype = C.c_char_p
         for name in ABI_FUNCTIONS:
             if name != "qed_last_error":
@@ -439,7 +449,15 @@ def fields_from_spec(spec: dict, grid=None) -> qed_fields:
         f.ny, f.nx = grid["Ey"].shape
         f.dx, f.dy = float(grid["dx"]), float(grid["dy"])
         f.x0, f.y0 = float(grid.get("x0", 0.0)), float(grid.get("y0", 0.0))
+        f.periodic = int(grid.get("periodic", 0))
+        for k in ("Jx", "Jy", "Jz"):
+            if k in grid:
+                setattr(f, "g" + k, grid[k].data_ptr())
     return f
+
+
+def qed_fdtd_advance(g: qed_grid2d, which, dt, stream=None):
+    _check(lib().qed_fdtd_advance(C.byref(g), int(which), float(dt), _stream(stream)), "qed_fdtd_advance")
 
 
 class Simulation:
@@ -545,3 +563,42 @@ class Batch:
         if self.own_ctx:
             qed_destroy(self.ctx)
             self.own_ctx = False
+
+
+class PicSimulation(Simulation):
+    """The step inside the PIC loop of Sec. II F on a 2D3V Yee grid of the library: E^n and
+    B^{n-1/2} stored in float device tensors; per step FDTD_B(dt/2), qed_step with
+    QED_F_DEPOSIT (gathers E^n, B^n; deposits J^{n+1/2}), FDTD_B(dt/2), FDTD_E(dt) (which
+    consumes J and clears it).  `fields` (optional) gives initial E, B arrays [ny][nx]."""
+
+    def __init__(self, wl: dict, nx, ny, dx, dy, periodic=1, fields=None, x0=0.0, y0=0.0, prec=QED_PREC_F64,
+                 **caps):
+        import torch
+        self.yee = {k: torch.zeros((ny, nx), dtype=torch.float32, device="cuda")
+                    for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")}
+        for k, v in (fields or {}).items():
+            self.yee[k].copy_(torch.as_tensor(np.asarray(v, dtype=np.float32)))
+        # the particle sets and context; the field descriptor is set to the Yee grid below
+        super().__init__(dict(wl, field={"kind": "none"}), prec=prec, **caps)
+        grid = dict(self.yee)
+        grid.update({"dx": dx, "dy": dy, "x0": x0, "y0": y0, "periodic": periodic})
+        self.grid = grid
+        self.fields = fields_from_spec({"kind": "grid2d"}, grid)
+        self.g = qed_grid2d()
+        for k, v in self.yee.items():
+            setattr(self.g, k, v.data_ptr())
+        self.g.nx, self.g.ny, self.g.dx, self.g.dy, self.g.periodic = nx, ny, float(dx), float(dy), int(periodic)
+
+    def run(self, nsteps, flags, stream=None):
+        for _ in range(nsteps):
+            qed_fdtd_advance(self.g, QED_FDTD_B, 0.5 * self.dt, stream)
+            qed_step(self.ctx, self.e.handle, self.pos.handle, self.ph.handle, self.fields, self.t, self.dt,
+                     self.seed, self.step_no, flags | QED_F_DEPOSIT, self.stats.data_ptr(), stream)
+            qed_fdtd_advance(self.g, QED_FDTD_B, 0.5 * self.dt, stream)
+            qed_fdtd_advance(self.g, QED_FDTD_E, self.dt, stream)
+            self.t += self.dt
+            self.step_no += 1
+
+    def field_arrays(self) -> dict:
+        self.torch.cuda.synchronize()
+        return {k: v.cpu().numpy().astype(np.float64) for k, v in self.yee.items()}

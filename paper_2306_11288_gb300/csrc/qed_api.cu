@@ -341,6 +341,13 @@ qed_status check_mlp_flag(const qed_ctx* c, uint32_t flags, qed_precision prec, 
   return QED_OK;
 }
 
+qed_status check_deposit(uint32_t flags, const qed_fields* f, const char* who) {
+  if (!(flags & QED_F_DEPOSIT)) return QED_OK;
+  if (f->kind != QED_FIELD_GRID2D || !f->gJx || !f->gJy || !f->gJz)
+    FAIL(QED_ERR_INVALID_ARG, "%s: QED_F_DEPOSIT needs a grid field with current arrays", who);
+  return QED_OK;
+}
+
 qed_status check_fields(const qed_fields* f, const char* who) {
   // every parameter the kind uses must be finite: a NaN or inf here would reach every
   // particle of the step
@@ -366,6 +373,7 @@ qed_status check_fields(const qed_fields* f, const char* who) {
     case QED_FIELD_GRID2D:
       if (!f->gEx || !f->gEy || !f->gEz || !f->gBx || !f->gBy || !f->gBz)
         FAIL(QED_ERR_INVALID_ARG, "%s: grid arrays must be non-NULL", who);
+      if (f->periodic != 0 && f->periodic != 1) FAIL(QED_ERR_INVALID_ARG, "%s: periodic must be 0 or 1", who);
       if (f->nx < 1 || f->ny < 1 || !(f->dx > 0) || !(f->dy > 0)) FAIL(QED_ERR_INVALID_ARG, "%s: bad grid geometry", who);
       break;
     default:
@@ -399,6 +407,8 @@ static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos
   qed_status r_ = check_mlp_flag(c, flags, *prec, "qed_step");
   if (r_ != QED_OK) return r_;
   r_ = check_fields(f, "qed_step");
+  if (r_ != QED_OK) return r_;
+  r_ = check_deposit(flags, f, "qed_step");
   if (r_ != QED_OK) return r_;
   const unsigned long long tp = ph ? tiles_of(ph->cap) : 0;
   const unsigned long long tl = (e ? tiles_of(e->cap) : 0) + (pos ? tiles_of(pos->cap) : 0);

@@ -92,12 +92,13 @@ void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos,
 void step_time_floats(double t, double phi0, float* t_rel, float* t_mod);
 // host validation of a field descriptor (message prefixed by who)
 qed_status check_fields(const qed_fields* f, const char* who);
+qed_status check_deposit(uint32_t flags, const qed_fields* f, const char* who);
 }  // namespace qedk
 struct qed_ctx;
 namespace qedk {
 // QED_F_MLP needs the mixed path and trained (or set) sampler parameters
 // every flag bit the step kernels know; validation of flag combinations
-constexpr uint32_t kAllFlags = 1023u;
+constexpr uint32_t kAllFlags = 2047u;
 qed_status check_flag_bits(uint32_t flags, const char* who);
 qed_status check_mlp_flag(const qed_ctx* c, uint32_t flags, qed_precision prec, const char* who);
 // occupancy-derived persistent grid sizes

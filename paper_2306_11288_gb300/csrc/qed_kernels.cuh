@@ -55,8 +55,17 @@ __device__ __forceinline__ double f2d_bits(float f) {
 template <typename R>
 struct EB { V3<R> E, B; };
 
+// node index on a grid axis of n nodes: wrapped (periodic grid) or -1 outside the grid
+__device__ __forceinline__ int grid_node(int i, int n, int periodic) {
+  if (periodic) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  return (i < 0 || i >= n) ? -1 : i;
+}
+
 template <typename R>
-__device__ __forceinline__ R tsc_gather(const float* g, int nx, int ny, double X, double Y) {
+__device__ __forceinline__ R tsc_gather(const float* g, int nx, int ny, int periodic, double X, double Y) {
   const double fx = floor(X + 0.5), fy = floor(Y + 0.5);
   const int ig = (int)fx, jg = (int)fy;
   const R dx = (R)(X - fx), dy = (R)(Y - fy);
@@ -65,13 +74,13 @@ __device__ __forceinline__ R tsc_gather(const float* g, int nx, int ny, double X
   R acc = R(0);
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
-    const int j = jg - 1 + b;
-    if (j < 0 || j >= ny) continue;
+    const int j = grid_node(jg - 1 + b, ny, periodic);
+    if (j < 0) continue;
     R row = R(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const int i = ig - 1 + c;
-      if (i < 0 || i >= nx) continue;
+      const int i = grid_node(ig - 1 + c, nx, periodic);
+      if (i < 0) continue;
       row += wx[c] * (R)__ldg(g + (size_t)j * nx + i);
     }
     acc += wy[b] * row;
@@ -93,8 +102,8 @@ __device__ __forceinline__ int tsc_axis(float X, float w[3]) {
   w[2] = 0.5f * hi * hi;
   return (int)f - 1;
 }
-__device__ __forceinline__ float tsc_sum(const float* g, int nx, int ny, int i0, int j0, const float* wx,
-                                         const float* wy) {
+__device__ __forceinline__ float tsc_sum(const float* g, int nx, int ny, int periodic, int i0, int j0,
+                                         const float* wx, const float* wy) {
   float acc = 0.0f;
   if (i0 >= 0 && j0 >= 0 && i0 + 2 < nx && j0 + 2 < ny) {   // interior: the whole stencil is on the grid
     const float* r = g + (size_t)j0 * nx + i0;
@@ -107,13 +116,13 @@ __device__ __forceinline__ float tsc_sum(const float* g, int nx, int ny, int i0,
   }
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
-    const int j = j0 + b;
-    if (j < 0 || j >= ny) continue;
+    const int j = grid_node(j0 + b, ny, periodic);
+    if (j < 0) continue;
     float row = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const int i = i0 + c;
-      if (i < 0 || i >= nx) continue;
+      const int i = grid_node(i0 + c, nx, periodic);
+      if (i < 0) continue;
       row += wx[c] * __ldg(g + (size_t)j * nx + i);
     }
     acc += wy[b] * row;
@@ -215,20 +224,20 @@ __device__ __forceinline__ EB<R> gather(const EnsArgs& E, const EnsTime& tm, dou
     float wx0[3], wx1[3], wy0[3], wy1[3];
     const int i0 = tsc_axis(X, wx0), ih = tsc_axis(X - 0.5f, wx1);
     const int j0 = tsc_axis(Y, wy0), jh = tsc_axis(Y - 0.5f, wy1);
-    r.E.x = (R)tsc_sum(f.gEx, f.nx, f.ny, ih, j0, wx1, wy0);
-    r.E.y = (R)tsc_sum(f.gEy, f.nx, f.ny, i0, jh, wx0, wy1);
-    r.E.z = (R)tsc_sum(f.gEz, f.nx, f.ny, i0, j0, wx0, wy0);
-    r.B.x = (R)tsc_sum(f.gBx, f.nx, f.ny, i0, jh, wx0, wy1);
-    r.B.y = (R)tsc_sum(f.gBy, f.nx, f.ny, ih, j0, wx1, wy0);
-    r.B.z = (R)tsc_sum(f.gBz, f.nx, f.ny, ih, jh, wx1, wy1);
+    r.E.x = (R)tsc_sum(f.gEx, f.nx, f.ny, f.periodic, ih, j0, wx1, wy0);
+    r.E.y = (R)tsc_sum(f.gEy, f.nx, f.ny, f.periodic, i0, jh, wx0, wy1);
+    r.E.z = (R)tsc_sum(f.gEz, f.nx, f.ny, f.periodic, i0, j0, wx0, wy0);
+    r.B.x = (R)tsc_sum(f.gBx, f.nx, f.ny, f.periodic, i0, jh, wx0, wy1);
+    r.B.y = (R)tsc_sum(f.gBy, f.nx, f.ny, f.periodic, ih, j0, wx1, wy0);
+    r.B.z = (R)tsc_sum(f.gBz, f.nx, f.ny, f.periodic, ih, jh, wx1, wy1);
   } else if (f.kind == QED_FIELD_GRID2D) {
     const double X = (x - f.x0) / f.dx, Y = (y - f.y0) / f.dy;
-    r.E.x = tsc_gather<R>(f.gEx, f.nx, f.ny, X - 0.5, Y);
-    r.E.y = tsc_gather<R>(f.gEy, f.nx, f.ny, X, Y - 0.5);
-    r.E.z = tsc_gather<R>(f.gEz, f.nx, f.ny, X, Y);
-    r.B.x = tsc_gather<R>(f.gBx, f.nx, f.ny, X, Y - 0.5);
-    r.B.y = tsc_gather<R>(f.gBy, f.nx, f.ny, X - 0.5, Y);
-    r.B.z = tsc_gather<R>(f.gBz, f.nx, f.ny, X - 0.5, Y - 0.5);
+    r.E.x = tsc_gather<R>(f.gEx, f.nx, f.ny, f.periodic, X - 0.5, Y);
+    r.E.y = tsc_gather<R>(f.gEy, f.nx, f.ny, f.periodic, X, Y - 0.5);
+    r.E.z = tsc_gather<R>(f.gEz, f.nx, f.ny, f.periodic, X, Y);
+    r.B.x = tsc_gather<R>(f.gBx, f.nx, f.ny, f.periodic, X, Y - 0.5);
+    r.B.y = tsc_gather<R>(f.gBy, f.nx, f.ny, f.periodic, X - 0.5, Y);
+    r.B.z = tsc_gather<R>(f.gBz, f.nx, f.ny, f.periodic, X - 0.5, Y - 0.5);
   }
   return r;
 }
@@ -668,11 +677,78 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
   }
 }
 
+// ---- Esirkepov current deposition (Sec. II C) with the TSC shape of Sec. II E, 2D3V ----
+// The move (X0, Y0) -> (X1, Y1) in cell units (less than one cell per axis).  Shapes S0, S1
+// on the 5 nodes around the old nearest node, DS = S1 - S0;
+//   Wx = DS_x (S0_y + DS_y/2), Wy = DS_y (S0_x + DS_x/2),
+//   Wz = S0_x S0_y + DS_x S0_y/2 + S0_x DS_y/2 + DS_x DS_y/3;
+//   Jx(i+1/2,j) = -(q w/(dy dt)) sum_{i'<=i} Wx(i',j), Jy likewise along y,
+//   Jz(i,j) = q w vz Wz(i,j)/(dx dy),
+// so that (rho^{n+1} - rho^n)/dt + div J = 0 on the grid for the TSC charge of S0, S1.
+// T is double on the FP64 path and float on the mixed one; J is float (the grid's type)
+// and accumulated with atomic adds.
+template <typename T>
+__device__ __forceinline__ void tsc5(T X, int base, int shift, T S[5]) {
+  // the 3 TSC weights of position X (nearest node base + shift) on nodes base-2..base+2
+  const int ic = base + shift;
+  const T d = X - T(ic);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) S[k] = T(0);
+  const T lo = T(0.5) - d, hi = T(0.5) + d;
+  S[1 + shift] = T(0.5) * lo * lo;
+  S[2 + shift] = T(0.75) - d * d;
+  S[3 + shift] = T(0.5) * hi * hi;
+}
+
+template <typename T>
+__device__ __noinline__ void esirkepov_deposit(const qed_fields& f, T X0, T Y0, T X1, T Y1, T cx, T cy, T cz) {
+  const int i0 = (int)floor(X0 + T(0.5)), j0 = (int)floor(Y0 + T(0.5));
+  const int di = (int)floor(X1 + T(0.5)) - i0, dj = (int)floor(Y1 + T(0.5)) - j0;
+  if (di < -1 || di > 1 || dj < -1 || dj > 1) return;   // beyond the solver's CFL: not deposited
+  T S0x[5], S1x[5], S0y[5], S1y[5];
+  tsc5<T>(X0, i0, 0, S0x);
+  tsc5<T>(X1, i0, di, S1x);
+  tsc5<T>(Y0, j0, 0, S0y);
+  tsc5<T>(Y1, j0, dj, S1y);
+  const int nx = f.nx, ny = f.ny, per = f.periodic;
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    const int j = grid_node(j0 - 2 + b, ny, per);
+    const T dsy = S1y[b] - S0y[b];
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const T dsx = S1x[c] - S0x[c];
+      acc += dsx * (S0y[b] + T(0.5) * dsy);
+      const T wz = S0x[c] * S0y[b] + T(0.5) * dsx * S0y[b] + T(0.5) * S0x[c] * dsy + dsx * dsy * T(1.0 / 3.0);
+      const int i = grid_node(i0 - 2 + c, nx, per);
+      if (i < 0 || j < 0) continue;
+      const size_t k = (size_t)j * nx + i;
+      if (c < 4 && acc != T(0)) atomicAdd(f.gJx + k, (float)(cx * acc));
+      if (wz != T(0)) atomicAdd(f.gJz + k, (float)(cz * wz));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const int i = grid_node(i0 - 2 + c, nx, per);
+    const T dsx = S1x[c] - S0x[c];
+    T acc = T(0);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      acc += (S1y[b] - S0y[b]) * (S0x[c] + T(0.5) * dsx);
+      const int j = grid_node(j0 - 2 + b, ny, per);
+      if (i < 0 || j < 0 || acc == T(0)) continue;
+      atomicAdd(f.gJy + (size_t)j * nx + i, (float)(cy * acc));
+    }
+  }
+}
+
 // ======================================================================================
 // lepton streaming pass
 // ======================================================================================
-template <typename R, bool kB, bool kSm, bool kRad = false>
-__global__ void __launch_bounds__(kTile, kRad ? OccPh<R>::v : Occ<R>::v) k_lepton(const __grid_constant__ StepArgs a) {
+template <typename R, bool kB, bool kSm, bool kRad = false, bool kDep = false>
+__global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::v)
+    k_lepton(const __grid_constant__ StepArgs a) {
   __shared__ R s_rates[kSm ? kSmemRateLen : 1];
   __shared__ TileShared s_tile;
   __shared__ unsigned int s_off[kB ? kMaxEns + 1 : 1];
@@ -757,9 +833,25 @@ __global__ void __launch_bounds__(kTile, kRad ? OccPh<R>::v : Occ<R>::v) k_lepto
       const R inv_g1 = f_rsqrt(g12);
       const R g1 = g12 * inv_g1;
       if (sizeof(R) == 8) {
+        const double xo = x, yo = y;
         x += a.dt * (double)(pn.x / g1); y += a.dt * (double)(pn.y / g1); z += a.dt * (double)(pn.z / g1);
+        if constexpr (kDep) {
+          // the move x^n -> x^{n+1} in cell units, as the positions are stored
+          const qed_fields& f = E.f;
+          const double qw = (double)q * (double)ld<R>(L.w, i);
+          esirkepov_deposit<double>(f, (xo - f.x0) / f.dx, (yo - f.y0) / f.dy, (x - f.x0) / f.dx, (y - f.y0) / f.dy,
+                                    -qw / (f.dy * a.dt), -qw / (f.dx * a.dt), qw * (double)(pn.z / g1) / (f.dx * f.dy));
+        }
       } else {
         const R c = dt * inv_g1;
+        if constexpr (kDep) {
+          // cell coordinates in float (as the gather), the move from the float displacement
+          const float X0 = d2f_bits(x) * E.ff.gix - E.ff.gox, Y0 = d2f_bits(y) * E.ff.giy - E.ff.goy;
+          const float qw = (float)q * (float)ld<R>(L.w, i), idt = 1.0f / (float)dt;
+          esirkepov_deposit<float>(E.f, X0, Y0, X0 + (float)(c * pn.x) * E.ff.gix, Y0 + (float)(c * pn.y) * E.ff.giy,
+                                   -qw * E.ff.giy * idt, -qw * E.ff.gix * idt,
+                                   qw * (float)(c * pn.z) * idt * E.ff.gix * E.ff.giy);
+        }
         x = add_pos(x, c * pn.x); y = add_pos(y, c * pn.y); z = add_pos(z, c * pn.z);
       }
       if (a.flags & QED_F_NCS) {

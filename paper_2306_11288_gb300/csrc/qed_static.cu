@@ -115,7 +115,8 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
     return QED_ERR_INVALID_ARG;
   }
   {
-    const qed_status rf = check_fields(f, "qed_step_static");
+    qed_status rf = check_fields(f, "qed_step_static");
+    if (rf == QED_OK) rf = check_deposit(flags, f, "qed_step_static");
     if (rf != QED_OK) return rf;
   }
   const qed_precision pr = prec < 0 ? QED_PREC_F64 : (qed_precision)prec;

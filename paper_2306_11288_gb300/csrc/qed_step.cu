@@ -14,7 +14,10 @@ size_t ncs_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NcsRec
 // the lepton pass: with the radiative pusher flags its kRad instantiation
 template <typename R>
 static void launch_lepton(const StepArgs& a, int grid, cudaStream_t s) {
-  if (a.flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT)) k_lepton<R, false, true, true><<<grid, kTile, 0, s>>>(a);
+  const bool rad = a.flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT), dep = a.flags & QED_F_DEPOSIT;
+  if (rad && dep) k_lepton<R, false, true, true, true><<<grid, kTile, 0, s>>>(a);
+  else if (rad) k_lepton<R, false, true, true><<<grid, kTile, 0, s>>>(a);
+  else if (dep) k_lepton<R, false, true, false, true><<<grid, kTile, 0, s>>>(a);
   else k_lepton<R, false, true><<<grid, kTile, 0, s>>>(a);
 }
 
