@@ -27,6 +27,8 @@
 //
 // Every kernel is a template on <precision, kB (batched), ...>: qed_step.cu instantiates
 // the single-ensemble kernels, qed_batch.cu the batched ones.
+#include <type_traits>
+
 #include "qed_common.cuh"
 #include "qed_internal.h"
 #include "qed_mlp.cuh"
@@ -700,47 +702,127 @@ __device__ __forceinline__ void tsc5(T X, int base, int shift, T S[5]) {
   S[3 + shift] = T(0.5) * hi * hi;
 }
 
+// A lepton's move for the deposition, in cell units, and its charge factors
 template <typename T>
-__device__ __noinline__ void esirkepov_deposit(const qed_fields& f, T X0, T Y0, T X1, T Y1, T cx, T cy, T cz) {
-  const int i0 = (int)floor(X0 + T(0.5)), j0 = (int)floor(Y0 + T(0.5));
-  const int di = (int)floor(X1 + T(0.5)) - i0, dj = (int)floor(Y1 + T(0.5)) - j0;
-  if (di < -1 || di > 1 || dj < -1 || dj > 1) return;   // beyond the solver's CFL: not deposited
+struct DepMove {
+  T X0, Y0, X1, Y1;     // old and new position (cells)
+  T cx, cy, cz;         // -q w/(dy dt), -q w/(dx dt), q w vz/(dx dy)
+  int i0, j0;           // old nearest node
+  bool on;              // live and within one cell per axis
+};
+
+template <typename T>
+__device__ __forceinline__ void dep_move(DepMove<T>& m, T X0, T Y0, T X1, T Y1, T cx, T cy, T cz) {
+  m.X0 = X0; m.Y0 = Y0; m.X1 = X1; m.Y1 = Y1; m.cx = cx; m.cy = cy; m.cz = cz;
+  m.i0 = (int)floor(X0 + T(0.5));
+  m.j0 = (int)floor(Y0 + T(0.5));
+  const int di = (int)floor(X1 + T(0.5)) - m.i0, dj = (int)floor(Y1 + T(0.5)) - m.j0;
+  m.on = di >= -1 && di <= 1 && dj >= -1 && dj <= 1;   // beyond the solver's CFL: not deposited
+}
+
+// Every term of the move on the support of its shapes goes to add(component, i, j, value),
+// with the unwrapped node indices (i, j) of the component's position (Jx at i+1/2, Jy at
+// j+1/2).  The support is the union of the old and new 3-node stencils: faces outside it
+// carry no current (their cumulative sums vanish), so they are not visited.
+template <typename T, typename Add>
+__device__ __forceinline__ void esirkepov_terms(const DepMove<T>& m, Add add) {
+  const int i0 = m.i0, j0 = m.j0;
+  const int di = (int)floor(m.X1 + T(0.5)) - i0, dj = (int)floor(m.Y1 + T(0.5)) - j0;
   T S0x[5], S1x[5], S0y[5], S1y[5];
-  tsc5<T>(X0, i0, 0, S0x);
-  tsc5<T>(X1, i0, di, S1x);
-  tsc5<T>(Y0, j0, 0, S0y);
-  tsc5<T>(Y1, j0, dj, S1y);
-  const int nx = f.nx, ny = f.ny, per = f.periodic;
+  tsc5<T>(m.X0, i0, 0, S0x);
+  tsc5<T>(m.X1, i0, di, S1x);
+  tsc5<T>(m.Y0, j0, 0, S0y);
+  tsc5<T>(m.Y1, j0, dj, S1y);
+  const int cl = 1 + (di < 0 ? di : 0), ch = 3 + (di > 0 ? di : 0);
+  const int bl = 1 + (dj < 0 ? dj : 0), bh = 3 + (dj > 0 ? dj : 0);
+  // unrolled over the 5 stencil nodes (register arrays), predicated on the support
 #pragma unroll
   for (int b = 0; b < 5; ++b) {
-    const int j = grid_node(j0 - 2 + b, ny, per);
+    if (b < bl || b > bh) continue;
     const T dsy = S1y[b] - S0y[b];
     T acc = T(0);
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
+      if (c < cl || c > ch) continue;
       const T dsx = S1x[c] - S0x[c];
       acc += dsx * (S0y[b] + T(0.5) * dsy);
       const T wz = S0x[c] * S0y[b] + T(0.5) * dsx * S0y[b] + T(0.5) * S0x[c] * dsy + dsx * dsy * T(1.0 / 3.0);
-      const int i = grid_node(i0 - 2 + c, nx, per);
-      if (i < 0 || j < 0) continue;
-      const size_t k = (size_t)j * nx + i;
-      if (c < 4 && acc != T(0)) atomicAdd(f.gJx + k, (float)(cx * acc));
-      if (wz != T(0)) atomicAdd(f.gJz + k, (float)(cz * wz));
+      if (c < ch && acc != T(0)) add(0, i0 - 2 + c, j0 - 2 + b, (float)(m.cx * acc));
+      if (wz != T(0)) add(2, i0 - 2 + c, j0 - 2 + b, (float)(m.cz * wz));
     }
   }
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    const int i = grid_node(i0 - 2 + c, nx, per);
+    if (c < cl || c > ch) continue;
     const T dsx = S1x[c] - S0x[c];
     T acc = T(0);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
+      if (b < bl || b >= bh) continue;
       acc += (S1y[b] - S0y[b]) * (S0x[c] + T(0.5) * dsx);
-      const int j = grid_node(j0 - 2 + b, ny, per);
-      if (i < 0 || j < 0 || acc == T(0)) continue;
-      atomicAdd(f.gJy + (size_t)j * nx + i, (float)(cy * acc));
+      if (acc != T(0)) add(1, i0 - 2 + c, j0 - 2 + b, (float)(m.cy * acc));
     }
   }
+}
+
+// Deposition of one tile of leptons.  The current is first summed in a shared-memory
+// window covering every stencil of the tile (tile-sorted particles share a few grid
+// cells), then added to the grid once per window cell; tiles whose stencils do not fit
+// the window add every term to the grid directly.  Float atomics in both cases.
+// Window cells: with the rate tables the block's static shared memory stays below 48 KB
+// (mixed: 14 KB of tables + 33 KB of window; FP64: 28 KB + 19 KB).
+template <typename T> struct DepWin { static constexpr int v = sizeof(T) == 4 ? 2816 : 1600; };
+template <typename T>
+struct DepShared {
+  int imin, imax, jmin, jmax;
+  float J[3 * DepWin<T>::v];
+};
+
+template <typename T>
+__device__ __forceinline__ void deposit_tile(const qed_fields& f, const DepMove<T>& m, DepShared<T>& sh) {
+  const int nx = f.nx, ny = f.ny, per = f.periodic;
+  float* const gJ[3] = {f.gJx, f.gJy, f.gJz};
+  if (threadIdx.x == 0) {
+    sh.imin = 0x7fffffff; sh.jmin = 0x7fffffff; sh.imax = -0x7fffffff; sh.jmax = -0x7fffffff;
+  }
+  __syncthreads();
+  if (m.on) {
+    atomicMin(&sh.imin, m.i0); atomicMax(&sh.imax, m.i0);
+    atomicMin(&sh.jmin, m.j0); atomicMax(&sh.jmax, m.j0);
+  }
+  __syncthreads();
+  const int imin = sh.imin, imax = sh.imax, jmin = sh.jmin, jmax = sh.jmax;
+  if (imax < imin) {            // nothing to deposit in this tile
+    __syncthreads();
+    return;
+  }
+  const long long ww = (long long)imax - imin + 5, wh = (long long)jmax - jmin + 5;
+  if (ww * wh <= DepWin<T>::v) {
+    const int w = (int)ww, h = (int)wh, wi0 = imin - 2, wj0 = jmin - 2, nc = w * h;
+    for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) sh.J[k] = 0.0f;
+    __syncthreads();
+    if (m.on)
+      esirkepov_terms<T>(m, [&](int comp, int i, int j, float v) {
+        atomicAdd(&sh.J[comp * nc + (j - wj0) * w + (i - wi0)], v);
+      });
+    __syncthreads();
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+      const int gi = grid_node(wi0 + k % w, nx, per), gj = grid_node(wj0 + k / w, ny, per);
+      if (gi < 0 || gj < 0) continue;
+      const size_t o = (size_t)gj * nx + gi;
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        const float v = sh.J[comp * nc + k];
+        if (v != 0.0f) atomicAdd(gJ[comp] + o, v);
+      }
+    }
+  } else if (m.on) {
+    esirkepov_terms<T>(m, [&](int comp, int i, int j, float v) {
+      const int gi = grid_node(i, nx, per), gj = grid_node(j, ny, per);
+      if (gi >= 0 && gj >= 0) atomicAdd(gJ[comp] + (size_t)gj * nx + gi, v);
+    });
+  }
+  __syncthreads();   // the window and its bounds are reused by the next tile
 }
 
 // ======================================================================================
@@ -753,6 +835,7 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
   __shared__ TileShared s_tile;
   __shared__ unsigned int s_off[kB ? kMaxEns + 1 : 1];
   __shared__ unsigned int s_et[kB ? kMaxEns : 1];
+  __shared__ typename std::conditional<kDep, DepShared<R>, char>::type s_dep;
   DevState* gst = a.st;
   unsigned int ntiles, t0s = 0;
   unsigned long long n0s = 0, n1s = 0;   // single ensemble: its e-, e+ counts, read once
@@ -789,6 +872,8 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
     const bool live = i < (unsigned int)nsp;
     const R q = sp_idx == 0 ? R(-1) : R(1);
     bool emit = false, range = false;
+    DepMove<R> dm;
+    dm.on = false;
     R chi = 0;
     V3<R> av = mk<R>(0, 0, 0);
     if (live) {
@@ -839,8 +924,8 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
           // the move x^n -> x^{n+1} in cell units, as the positions are stored
           const qed_fields& f = E.f;
           const double qw = (double)q * (double)ld<R>(L.w, i);
-          esirkepov_deposit<double>(f, (xo - f.x0) / f.dx, (yo - f.y0) / f.dy, (x - f.x0) / f.dx, (y - f.y0) / f.dy,
-                                    -qw / (f.dy * a.dt), -qw / (f.dx * a.dt), qw * (double)(pn.z / g1) / (f.dx * f.dy));
+          dep_move<R>(dm, (xo - f.x0) / f.dx, (yo - f.y0) / f.dy, (x - f.x0) / f.dx, (y - f.y0) / f.dy,
+                      -qw / (f.dy * a.dt), -qw / (f.dx * a.dt), qw * (double)(pn.z / g1) / (f.dx * f.dy));
         }
       } else {
         const R c = dt * inv_g1;
@@ -848,9 +933,8 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
           // cell coordinates in float (as the gather), the move from the float displacement
           const float X0 = d2f_bits(x) * E.ff.gix - E.ff.gox, Y0 = d2f_bits(y) * E.ff.giy - E.ff.goy;
           const float qw = (float)q * (float)ld<R>(L.w, i), idt = 1.0f / (float)dt;
-          esirkepov_deposit<float>(E.f, X0, Y0, X0 + (float)(c * pn.x) * E.ff.gix, Y0 + (float)(c * pn.y) * E.ff.giy,
-                                   -qw * E.ff.giy * idt, -qw * E.ff.gix * idt,
-                                   qw * (float)(c * pn.z) * idt * E.ff.gix * E.ff.giy);
+          dep_move<R>(dm, X0, Y0, X0 + (float)(c * pn.x) * E.ff.gix, Y0 + (float)(c * pn.y) * E.ff.giy,
+                      -qw * E.ff.giy * idt, -qw * E.ff.gix * idt, qw * (float)(c * pn.z) * idt * E.ff.gix * E.ff.giy);
         }
         x = add_pos(x, c * pn.x); y = add_pos(y, c * pn.y); z = add_pos(z, c * pn.z);
       }
@@ -907,6 +991,7 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
       stv<R>(L.px, i, pn.x); stv<R>(L.py, i, pn.y); stv<R>(L.pz, i, pn.z);
       stv<R>(L.s1, i, S.x); stv<R>(L.s2, i, S.y); stv<R>(L.s3, i, S.z);
     }
+    if constexpr (kDep) deposit_tile<R>(E.f, dm, s_dep);
     count_event(&st->ev[sp_idx], emit);
     count_event(&st->ev[3], range);
     unsigned int r_in;

@@ -95,17 +95,27 @@ def _div_j(J, dx, dy, periodic):
     return d
 
 
+def _cell_sorted(d, dx, dy):
+    o = np.lexsort((np.floor(d["x"] / dx), np.floor(d["y"] / dy)))
+    return {k: v[o] for k, v in d.items()}
+
+
 @pytest.mark.parametrize("prec", [q.QED_PREC_F64, q.QED_PREC_MIXED])
 @pytest.mark.parametrize("periodic", [1, 0])
-def test_deposit_matches_oracle_and_conserves_charge(orc, ctx, prec, periodic):
+@pytest.mark.parametrize("order", ["random", "cell-sorted"])
+def test_deposit_matches_oracle_and_conserves_charge(orc, ctx, prec, periodic, order):
     """One step of e- and e+ (ragged counts, several tiles) with zero fields: the deposited
-    current against the oracle's, and the continuity equation on the library's current."""
+    current against the oracle's, and the continuity equation on the library's current.
+    Random order: every tile spans the grid (direct atomic adds to the grid); cell-sorted:
+    each tile's stencils fit the shared-memory window (summed there, then added)."""
     nx, ny, dx, dy, dt = 64, 48, 0.3, 0.25, 0.11
     rng = np.random.default_rng(5 + periodic)
     m = 0.0 if periodic else 3.0
     box = ((m * dx, (nx - m) * dx), (m * dy, (ny - m) * dy))
     e = _leptons(3001, rng, box, 3.0)
     pos = _leptons(1299, rng, box, 3.0, first=3001)
+    if order == "cell-sorted":
+        e, pos = _cell_sorted(e, dx, dy), _cell_sorted(pos, dx, dy)
     wl = {"e": e, "pos": pos, "ph": workloads.empty(True), "dt": dt, "seed": 1, "next_id": 4300}
     sim = q.PicSimulation(wl, nx, ny, dx, dy, periodic=periodic, prec=prec, ctx=ctx)
     # the deposit alone: one qed_step with QED_F_DEPOSIT on the zero grid (no FDTD)
