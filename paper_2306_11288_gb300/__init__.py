@@ -482,6 +482,7 @@ class Simulation:
                          for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz")}
             self.grid.update({k: g[k] for k in ("dx", "dy") if k in g})
             self.grid.update({k: g.get(k, 0.0) for k in ("x0", "y0")})
+            self.grid["periodic"] = int(g.get("periodic", 0))
         self.fields = fields_from_spec(wl["field"], self.grid)
         self.dt = float(wl["dt"])
         self.t = float(wl.get("t0", 0.0))

@@ -166,6 +166,23 @@ __device__ __forceinline__ int find_ens(const unsigned int* off, int n, unsigned
   return lo;
 }
 
+// block-wide bounds of (i, j) over the threads with on = true, into b[0..3] = imin, imax,
+// jmin, jmax (shared): one warp reduction and one shared atomic per warp and bound
+__device__ __forceinline__ void block_bounds(bool on, int i, int j, int* b) {
+  if (threadIdx.x == 0) {
+    b[0] = 0x7fffffff; b[1] = -0x7fffffff; b[2] = 0x7fffffff; b[3] = -0x7fffffff;
+  }
+  __syncthreads();
+  const int imin = __reduce_min_sync(0xffffffffu, on ? i : 0x7fffffff);
+  const int imax = __reduce_max_sync(0xffffffffu, on ? i : -0x7fffffff);
+  const int jmin = __reduce_min_sync(0xffffffffu, on ? j : 0x7fffffff);
+  const int jmax = __reduce_max_sync(0xffffffffu, on ? j : -0x7fffffff);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(b, imin); atomicMax(b + 1, imax);
+    atomicMin(b + 2, jmin); atomicMax(b + 3, jmax);
+  }
+  __syncthreads();
+}
 // FP64 path: the field formulas in double.  Mixed path: the phase is formed in float from
 // host-reduced time offsets (t - phi0 and t mod 2 pi) plus float(z).
 template <typename R>
@@ -774,7 +791,7 @@ __device__ __forceinline__ void esirkepov_terms(const DepMove<T>& m, Add add) {
 template <typename T> struct DepWin { static constexpr int v = sizeof(T) == 4 ? 2816 : 1600; };
 template <typename T>
 struct DepShared {
-  int imin, imax, jmin, jmax;
+  int bnd[4];           // imin, imax, jmin, jmax of the tile's nearest nodes
   float J[3 * DepWin<T>::v];
 };
 
@@ -782,16 +799,8 @@ template <typename T>
 __device__ __forceinline__ void deposit_tile(const qed_fields& f, const DepMove<T>& m, DepShared<T>& sh) {
   const int nx = f.nx, ny = f.ny, per = f.periodic;
   float* const gJ[3] = {f.gJx, f.gJy, f.gJz};
-  if (threadIdx.x == 0) {
-    sh.imin = 0x7fffffff; sh.jmin = 0x7fffffff; sh.imax = -0x7fffffff; sh.jmax = -0x7fffffff;
-  }
-  __syncthreads();
-  if (m.on) {
-    atomicMin(&sh.imin, m.i0); atomicMax(&sh.imax, m.i0);
-    atomicMin(&sh.jmin, m.j0); atomicMax(&sh.jmax, m.j0);
-  }
-  __syncthreads();
-  const int imin = sh.imin, imax = sh.imax, jmin = sh.jmin, jmax = sh.jmax;
+  block_bounds(m.on, m.i0, m.j0, sh.bnd);
+  const int imin = sh.bnd[0], imax = sh.bnd[1], jmin = sh.bnd[2], jmax = sh.bnd[3];
   if (imax < imin) {            // nothing to deposit in this tile
     __syncthreads();
     return;
@@ -806,14 +815,21 @@ __device__ __forceinline__ void deposit_tile(const qed_fields& f, const DepMove<
         atomicAdd(&sh.J[comp * nc + (j - wj0) * w + (i - wi0)], v);
       });
     __syncthreads();
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-      const int gi = grid_node(wi0 + k % w, nx, per), gj = grid_node(wj0 + k / w, ny, per);
-      if (gi < 0 || gj < 0) continue;
-      const size_t o = (size_t)gj * nx + gi;
+    // one warp per window row, lanes along the row
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int lj = threadIdx.x >> 5; lj < h; lj += nwarp) {
+      const int gj = grid_node(wj0 + lj, ny, per);
+      if (gj < 0) continue;
+      for (int li = lane; li < w; li += 32) {
+        const int gi = grid_node(wi0 + li, nx, per);
+        if (gi < 0) continue;
+        const size_t o = (size_t)gj * nx + gi;
+        const int k = lj * w + li;
 #pragma unroll
-      for (int comp = 0; comp < 3; ++comp) {
-        const float v = sh.J[comp * nc + k];
-        if (v != 0.0f) atomicAdd(gJ[comp] + o, v);
+        for (int comp = 0; comp < 3; ++comp) {
+          const float v = sh.J[comp * nc + k];
+          if (v != 0.0f) atomicAdd(gJ[comp] + o, v);
+        }
       }
     }
   } else if (m.on) {
@@ -876,8 +892,11 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
     dm.on = false;
     R chi = 0;
     V3<R> av = mk<R>(0, 0, 0);
+    double x = 0.0, y = 0.0, z = 0.0;
     if (live) {
-      double x = L.x[i], y = L.y[i], z = L.z[i];
+      x = L.x[i]; y = L.y[i]; z = L.z[i];
+    }
+    if (live) {
       V3<R> p = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
       V3<R> S = mk<R>(ld<R>(L.s1, i), ld<R>(L.s2, i), ld<R>(L.s3, i));
       const uint64_t id = L.id[i];

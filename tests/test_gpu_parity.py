@@ -192,6 +192,29 @@ def test_uniform_field_grid_matches_analytic_gather(orc, ctx):
     _compare_all(sim, osim, 1e-9, 1e-9)
 
 
+@pytest.mark.parametrize("periodic", [0, 1])
+def test_grid_gather_independent_of_particle_order(ctx, periodic):
+    """Mixed path: the same particles tile-sorted and shuffled (every tile then spans the
+    grid) give the same momenta, spins and positions bit for bit (push and spin only: no
+    events, so nothing may depend on the order); bounded and periodic grids."""
+    g = workloads.c3_grid(nx=256, ny=128, a0=150.0)
+    g["periodic"] = periodic
+    wl = workloads.c3(n=20000, seed=14, nx=256, ny=128, grid=g)
+    rng = np.random.default_rng(2)
+    perm = rng.permutation(len(wl["e"]["id"]))
+    wl2 = dict(wl, e={k: v[perm] for k, v in wl["e"].items()})
+    out = []
+    for w in (wl, wl2):
+        sim = q.Simulation(w, prec=q.QED_PREC_MIXED, ctx=ctx)
+        sim.run(15, q.QED_F_SPIN)
+        out.append(_by_id(sim.state()["e"]))
+        sim.close()
+    moved = np.abs(out[0]["py"]).max()
+    assert moved > 1.0   # the fields acted
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
 # ---------------------------------------------------------------------------------------
 def test_mixed_precision_short_run_per_particle(orc, ctx):
     """Mixed path: per-particle 2e-5 against the FP64 oracle over a short run (particles
