@@ -298,11 +298,13 @@ def c4_workload(seed=4):
     return wls
 
 
-def run_c4(q, torch, steps, warmup, tune_steps=2):
+def run_c4(q, torch, steps, warmup, tune_steps=2, f64_steps=10):
     """Batched ensembles: CUDA-graph replay of one batched step after the autotuner picked
     the launch shape.  For comparison the same ensembles, advanced to the same step on a
     second copy (runs are deterministic), step one by one with qed_step over the same
-    segment of the trajectory."""
+    segment of the trajectory; and an FP64 batch of the same ensembles, advanced to the
+    same step, over f64_steps steps of that segment.  Streamed bytes: the mean live e-, e+
+    and photons of the timed window (start and end) times 104 / 100 B per particle-step."""
     wls = c4_workload()
     caps = []
     for wl in wls:
@@ -315,6 +317,10 @@ def run_c4(q, torch, steps, warmup, tune_steps=2):
     def processed(b):
         return int(torch.stack([s.stats for s in b.sims]).sum(0)[6].item())
 
+    def live(b):
+        lep = sum(s.e.count() + s.pos.count() for s in b.sims)
+        return lep, sum(s.ph.count() for s in b.sims)
+
     b = q.Batch(wls, prec=q.QED_PREC_MIXED, flags=flags, caps=caps)
     b.run(C4_PRE)
     cfg, tune_rate = q.qed_batch_tune(b.b, tune_steps)
@@ -322,14 +328,31 @@ def run_c4(q, torch, steps, warmup, tune_steps=2):
     torch.cuda.synchronize()
     done = b.clocks()[0][1] - wls[0]["step0"]
     p0 = processed(b)
+    l0, g0 = live(b)
     ev0.record()
     b.run(steps)
     ev1.record()
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
     value = (processed(b) - p0) / (ms * 1e-3)
+    l1, g1 = live(b)
+    gbs = 0.5 * ((l0 + l1) * BYTES["mixed"]["lep"] + (g0 + g1) * BYTES["mixed"]["ph"]) * steps / (ms * 1e-3) / 1e9
     status = q.qed_read_status(b.ctx)
     b.close()
+    # FP64 batch of the same ensembles over the start of the same segment
+    f64 = None
+    if f64_steps > 0:
+        b = q.Batch(c4_workload(), prec=q.QED_PREC_F64, flags=flags, caps=caps)
+        b.run(done)
+        torch.cuda.synchronize()
+        p0 = processed(b)
+        ev0.record()
+        b.run(f64_steps)
+        ev1.record()
+        ev1.synchronize()
+        ms64 = ev0.elapsed_time(ev1)
+        f64 = {"value": (processed(b) - p0) / (ms64 * 1e-3), "ms_per_step": ms64 / f64_steps, "steps": f64_steps}
+        b.close()
     # second copy, advanced to the same step, then one qed_step per ensemble per step
     b = q.Batch(c4_workload(), prec=q.QED_PREC_MIXED, flags=flags, caps=caps)
     b.run(done)
@@ -352,6 +375,8 @@ def run_c4(q, torch, steps, warmup, tune_steps=2):
             "sequential_qed_step": {"value": seq_value, "ms_per_step": ms_seq / steps,
                                     "note": "same ensembles, same steps, 64 qed_step calls per step"},
             "batched_over_sequential": value / seq_value, "status": status,
+            "step_GBs_approx": gbs, "step_hbm_frac_approx": gbs / _peaks()[0],
+            "f64": f64, "speedup_mixed_over_f64": value / f64["value"] if f64 else None,
             "l2": "not flushed: every step streams > 1 GB of particle state (L2 is 129 MB)"}
 
 
