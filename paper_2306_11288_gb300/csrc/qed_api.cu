@@ -39,6 +39,7 @@ static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s)
 extern "C" const char* qed_last_error(void) { return g_err; }
 
 extern "C" qed_status qed_init_tables(qed_ctx** out, void* stream) {
+  const qedk::NvtxRange nvtx_range("qed_init_tables");
   if (!out) FAIL(QED_ERR_INVALID_ARG, "qed_init_tables: out is NULL");
   *out = nullptr;
   g_err[0] = 0;
@@ -420,6 +421,7 @@ static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos
 extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
                                const qed_fields* f, double t, double dt, uint64_t seed, uint32_t step,
                                uint32_t flags, qed_step_stats* dev_stats, void* stream) {
+  const qedk::NvtxRange nvtx_range("qed_step");
   qed_precision prec;
   qed_status r = validate_step(c, e, pos, ph, f, dt, flags, &prec);
   if (r != QED_OK) return r;
@@ -498,6 +500,7 @@ extern "C" qed_status qed_step_host(qed_ctx* c, qed_particles* e, qed_particles*
                                     const qed_soa* he, const qed_soa* hp, const qed_soa* hg, uint64_t n_host[3],
                                     const qed_fields* f, double t, double dt, uint64_t seed, uint32_t step,
                                     uint32_t flags, void* stream) {
+  const qedk::NvtxRange nvtx_range("qed_step_host");
   qed_precision prec;
   qed_status r = validate_step(c, e, pos, ph, f, dt, flags, &prec);
   if (r != QED_OK) return r;

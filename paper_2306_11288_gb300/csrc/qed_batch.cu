@@ -358,6 +358,7 @@ static qed_status batch_capture(qed_batch* b) {
 }
 
 extern "C" qed_status qed_batch_run(qed_batch* b, uint32_t nsteps, void* stream) {
+  const qedk::NvtxRange nvtx_range("qed_batch_run");
   if (!b) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_run: batch is NULL");
   if (!b->graph_ok) {
     const qed_status r = batch_capture(b);

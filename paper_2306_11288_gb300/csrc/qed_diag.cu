@@ -146,6 +146,7 @@ using namespace qedk;
 
 extern "C" qed_status qed_diag(qed_ctx* c, const qed_particles* set, const qed_diag_spec* spec, double* dev_out,
                                void* stream) {
+  const qedk::NvtxRange nvtx_range("qed_diag");
   if (!c || !c->alive) {
     set_error("qed_diag: invalid context");
     return QED_ERR_NOT_INITIALIZED;

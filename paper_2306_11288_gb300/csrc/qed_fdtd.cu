@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(256) k_fdtd_e(qed_grid2d g, float cdx, float c
 using namespace qedk;
 
 extern "C" qed_status qed_fdtd_advance(const qed_grid2d* g, int which, double dt, void* stream) {
+  const qedk::NvtxRange nvtx_range("qed_fdtd_advance");
   if (!g) {
     set_error("qed_fdtd_advance: grid is NULL");
     return QED_ERR_INVALID_ARG;

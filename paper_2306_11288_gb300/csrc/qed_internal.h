@@ -1,6 +1,7 @@
 // qed_internal.h -- host-side internals shared by the library's translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 
@@ -12,6 +13,14 @@ struct DevState;
 
 // thread-local error message (qed_last_error)
 void set_error(const char* fmt, ...);
+
+// NVTX range over a host entry point (visible in Nsight timelines; inert without a tool)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // builds the FP64 tables into d64 (kTableLen doubles) and the float copy into d32
 qed_status build_tables(double* d64, float* d32, cudaStream_t st);
