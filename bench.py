@@ -120,6 +120,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def replica_seed(rank):
+    """seed of the 1e6-electron workload on a rank: replicas are independent collisions"""
+    return 2 + rank
+
+
+def aggregate(torch, dist, device, ms, parts):
+    """whole-job timing over replicas: the slowest rank's time and every rank's particle-steps
+    (identity without a process group)"""
+    if dist is None:
+        return ms, parts
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([parts], device=device, dtype=torch.float64)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def run_gpu_path(q, torch, wl, prec, steps, warmup, flush, flags, kernel_steps, pre=PRE_STEPS, caps=None):
     """Pre-run, warm up, time `steps` steps (the headline), then `kernel_steps` more steps
     with the library's per-kernel timing on (kernels serialised, event records and a sync
@@ -515,7 +532,7 @@ def run_e2e(q, torch, sim, prec, steps, flags):
         sim.step_no += 1
     el = time.perf_counter() - t0
     return {"value": tot_p / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // steps,
-            "d2h_bytes_per_step": d2h // steps, "steps": steps}
+            "d2h_bytes_per_step": d2h // steps, "steps": steps, "particles": tot_p, "seconds": el}
 
 
 def oracle_sample(n_e, steps_timed, warmup=0, seed=2):
@@ -585,6 +602,10 @@ def main():
     import torch
     import paper_2306_11288_gb300 as q
 
+    if world > 1:
+        # replicas: the headline and e2e on every rank; the single-GPU side legs only at N = 1
+        args.c3_steps = args.c4_steps = args.c5_steps = args.rr_steps = args.pic_steps = 0
+        args.no_f64 = True
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -596,7 +617,7 @@ def main():
         dist.barrier()
     flags = q.QED_F_NCS | q.QED_F_NBW | q.QED_F_VB | q.QED_F_SPIN
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    wl = c2_workload(args.n, seed=2 + rank)
+    wl = c2_workload(args.n, seed=replica_seed(rank))
 
     if dist is not None:
         dist.barrier()
@@ -609,7 +630,7 @@ def main():
         dist.barrier()
     f64 = None
     if not args.no_f64:
-        sim64, f64 = run_gpu_path(q, torch, c2_workload(args.n, seed=2 + rank), q.QED_PREC_F64, args.steps,
+        sim64, f64 = run_gpu_path(q, torch, c2_workload(args.n, seed=replica_seed(rank)), q.QED_PREC_F64, args.steps,
                                   args.warmup, flush, flags, min(args.kernel_steps, args.steps))
         sim64.close()
     diag = run_diag(q, torch, sim)
@@ -621,13 +642,11 @@ def main():
     c5 = run_c5(q, torch, args.c5_steps) if args.c5_steps > 0 else None
     e2e = run_e2e(q, torch, sim, q.QED_PREC_MIXED, args.e2e_steps, flags)
 
-    ms, parts = info["ms"], info["particles"]
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        p = torch.tensor([parts], device="cuda", dtype=torch.float64)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        ms, parts = float(t.item()), float(p.item())
+    ms, parts = aggregate(torch, dist, "cuda", info["ms"], info["particles"])
+    e2e_ms, e2e_parts = aggregate(torch, dist, "cuda", 1e3 * e2e["seconds"], e2e["particles"])
+    e2e["value"] = e2e_parts / (e2e_ms * 1e-3)
+    for k in ("h2d_bytes_per_step", "d2h_bytes_per_step"):   # whole job: every rank's copies
+        e2e[k] = int(aggregate(torch, dist, "cuda", 0.0, e2e[k])[1])
     if rank != 0:
         sim.close()
         dist.destroy_process_group()

@@ -1,0 +1,61 @@
+"""The multi-GPU form of the benchmark is replicas: every rank steps its own collision
+(seed per rank) with no data-path collective, and only the timing is combined -- the
+slowest rank's time and the sum of every rank's particle-steps.  This runs the combining
+step on two gloo ranks on the CPU, and the reference arm's rank rule (rank 0 alone
+works and prints; the others exit 0 silently)."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms, parts = bench.aggregate(torch, dist, "cpu", 10.0 + rank, 1000.0 * (rank + 1))
+    seeds = [None] * world
+    dist.all_gather_object(seeds, bench.replica_seed(rank))
+    out.put((rank, ms, parts, seeds))
+    dist.destroy_process_group()
+
+
+def test_replica_timing_is_combined_over_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, parts, seeds in res:
+        assert ms == 11.0            # the slowest rank
+        assert parts == 3000.0       # every rank's particle-steps
+        assert len(set(seeds)) == 2  # independent replicas
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2"],
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
