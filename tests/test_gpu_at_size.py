@@ -170,6 +170,12 @@ def _sample_parity(orc, sim, wl, pre, tol, max_mismatch):
     sim.run(1, ALL)
     torch.cuda.synchronize()
     assert sim.status() == 0
+    return _compare_sample(orc, sim, wl, pre, t, step, qed_next_id, tol, max_mismatch)
+
+
+def _compare_sample(orc, sim, wl, pre, t, step, qed_next_id, tol, max_mismatch):
+    """the sampled rows `pre` (state at (t, step)) stepped once by the oracle, against the
+    rows of the same ids in the GPU set after its step"""
     pick = {sp: np.sort(pre[sp]["id"]) for sp in ("e", "pos", "ph")}
     post = {sp: _rows_of_ids(getattr(sim, sp), pick[sp]) for sp in ("e", "pos", "ph")}
     owl = {"field": wl["field"], "dt": wl["dt"], "seed": wl["seed"], "t0": t, "step0": step,
@@ -271,3 +277,42 @@ def test_grid_workload_sampled_parity_fp64(orc, ctx, grid_wl):
 
 def test_grid_workload_sampled_parity_mixed(orc, ctx, grid_wl):
     _grid_sample_step(orc, ctx, grid_wl, q.QED_PREC_MIXED, 2e-5, 0.005)
+
+
+def test_batch_workload_sampled_parity_mixed(orc, ctx):
+    """The 64-ensemble batch at its full size (sizes 10^U(3,6), a0 10-200, gamma0 500-2e4,
+    LP/CP, every fourth a gamma beam) in the benchmark's launch configuration (graph replay
+    of one batched step): 150 steps in, one more batched step, and for eight ensembles a
+    sample of their particles stepped by the oracle from the same pre-step state (each
+    ensemble's own field, seed and clock), compared one by one (mixed path: 2e-5, at most
+    0.5 % decision differences)."""
+    import bench
+    wls = bench.c4_workload()
+    caps = []
+    for wl in wls:
+        n = len(wl["e"]["id"]) + len(wl["ph"]["id"])
+        caps.append({"cap_e": n + n // 2 + 4096, "cap_p": n // 2 + 4096, "cap_ph": 24 * n + 4096})
+    b = q.Batch(wls, prec=q.QED_PREC_MIXED, flags=ALL, ctx=ctx, caps=caps)
+    b.run(bench.C4_PRE)
+    torch.cuda.synchronize()
+    sizes = np.array([len(w["e"]["id"]) + len(w["ph"]["id"]) for w in wls])
+    order = np.argsort(sizes)
+    chosen = list(order[-4:]) + list(order[len(order) // 2: len(order) // 2 + 2]) + [3, 7]   # big, middle, gamma beams
+    rng = np.random.default_rng(8)
+    pres, clocks = {}, b.clocks()
+    for k in chosen:
+        s = b.sims[k]
+        pres[k] = ({sp: _pick(getattr(s, sp), n, rng) for sp, n in (("e", 1500), ("pos", 500), ("ph", 2000))},
+                   q.qed_get_next_id(s.ctx))
+    b.run(1)
+    torch.cuda.synchronize()
+    assert q.qed_read_status(b.ctx) == 0
+    total_nbw = total_ncs = 0
+    for k in chosen:
+        pre, nid = pres[k]
+        t, step = clocks[k]
+        ost = _compare_sample(orc, b.sims[k], wls[k], pre, t, step, nid, 2e-5, 0.005)
+        total_ncs += ost["n_ncs_e"]
+        total_nbw += ost["n_nbw"]
+    assert total_ncs > 0 and total_nbw > 0
+    b.close()
