@@ -226,6 +226,18 @@ def run_c3(q, torch, steps, warmup, flush, f64_steps, kernel_steps):
         sim.close()
     if "mixed" in out and "f64" in out:
         out["speedup_mixed"] = out["mixed"]["value"] / out["f64"]["value"]
+    # the same electrons ordered by cell inside each tile (what a periodic cell sort of a
+    # PIC code keeps): the grid gather's loads of a warp then share cache lines
+    if steps > 0:
+        wl_c = dict(wl, e=workloads.cell_sort(wl["e"], wl["grid"]))
+        sim, info = run_gpu_path(q, torch, wl_c, q.QED_PREC_MIXED, steps, warmup, flush, flags, kernel_steps,
+                                 pre=C3_PRE, caps=caps)
+        kn = info["kern"]
+        ks = max(kn["kernel_steps"], 1)
+        out["mixed_cell_sorted"] = {"value": info["particles"] / (info["ms"] * 1e-3),
+                                    "ms_per_step": info["ms"] / steps, "steps": steps, "status": info["status"],
+                                    "k_lepton_ms": kn["kernel_ms"][1] / ks, "k_photon_ms": kn["kernel_ms"][0] / ks}
+        sim.close()
     return out
 
 
