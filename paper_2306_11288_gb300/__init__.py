@@ -35,7 +35,7 @@ ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particle
                  "qed_batch_step", "qed_batch_run", "qed_batch_clock", "qed_batch_get_config",
                  "qed_batch_set_config", "qed_batch_tune", "qed_batch_destroy", "qed_mlp_train",
                  "qed_mlp_set_params", "qed_mlp_get_params", "qed_mlp_eval", "qed_mlp_target", "qed_fdtd_advance",
-                 "qed_last_error")
+                 "qed_sort_cells", "qed_last_error")
 MLP_PARAMS = 4481
 QED_DIAG_SPECTRUM, QED_DIAG_DETECTOR = 0, 1
 
@@ -128,6 +128,7 @@ def lib():
         L.qed_mlp_eval.argtypes = [vp, vp, vp, u64, vp]
         L.qed_mlp_target.argtypes = [vp, vp, vp, u64, vp]
         L.qed_fdtd_advance.argtypes = [C.POINTER(qed_grid2d), C.c_int, d, vp]
+        L.qed_sort_cells.argtypes = [vp, vp, C.POINTER(qed_fields), vp]
         L.qed_last_error.restype = C.c_char_p
         for name in ABI_FUNCTIONS:
             if name != "qed_last_error":
@@ -454,6 +455,10 @@ def fields_from_spec(spec: dict, grid=None) -> qed_fields:
             if k in grid:
                 setattr(f, "g" + k, grid[k].data_ptr())
     return f
+
+
+def qed_sort_cells(ctx, handle, grid: qed_fields, stream=None):
+    _check(lib().qed_sort_cells(ctx, handle, C.byref(grid), _stream(stream)), "qed_sort_cells")
 
 
 def qed_fdtd_advance(g: qed_grid2d, which, dt, stream=None):

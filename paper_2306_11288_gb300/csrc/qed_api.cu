@@ -131,6 +131,7 @@ extern "C" qed_status qed_destroy(qed_ctx* c) {
   for (int k = 0; k < 6; ++k)
     if (c->tev[k]) cudaEventDestroy(c->tev[k]);
   if (c->diag_buf) cudaFree(c->diag_buf);
+  if (c->sort_buf) cudaFree(c->sort_buf);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
   if (c->side) cudaStreamDestroy(c->side);

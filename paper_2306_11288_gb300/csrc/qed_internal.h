@@ -146,6 +146,8 @@ struct qed_ctx {
   unsigned long long tsteps;
   void* diag_buf;                     // per-block partial histograms of qed_diag
   size_t diag_bytes;
+  void* sort_buf;                     // qed_sort_cells scratch (keys, indices, one array)
+  size_t sort_bytes;
 };
 
 struct qed_particles {

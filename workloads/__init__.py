@@ -130,18 +130,6 @@ def c3_grid(nx=4096, ny=2048, a0=150.0, ncrit=100.0, seed=3):
             "xs": xs}
 
 
-def cell_sort(e, grid):
-    """the same particles ordered by 32x32-cell tile and, inside a tile, by cell (row-major):
-    the within-tile order a PIC code's periodic cell sort produces"""
-    dx, dy = grid["dx"], grid["dy"]
-    nx = grid["Ey"].shape[1]
-    ci = np.floor((e["x"] - grid.get("x0", 0.0)) / dx).astype(np.int64)
-    cj = np.floor((e["y"] - grid.get("y0", 0.0)) / dy).astype(np.int64)
-    key = ((cj // 32) * (nx // 32) + ci // 32) * 1024 + (cj % 32) * 32 + (ci % 32)
-    o = np.argsort(key, kind="stable")
-    return {k: v[o] for k, v in e.items()}
-
-
 def c3(n=30_000_000, seed=3, gamma0=4000.0, nx=4096, ny=2048, grid=None):
     """e- at gamma0 = 4000 moving along +x, uniform in the vacuum part of the box,
     unpolarised spins, counting-sorted by 32x32-cell tiles; dt = T0/64."""
