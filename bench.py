@@ -558,8 +558,34 @@ def run_e2e(q, torch, sim, prec, steps, flags):
         sim.t += sim.dt
         sim.step_no += 1
     el = time.perf_counter() - t0
-    return {"value": tot_p / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // steps,
-            "d2h_bytes_per_step": d2h // steps, "steps": steps, "particles": tot_p, "seconds": el}
+    out = {"value": tot_p / el, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d // steps,
+           "d2h_bytes_per_step": d2h // steps, "steps": steps, "particles": tot_p, "seconds": el}
+    out["copy_bound"] = copy_bound(torch, h2d / steps, d2h / steps, tot_p / steps)
+    return out
+
+
+def copy_bound(torch, h2d, d2h, particles):
+    """What the host-buffer step could reach if it were only its copies: one plain pinned
+    host->device and device->host copy of up to 1 GiB each, timed with CUDA events, and the
+    particle-steps/s of a step that moves h2d + d2h bytes at those rates."""
+    nb = int(min(max(h2d, d2h), 1 << 30)) // 16 * 16
+    if nb <= 0:
+        return None
+    h = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    rates = {}
+    for name, dst, src in (("h2d_GBs", d, h), ("d2h_GBs", h, d)):
+        dst.copy_(src, non_blocking=True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        ev1.record()
+        ev1.synchronize()
+        rates[name] = 3 * nb / (ev0.elapsed_time(ev1) * 1e-3) / 1e9
+    t = h2d / (rates["h2d_GBs"] * 1e9) + d2h / (rates["d2h_GBs"] * 1e9)
+    del h, d
+    return dict(rates, bytes_timed=nb, value=particles / t, unit="particle-steps/s", scope="one GPU")
 
 
 def oracle_sample(n_e, steps_timed, warmup=0, seed=2):

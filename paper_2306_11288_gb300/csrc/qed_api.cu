@@ -303,6 +303,10 @@ void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos,
   E.f = *f;
   E.t = t;
   E.seed = seed;
+  for (int r = 0; r < 10; ++r) {
+    E.rk[2 * r] = (uint32_t)seed + (uint32_t)r * kPhiloxW0;
+    E.rk[2 * r + 1] = (uint32_t)(seed >> 32) + (uint32_t)r * kPhiloxW1;
+  }
   E.step = step;
   E.st = st;
   E.user_stats = stats;

@@ -54,15 +54,32 @@ constexpr size_t kSmemRateLen = kOffCY - kOffRA;
 // ---- Philox4x32-10 (Salmon et al., SC'11) ------------------------------------------
 struct U4 { uint32_t a, b, c, d; };
 
+// round multipliers and key increments (the generator's published constants)
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
 __device__ __forceinline__ U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                        uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
     const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
     c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    k0 += kPhiloxW0; k1 += kPhiloxW1;
+  }
+  return U4{c0, c1, c2, c3};
+}
+// The same rounds with the key schedule given: rk[2r], rk[2r+1] are the two key words of
+// round r (k0 + r W0, k1 + r W1 mod 2^32).  A schedule in kernel-parameter space enters
+// each round as an operand, so a draw costs no key arithmetic.
+__device__ __forceinline__ U4 philox10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ rk[2 * r], n2 = hi0 ^ c3 ^ rk[2 * r + 1];
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
   }
   return U4{c0, c1, c2, c3};
 }
@@ -126,6 +143,9 @@ __device__ __forceinline__ void f_sincos(float x, float* s, float* c) {
   __sincosf(r, s, c);
 }
 __device__ __forceinline__ void f_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+// the same for an argument already in [-pi, pi] (no reduction)
+__device__ __forceinline__ void f_sincos_pi(float x, float* s, float* c) { __sincosf(x, s, c); }
+__device__ __forceinline__ void f_sincos_pi(double x, double* s, double* c) { sincos(x, s, c); }
 // arctangent on [0,1]: odd polynomial of degree 15 fitted to atan (max error 4e-8)
 __device__ __forceinline__ float atan01(float t) {
   const float t2 = t * t;

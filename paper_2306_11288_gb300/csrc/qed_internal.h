@@ -48,6 +48,7 @@ struct EnsArgs {
   double inv_len;                    // 1 / envelope length
   FloatConsts ff;                    // float constants; t_rel, t_mod only for single launches
   unsigned long long seed;
+  unsigned int rk[20];               // Philox key schedule of seed (single-ensemble launches)
   unsigned int step;                 // step number (single launches; batched: DevState::step)
   DevState* st;                      // the ensemble's counts, id counter, per-step totals
   qed_step_stats* user_stats;

@@ -39,11 +39,15 @@ namespace qedk {
 // double -> float by truncating the mantissa (error below one float ulp); |x| < 2^-126
 // flushes to zero.  Positions never approach the float overflow threshold.
 __device__ __forceinline__ float d2f_bits(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int hi = (unsigned int)(b >> 32), lo = (unsigned int)b;
-  const int e = (int)((hi >> 20) & 0x7FFu) - (1023 - 127);
-  const unsigned int f = (hi & 0x80000000u) | ((unsigned int)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  return __uint_as_float(e > 0 ? f : (hi & 0x80000000u));
+  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+  // (hi << 3 | lo >> 29) holds the low 9 bits of the exponent E above the top 23 mantissa
+  // bits.  E - (1023 - 127) is the float exponent; 1023 - 127 = 896 = 384 (mod 512), and
+  // subtracting 384 << 23 (adding 2^30 mod 2^32) turns E mod 512 into E - 896 whether or
+  // not E mod 512 wrapped, for float exponents 1..255.
+  const unsigned int f = __funnelshift_l(lo, hi, 3) + 0x40000000u;
+  const unsigned int sign = hi & 0x80000000u;
+  // E < 897 (|x| < 2^-126, zero included): signed zero
+  return __uint_as_float((hi << 1) >= (897u << 21) ? (f & 0x7FFFFFFFu) | sign : sign);
 }
 // float -> double, exact for normal floats (zero and subnormal floats give signed zero)
 __device__ __forceinline__ double f2d_bits(float f) {
@@ -209,7 +213,7 @@ __device__ __forceinline__ EB<R> gather(const EnsArgs& E, const EnsTime& tm, dou
     }
     if (s < R(0) || s > R(1)) return r;
     R sn, cs;
-    f_sincos(R(kPi) * s, &sn, &cs);
+    f_sincos_pi(R(kPi) * s, &sn, &cs);
     R g = (sizeof(R) == 8 ? (R)f.a0 : (R)E.ff.a0) * sn * sn;
     if (f.kind == QED_FIELD_GAUSS) {
       if (sizeof(R) == 8) {
@@ -282,15 +286,19 @@ __device__ __forceinline__ void frame(V3<R> n, V3<R>& e1, V3<R>& e2) {
 template <typename R>
 struct URand { R u0, u1; };
 
-template <typename R>
-__device__ __forceinline__ URand<R> urand(uint64_t seed, uint64_t id, uint32_t step, uint32_t ctr) {
+// kRk: take the ensemble's precomputed key schedule (single-ensemble launches, where the
+// ensemble's arguments are kernel parameters) instead of forming the keys from the seed
+template <typename R, bool kRk>
+__device__ __forceinline__ URand<R> urand(const EnsArgs& E, uint64_t id, uint32_t step, uint32_t ctr) {
+  const uint32_t c0 = (uint32_t)id, c1 = (uint32_t)(id >> 32);
+  const U4 o = kRk ? philox10_rk(c0, c1, step, ctr, E.rk)
+                   : philox10(c0, c1, step, ctr, (uint32_t)E.seed, (uint32_t)(E.seed >> 32));
   URand<R> r;
   if (sizeof(R) == 8) {
-    const Uni2 u = uniforms(seed, id, step, ctr);
-    r.u0 = (R)u.u0;
-    r.u1 = (R)u.u1;
+    const double s = 1.1102230246251565404e-16;  // 2^-53, as in uniforms()
+    r.u0 = (R)((double)((((uint64_t)(o.a >> 5)) << 26) | (uint64_t)(o.b >> 6)) * s);
+    r.u1 = (R)((double)((((uint64_t)(o.c >> 5)) << 26) | (uint64_t)(o.d >> 6)) * s);
   } else {
-    const U4 o = philox10((uint32_t)id, (uint32_t)(id >> 32), step, ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
     r.u0 = (R)(__uint2float_rn(o.a >> 5) * 0x1p-27f + __uint2float_rn(o.b >> 6) * 0x1p-53f);
     r.u1 = (R)(__uint2float_rn(o.c >> 5) * 0x1p-27f + __uint2float_rn(o.d >> 6) * 0x1p-53f);
   }
@@ -639,8 +647,10 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
         const R er = er2 * inv_er;
         chig = R(kXiL) * om * er;
         P1 = inv_er * Er;
-        V3<R> e1, e2;
-        frame(nn, e1, e2);
+        // the canonical frame of n without its normalisation (atan2 needs only the ratio)
+        R fa = nn.z, fb = R(0), fc = -nn.x;
+        if (fa * fa + fc * fc < R(1e-20)) { fa = R(0); fb = nn.z; fc = -nn.y; }
+        const V3<R> e1 = mk<R>(fa, fb, fc), e2 = cross(nn, e1);
         const R thn = f_atan2(dot(P1, e2), dot(P1, e1));
         R s2, c2;
         f_sincos(R(2) * (thn - th), &s2, &c2);
@@ -652,10 +662,15 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
           tb.vb_m(chig > R(kVbMax) ? R(kVbMax) : chig, mp, mq);
           const R dphi = (mp - mq) * R(kAlpha / (90.0 * kPi) * kXiL) * om * er * er * dt;
           R sd, cd;
-          if (dphi < R(1e-2) && dphi > R(-1e-2)) {   // Taylor to 5th/6th order: error below 2e-15
+          if (dphi < R(1e-2) && dphi > R(-1e-2)) {
             const R d2 = dphi * dphi;
-            sd = dphi * (R(1) - d2 * (R(1.0 / 6.0) - d2 * R(1.0 / 120.0)));
-            cd = R(1) - d2 * (R(0.5) - d2 * (R(1.0 / 24.0) - d2 * R(1.0 / 720.0)));
+            if (sizeof(R) == 8) {   // Taylor to 5th/6th order: error below 2e-15
+              sd = dphi * (R(1) - d2 * (R(1.0 / 6.0) - d2 * R(1.0 / 120.0)));
+              cd = R(1) - d2 * (R(0.5) - d2 * (R(1.0 / 24.0) - d2 * R(1.0 / 720.0)));
+            } else {                // to 3rd/2nd order: the next terms are below 1e-9
+              sd = dphi * (R(1) - d2 * R(1.0 / 6.0));
+              cd = R(1) - d2 * R(0.5);
+            }
           } else {
             f_sincos(dphi, &sd, &cd);
           }
@@ -667,7 +682,7 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
           R T0, T3;
           tb.nbw_rates(chig, T0, T3);
           const R Pd = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) * inv_om * (T0 - xi.z * T3) * dt;
-          const URand<R> u = urand<R>(E.seed, id, tm.step, 3u);
+          const URand<R> u = urand<R, !kB>(E, id, tm.step, 3u);
           decay = u.u0 < Pd;
           rmix = u.u1;
         }
@@ -992,7 +1007,7 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
           const R pref = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) * inv_g1;
           const R Wa = pref * A, Wb = pref * B;
           const R Pe = (Wa - s * Wb) * dt;
-          const URand<R> u = urand<R>(E.seed, id, tm.step, 0u);
+          const URand<R> u = urand<R, !kB>(E, id, tm.step, 0u);
           if (u.u0 < Pe) {
             emit = true;   // completed by k_ncs_ev
           } else {
