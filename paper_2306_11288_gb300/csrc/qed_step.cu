@@ -7,11 +7,10 @@ namespace qedk {
 size_t nbw_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NbwRec<double>) : sizeof(NbwRec<float>); }
 size_t ncs_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NcsRec<double>) : sizeof(NcsRec<float>); }
 
-// Photon chain on the caller's stream; the lepton pass and the scan of its tile counts on
-// the context's side stream (forked after all earlier work on the caller's stream, joined
-// before the emissions): the lepton pass reads only particles below the counts of the
-// step start, the pair births of k_nbw_ev go above them, and the two scans write
-// different totals, so the two chains are independent until k_ncs_ev.
+// Photon chain on the caller's stream; the lepton pass on the context's side stream
+// (forked after all earlier work on the caller's stream, joined before the lepton scan):
+// the lepton pass reads only particles below the counts of the step start, the pair
+// births of k_nbw_ev go above them, so the two chains are independent until k_ncs_ev.
 // the lepton pass: with the radiative pusher flags its kRad instantiation
 template <typename R>
 static void launch_lepton(const StepArgs& a, int grid, cudaStream_t s) {
@@ -33,7 +32,6 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     if (ss.tev) cudaEventRecord(ss.tev[4], ss.side);
     launch_lepton<R>(a, nb[1], ss.side);
     if (ss.tev) cudaEventRecord(ss.tev[5], ss.side);
-    launch_k(k_scan<false>, 1, kScanThreads, ss.side, pdl, a, 1);
     cudaEventRecord(ss.join, ss.side);
   }
   k_photon<R, false, true><<<nb[0], kTile, 0, s>>>(a);
@@ -47,8 +45,8 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     if (ss.tev) cudaEventRecord(ss.tev[4], s);
     launch_lepton<R>(a, nb[1], s);
     if (ss.tev) cudaEventRecord(ss.tev[5], s);
-    k_scan<false><<<1, kScanThreads, 0, s>>>(a, 1);
   }
+  k_scan<false><<<1, kScanThreads, 0, s>>>(a, 1);
   if constexpr (sizeof(R) == 4) {
     if (a.flags & QED_F_MLP) launch_k(k_ncs_ev_mlp<false>, nb[2] * 2, kMlpRows, s, pdl, a);
     else launch_k(k_ncs_ev<R, false>, nb[2], kTile, s, pdl, a);
