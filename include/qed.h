@@ -325,6 +325,18 @@ qed_status qed_get_timing(qed_ctx *ctx, double ms[3], uint64_t *steps);
  * >= the count.  Errors: QED_ERR_INVALID_ARG (bad which, cap too small). */
 qed_status qed_copy_table(qed_ctx *ctx, int which, double *host, uint64_t cap, uint64_t *len, void *stream);
 
+/* Diagnostics: the step's random-number generator, Philox4x32-10 (Salmon et al., SC'11,
+ * the counter-based generator every Monte Carlo decision of the step draws from), run on
+ * the device for n counters under one 64-bit key.
+ * ctr: device memory, n x 4 words (counter words 0..3 of each block); key: key word 0 in
+ * the low 32 bits, key word 1 in the high 32 bits; out: device memory, n x 8 words --
+ * words 0..3 of each block from the form that derives the ten round keys inside the kernel
+ * (batched launches), words 4..7 from the form that takes them precomputed on the host as
+ * kernel parameters (single-ensemble launches).  The two halves must agree.  Async on
+ * `stream`; the caller owns both buffers.  Errors: QED_ERR_INVALID_ARG (NULL buffer with
+ * n > 0), QED_ERR_CUDA (launch failure). */
+qed_status qed_philox_blocks(const uint32_t *ctr, uint64_t key, uint32_t *out, uint64_t n, void *stream);
+
 /* ---- End-of-run observables (paper Sec. IV: post-processing of the photon polarization,
  * Figs. of spectra, mean spin and pair yield) ------------------------------------------
  * qed_diag histograms one particle set on the device.

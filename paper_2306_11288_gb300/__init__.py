@@ -35,7 +35,7 @@ ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particle
                  "qed_batch_step", "qed_batch_run", "qed_batch_clock", "qed_batch_get_config",
                  "qed_batch_set_config", "qed_batch_tune", "qed_batch_destroy", "qed_mlp_train",
                  "qed_mlp_set_params", "qed_mlp_get_params", "qed_mlp_eval", "qed_mlp_target", "qed_fdtd_advance",
-                 "qed_sort_cells", "qed_last_error")
+                 "qed_sort_cells", "qed_philox_blocks", "qed_last_error")
 MLP_PARAMS = 4481
 QED_DIAG_SPECTRUM, QED_DIAG_DETECTOR = 0, 1
 
@@ -110,6 +110,7 @@ def lib():
         L.qed_step_static.argtypes = [vp, vp, vp, vp, C.POINTER(qed_fields), d, d, u64, u32, u32, vp, vp]
         L.qed_read_status.argtypes = [vp, C.POINTER(u32), C.c_int, vp]
         L.qed_copy_table.argtypes = [vp, C.c_int, C.POINTER(C.c_double), u64, C.POINTER(u64), vp]
+        L.qed_philox_blocks.argtypes = [vp, u64, vp, u64, vp]
         L.qed_set_timing.argtypes = [vp, C.c_int]
         L.qed_get_timing.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(u64)]
         L.qed_diag.argtypes = [vp, vp, C.POINTER(qed_diag_spec), vp, vp]
@@ -324,6 +325,21 @@ def qed_copy_table(ctx, which, stream=None) -> np.ndarray:
     _check(lib().qed_copy_table(ctx, int(which), out.ctypes.data_as(C.POINTER(C.c_double)), n.value,
                                 C.byref(n), _stream(stream)), "qed_copy_table")
     return out
+
+
+def qed_philox_blocks(ctr, key, out, stream=None):
+    """Philox4x32-10 on the device for the counters ctr (int32 CUDA tensor, n x 4) under the
+    64-bit key; out (int32 CUDA tensor, n x 8) receives per block the words of the kernel-side
+    key schedule form, then those of the host-precomputed form (argument marshalling only)."""
+    n = ctr.shape[0] if ctr.dim() == 2 else 0
+    if ctr.dim() != 2 or ctr.shape[1] != 4 or out.dim() != 2 or out.shape[0] != n or out.shape[1] != 8:
+        raise ValueError("qed_philox_blocks: ctr must be n x 4 and out n x 8")
+    for tns in (ctr, out):
+        if not tns.is_contiguous() or tns.element_size() != 4 or not tns.is_cuda:
+            raise ValueError("qed_philox_blocks: contiguous 32-bit CUDA tensors required")
+    _check(lib().qed_philox_blocks(C.c_void_p(ctr.data_ptr()), C.c_uint64(int(key) & (2**64 - 1)),
+                                   C.c_void_p(out.data_ptr()), C.c_uint64(n), _stream(stream)),
+           "qed_philox_blocks")
 
 
 def diag_spec(kind, nx, ny=1, lo_x=1.0, hi_x=2.0, lo_y=0.0, hi_y=1.0, ref=(0.0, 0.0, 0.0)) -> qed_diag_spec:

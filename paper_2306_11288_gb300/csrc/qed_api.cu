@@ -293,6 +293,13 @@ void step_time_floats(double t, double phi0, float* t_rel, float* t_mod) {
   *t_mod = (float)std::fma(-kTwoPi, std::floor(t / kTwoPi), t);
 }
 
+void philox_key_schedule(uint64_t seed, unsigned int rk[20]) {
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = (uint32_t)seed + (uint32_t)r * kPhiloxW0;
+    rk[2 * r + 1] = (uint32_t)(seed >> 32) + (uint32_t)r * kPhiloxW1;
+  }
+}
+
 void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos, const qed_particles* ph,
                    const qed_fields* f, double t, uint64_t seed, uint32_t step, DevState* st,
                    qed_step_stats* stats) {
@@ -303,10 +310,7 @@ void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos,
   E.f = *f;
   E.t = t;
   E.seed = seed;
-  for (int r = 0; r < 10; ++r) {
-    E.rk[2 * r] = (uint32_t)seed + (uint32_t)r * kPhiloxW0;
-    E.rk[2 * r + 1] = (uint32_t)(seed >> 32) + (uint32_t)r * kPhiloxW1;
-  }
+  philox_key_schedule(seed, E.rk);
   E.step = step;
   E.st = st;
   E.user_stats = stats;
@@ -537,6 +541,14 @@ extern "C" qed_status qed_step_host(qed_ctx* c, qed_particles* e, qed_particles*
     n_host[k] = counts[k];
   }
   CK(cudaStreamSynchronize(s));
+  return QED_OK;
+}
+
+extern "C" qed_status qed_philox_blocks(const uint32_t* ctr, uint64_t key, uint32_t* out, uint64_t n, void* stream) {
+  if (n == 0) return QED_OK;
+  if (!ctr || !out) FAIL(QED_ERR_INVALID_ARG, "qed_philox_blocks: NULL buffer");
+  if (n > (1ull << 40)) FAIL(QED_ERR_INVALID_ARG, "qed_philox_blocks: n too large");
+  CK(launch_philox_blocks(ctr, key, out, n, S(stream)));
   return QED_OK;
 }
 

@@ -100,6 +100,10 @@ void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos,
                    const qed_fields* f, double t, uint64_t seed, uint32_t step, DevState* st,
                    qed_step_stats* stats);
 void step_time_floats(double t, double phi0, float* t_rel, float* t_mod);
+// the ten Philox4x32-10 round keys of seed: rk[2r] = lo + r W0, rk[2r+1] = hi + r W1
+void philox_key_schedule(uint64_t seed, unsigned int rk[20]);
+// the generator check of qed_philox_blocks (arguments validated by the caller)
+cudaError_t launch_philox_blocks(const uint32_t* ctr, uint64_t key, uint32_t* out, uint64_t n, cudaStream_t s);
 // host validation of a field descriptor (message prefixed by who)
 qed_status check_fields(const qed_fields* f, const char* who);
 qed_status check_deposit(uint32_t flags, const qed_fields* f, const char* who);

@@ -464,4 +464,27 @@ qed_status build_tables(double* d64, float* d32, cudaStream_t st) {
   return QED_OK;
 }
 
+// ---- generator check (qed_philox_blocks) --------------------------------------------
+struct PhiloxKeys { unsigned int rk[20]; };
+
+__global__ void k_philox_blocks(const uint32_t* __restrict__ ctr, uint64_t key, uint32_t* __restrict__ out,
+                                uint64_t n, const __grid_constant__ PhiloxKeys ks) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c0 = ctr[4 * i], c1 = ctr[4 * i + 1], c2 = ctr[4 * i + 2], c3 = ctr[4 * i + 3];
+    const U4 a = philox10(c0, c1, c2, c3, (uint32_t)key, (uint32_t)(key >> 32));
+    const U4 b = philox10_rk(c0, c1, c2, c3, ks.rk);
+    uint32_t* o = out + 8 * i;
+    o[0] = a.a; o[1] = a.b; o[2] = a.c; o[3] = a.d;
+    o[4] = b.a; o[5] = b.b; o[6] = b.c; o[7] = b.d;
+  }
+}
+
+cudaError_t launch_philox_blocks(const uint32_t* ctr, uint64_t key, uint32_t* out, uint64_t n, cudaStream_t s) {
+  PhiloxKeys ks;
+  philox_key_schedule(key, ks.rk);
+  const uint64_t blocks = (n + 255) / 256;
+  k_philox_blocks<<<(unsigned int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(ctr, key, out, n, ks);
+  return cudaGetLastError();
+}
+
 }  // namespace qedk

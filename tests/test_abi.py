@@ -60,6 +60,9 @@ def test_host_validation_without_gpu(lib):
     g = q.qed_grid2d()
     assert L.qed_fdtd_advance(C.byref(g), 0, 1.0, None) == q.QED_ERR_INVALID_ARG
     assert "non-NULL" in q.qed_last_error()
+    assert L.qed_philox_blocks(None, 0, None, 0, None) == q.QED_OK          # nothing to do
+    assert L.qed_philox_blocks(None, 0, None, 4, None) == q.QED_ERR_INVALID_ARG
+    assert "NULL buffer" in q.qed_last_error()
     h = C.c_void_p()
     soa = q.qed_soa()
     assert L.particles_create(None, 0, C.byref(soa), 0, 0, 0, None, C.byref(h)) == q.QED_ERR_NOT_INITIALIZED
