@@ -65,7 +65,7 @@ BYTES = {
 # by the particles it processed) from the ncu capture summarised in
 # profiles/k_photon_k_lepton_c2_1e6_traffic.md; scaled to a launch by its particle count.
 # Must be re-captured whenever either streaming kernel changes.
-TRAFFIC_PER_UNIT = {"k_photon": 87.10, "k_lepton": 63.51}
+TRAFFIC_PER_UNIT = {"k_photon": 87.09, "k_lepton": 62.58}
 
 
 class ClockSampler:
