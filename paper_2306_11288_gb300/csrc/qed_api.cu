@@ -47,7 +47,7 @@ extern "C" qed_status qed_init_tables(qed_ctx** out, void* stream) {
   if (!c) FAIL(QED_ERR_INVALID_ARG, "qed_init_tables: host allocation failed");
   CK(cudaGetDevice(&c->device));
   cudaError_t e = cudaMalloc(&c->tab64, sizeof(double) * kTableLen);
-  if (e == cudaSuccess) e = cudaMalloc(&c->tab32, sizeof(float) * kTableLen);
+  if (e == cudaSuccess) e = cudaMalloc(&c->tab32, sizeof(float) * kTab32Len);
   if (e == cudaSuccess) e = cudaMalloc(&c->st, sizeof(DevState));
   if (e != cudaSuccess) {
     cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->st); free(c);

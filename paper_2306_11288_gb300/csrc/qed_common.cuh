@@ -48,8 +48,24 @@ constexpr size_t kOffBY = kOffCD + 2 * (size_t)kNCX * kNCT;    // [2][kNBX][kNBT
 constexpr size_t kOffBD = kOffBY + 2 * (size_t)kNBX * kNBT;
 constexpr size_t kOffRR = kOffBD + 2 * (size_t)kNBX * kNBT;    // [4][kNR] q, psi1..3 / chi^3
 constexpr size_t kTableLen = kOffRR + 4 * (size_t)kNR;
-// the 1-D rate tables are contiguous [kOffRA, kOffCY): staged to shared memory
+// the 1-D rate tables are contiguous [kOffRA, kOffCY): staged to shared memory (FP64 path)
 constexpr size_t kSmemRateLen = kOffCY - kOffRA;
+
+// Mixed path: the same 4-point Lagrange interpolation of the 1-D rate tables, held as the
+// cubic of each interval: for the row r = i - 1 of node interval i (i in [1, n-3], the
+// intervals lagrange4 selects) four floats c0..c3 with p(f) = c0 + f (c1 + f (c2 + f c3)),
+// f = X - i.  One 16-byte load and three FMAs per table instead of four loads, the weights
+// and four FMAs.  Appended to the float copy of the tables (16-byte aligned):
+//   VB:  the difference M_par - M_perp (the only combination the photon pass uses), [kNV-3][4];
+//   NBW: T0 and T3 of one interval side by side, [kNBX-3][2][4];
+//   NCS: A and B of one interval side by side, [kNR-3][2][4].
+constexpr size_t kOffCoefVB = (kTableLen + 3) / 4 * 4;
+constexpr size_t kOffCoefT = kOffCoefVB + 4 * (size_t)(kNV - 3);
+constexpr size_t kOffCoefN = kOffCoefT + 8 * (size_t)(kNBX - 3);
+constexpr size_t kTab32Len = kOffCoefN + 8 * (size_t)(kNR - 3);
+// staged to shared memory by the photon pass (VB and NBW) and by the lepton pass (NCS)
+constexpr size_t kCoefPhLen = kOffCoefN - kOffCoefVB;
+constexpr size_t kCoefLepLen = kTab32Len - kOffCoefN;
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) ------------------------------------------
 struct U4 { uint32_t a, b, c, d; };

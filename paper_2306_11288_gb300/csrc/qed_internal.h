@@ -22,7 +22,8 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
-// builds the FP64 tables into d64 (kTableLen doubles) and the float copy into d32
+// builds the FP64 tables into d64 (kTableLen doubles) and the float copy with the
+// mixed path's interval cubics into d32 (kTab32Len floats)
 qed_status build_tables(double* d64, float* d32, cudaStream_t st);
 
 // per-launch parameters of the step kernels (one struct, passed by value)

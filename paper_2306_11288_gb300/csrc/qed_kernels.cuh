@@ -332,14 +332,37 @@ __device__ __forceinline__ URand<R> urand(const EnsArgs& E, uint64_t id, uint32_
 }
 
 // ---- table access --------------------------------------------------------------------
+// Mixed path: the row of the interval lagrange4 selects for X (grid units) and the offset f
+// of X in it; the cubic of one row
+__device__ __forceinline__ int coef_row(float X, int n, float& f) {
+  X = fminf(fmaxf(X, 0.0f), (float)(n - 1));
+  int i = __float2int_rd(X);
+  i = min(max(i, 1), n - 3);
+  f = X - (float)i;
+  return i - 1;
+}
+__device__ __forceinline__ float coef_cubic(float4 c, float f) { return fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x); }
+
 template <typename R>
 struct Tabs {
   const R* g;     // full table block in global memory
-  const R* s;     // copy of the 1-D rate tables (shared memory in the streaming kernels)
+  const R* s;     // FP64 path: the 1-D rate tables (shared memory in the streaming kernels)
+  // mixed path: the interval cubics of the VB difference, NBW and NCS rate tables (shared
+  // memory where the streaming kernel staged them, else global memory)
+  const float4* cv;
+  const float4* cb;
+  const float4* cn;
   __device__ __forceinline__ void ncs_rates(R chi, R& A, R& B) const {
     const R X = (f_log(chi) - R(kRLo)) * R((kNR - 1) / (kRHi - kRLo));
-    A = chi * lagrange4(s, kNR, X);
-    B = chi * lagrange4(s + kNR, kNR, X);
+    if constexpr (sizeof(R) == 4) {
+      float f;
+      const int r = coef_row(X, kNR, f);
+      A = chi * coef_cubic(cn[2 * r], f);
+      B = chi * coef_cubic(cn[2 * r + 1], f);
+    } else {
+      A = chi * lagrange4(s, kNR, X);
+      B = chi * lagrange4(s + kNR, kNR, X);
+    }
   }
   __device__ __forceinline__ R ncs_inv(int comp, R chi, R t) const {
     const R X = (m_log(chi) - R(kRLo)) * R((kNCX - 1) / (kRHi - kRLo));
@@ -350,8 +373,15 @@ struct Tabs {
   __device__ __forceinline__ void nbw_rates(R chig, R& T0, R& T3) const {
     const R X = (f_log(chig) - R(kBLo)) * R((kNBX - 1) / (kBHi - kBLo));
     const R damp = f_exp(R(-8.0 / 3.0) * f_rcp(chig));
-    T0 = damp * lagrange4(s + (kOffT0 - kOffRA), kNBX, X);
-    T3 = damp * lagrange4(s + (kOffT3 - kOffRA), kNBX, X);
+    if constexpr (sizeof(R) == 4) {
+      float f;
+      const int r = coef_row(X, kNBX, f);
+      T0 = damp * coef_cubic(cb[2 * r], f);
+      T3 = damp * coef_cubic(cb[2 * r + 1], f);
+    } else {
+      T0 = damp * lagrange4(s + (kOffT0 - kOffRA), kNBX, X);
+      T3 = damp * lagrange4(s + (kOffT3 - kOffRA), kNBX, X);
+    }
   }
   __device__ __forceinline__ R nbw_inv(int comp, R chig, R t) const {
     const R X = (m_log(chig) - R(kBLo)) * R((kNBX - 1) / (kBHi - kBLo));
@@ -359,11 +389,17 @@ struct Tabs {
     const size_t o = (size_t)comp * kNBX * kNBT;
     return table2d(g + kOffBY + o, g + kOffBD + o, kNBX, kNBT, X, (t - R(kBTLo)) / ht, ht);
   }
-  __device__ __forceinline__ void vb_m(R chig, R& mp, R& mq) const {
-    if (chig < R(kVbMin)) { mp = R(4); mq = R(7); return; }
+  // M_par - M_perp (4 - 7 below the table)
+  __device__ __forceinline__ R vb_md(R chig) const {
+    if (chig < R(kVbMin)) return R(-3);
     const R X = (f_log(chig) - R(kVLo)) * R((kNV - 1) / (kVHi - kVLo));
-    mp = lagrange4(s + (kOffMP - kOffRA), kNV, X);
-    mq = lagrange4(s + (kOffMQ - kOffRA), kNV, X);
+    if constexpr (sizeof(R) == 4) {
+      float f;
+      const int r = coef_row(X, kNV, f);
+      return coef_cubic(cv[r], f);
+    } else {
+      return lagrange4(s + (kOffMP - kOffRA), kNV, X) - lagrange4(s + (kOffMQ - kOffRA), kNV, X);
+    }
   }
   __device__ __forceinline__ void k(R x, R& k13, R& k23, R& ik) const { kfun(g, x, k13, k23, ik); }
   // radiative pusher functions (read through L1/L2: used only with the radiative flags):
@@ -459,9 +495,37 @@ __device__ __forceinline__ void rad_spin_half(const RadSpin<R>& rs, R dt, V3<R>&
   S = S + h * (rs.p1 * S + (rs.p2 * sb) * rs.be + rs.p3 * rs.zeta);
 }
 
+// Tables in global memory (every pointer into the table block).
 template <typename R>
-__device__ __forceinline__ void stage_rates(const R* g, R* s) {
-  for (int i = threadIdx.x; i < (int)kSmemRateLen; i += blockDim.x) s[i] = g[kOffRA + i];
+__device__ __forceinline__ Tabs<R> tabs_global(const void* tables) {
+  const R* g = reinterpret_cast<const R*>(tables);
+  Tabs<R> t{g, g + kOffRA, nullptr, nullptr, nullptr};
+  if constexpr (sizeof(R) == 4) {
+    t.cv = reinterpret_cast<const float4*>(g + kOffCoefVB);
+    t.cb = reinterpret_cast<const float4*>(g + kOffCoefT);
+    t.cn = reinterpret_cast<const float4*>(g + kOffCoefN);
+  }
+  return t;
+}
+
+// What a streaming kernel stages to shared memory: FP64 path, the 1-D rate tables; mixed
+// path, the interval cubics it uses (photon pass: VB and NBW; lepton pass: NCS).
+template <typename R, bool kPh> struct SmemTab {
+  static constexpr size_t n = sizeof(R) == 8 ? kSmemRateLen : (kPh ? kCoefPhLen : kCoefLepLen);
+};
+// Copies them to s (16-byte aligned) and points the table accessors there.
+template <typename R, bool kPh>
+__device__ __forceinline__ void stage_rates(Tabs<R>& tb, R* s) {
+  const size_t o = sizeof(R) == 8 ? kOffRA : (kPh ? kOffCoefVB : kOffCoefN);
+  for (int i = threadIdx.x; i < (int)SmemTab<R, kPh>::n; i += blockDim.x) s[i] = tb.g[o + i];
+  if constexpr (sizeof(R) == 8) {
+    tb.s = s;
+  } else if constexpr (kPh) {
+    tb.cv = reinterpret_cast<const float4*>(s);
+    tb.cb = reinterpret_cast<const float4*>(s + (kOffCoefT - kOffCoefVB));
+  } else {
+    tb.cn = reinterpret_cast<const float4*>(s);
+  }
 }
 
 template <typename T>
@@ -605,7 +669,7 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
   // (whose tile-to-ensemble search needs the registers) load each tile at its top
   constexpr bool kPf = !kB;
   pdl_trigger();
-  __shared__ R s_rates[kSm ? kSmemRateLen : 1];
+  __shared__ __align__(16) R s_rates[kSm ? SmemTab<R, true>::n : 1];
   __shared__ TileShared s_tile;
   __shared__ unsigned int s_off[kB ? kMaxEns + 1 : 1];
   DevState* gst = a.st;
@@ -618,9 +682,8 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
     n_one = a.e0.sp[2].present ? a.e0.st->n_live[2] : 0ull;
     ntiles = (unsigned int)((n_one + kTile - 1) / kTile);
   }
-  const Tabs<R> tb{reinterpret_cast<const R*>(a.tables),
-                   kSm ? s_rates : reinterpret_cast<const R*>(a.tables) + kOffRA};
-  if constexpr (kSm) stage_rates(tb.g, s_rates);
+  Tabs<R> tb = tabs_global<R>(a.tables);
+  if constexpr (kSm) stage_rates<R, true>(tb, s_rates);
   __syncthreads();
   const unsigned int epoch = gst->epoch;
   const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.fdt;
@@ -684,9 +747,8 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
         xi.x = x1; xi.z = x3;
         th = thn;
         if (a.flags & QED_F_VB) {
-          R mp, mq;
-          tb.vb_m(chig > R(kVbMax) ? R(kVbMax) : chig, mp, mq);
-          const R dphi = (mp - mq) * R(kAlpha / (90.0 * kPi) * kXiL) * om * er * er * dt;
+          const R md = tb.vb_md(chig > R(kVbMax) ? R(kVbMax) : chig);
+          const R dphi = md * R(kAlpha / (90.0 * kPi) * kXiL) * om * er * er * dt;
           R sd, cd;
           if (dphi < R(1e-2) && dphi > R(-1e-2)) {
             const R d2 = dphi * dphi;
@@ -834,9 +896,9 @@ __device__ __forceinline__ void esirkepov_terms(const DepMove<T>& m, Add add) {
 // is at most 2^22 in units of 1/s, and one cell and component collects at most 256 terms
 // (one per lepton of the tile): below 2^30, inside int32.  Rounding a term to a multiple
 // of 1/s = 2^(e - 22) < 2c 2^-22 costs about one float ulp of the tile's largest term.
-// Window cells: with the rate tables the block's static shared memory stays below 48 KB
-// (mixed: 14 KB of tables + 33 KB of window; FP64: 28 KB + 19 KB).
-template <typename T> struct DepWin { static constexpr int v = sizeof(T) == 4 ? 2816 : 1600; };
+// Window cells: with the staged rate tables the block's static shared memory stays below
+// 48 KB (mixed: 16 KB of NCS interval cubics + 31 KB of window; FP64: 28 KB + 19 KB).
+template <typename T> struct DepWin { static constexpr int v = sizeof(T) == 4 ? 2600 : 1600; };
 template <typename T>
 struct DepShared {
   int bnd[5];           // imin, imax, jmin, jmax of the tile's nearest nodes; largest factor
@@ -904,7 +966,7 @@ __device__ __forceinline__ void deposit_tile(const qed_fields& f, const DepMove<
 template <typename R, bool kB, bool kSm, bool kRad = false, bool kDep = false>
 __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::v)
     k_lepton(const __grid_constant__ StepArgs a) {
-  __shared__ R s_rates[kSm ? kSmemRateLen : 1];
+  __shared__ __align__(16) R s_rates[kSm ? SmemTab<R, false>::n : 1];
   __shared__ TileShared s_tile;
   __shared__ unsigned int s_off[kB ? kMaxEns + 1 : 1];
   __shared__ unsigned int s_et[kB ? kMaxEns : 1];
@@ -924,9 +986,8 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
     t0s = (unsigned int)((n0s + kTile - 1) / kTile);
     ntiles = t0s + (unsigned int)((n1s + kTile - 1) / kTile);
   }
-  const Tabs<R> tb{reinterpret_cast<const R*>(a.tables),
-                   kSm ? s_rates : reinterpret_cast<const R*>(a.tables) + kOffRA};
-  if constexpr (kSm) stage_rates(tb.g, s_rates);
+  Tabs<R> tb = tabs_global<R>(a.tables);
+  if constexpr (kSm) stage_rates<R, false>(tb, s_rates);
   __syncthreads();
   const unsigned int epoch = gst->epoch;
   const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.fdt;
@@ -1305,7 +1366,7 @@ __global__ void __launch_bounds__(kTile) k_nbw_ev(const __grid_constant__ StepAr
   pdl_wait();
   pdl_trigger();
   DevState* gst = a.st;
-  const Tabs<R> tb{reinterpret_cast<const R*>(a.tables), reinterpret_cast<const R*>(a.tables) + kOffRA};
+  const Tabs<R> tb = tabs_global<R>(a.tables);
   const unsigned long long nrec = min(gst->cursor[0], a.rec_cap[0]);
   const unsigned int epoch = gst->epoch;
   const NbwRec<R>* evlog = reinterpret_cast<const NbwRec<R>*>(a.rec[0]);
@@ -1550,7 +1611,7 @@ template <typename R, bool kB>
 __global__ void __launch_bounds__(kTile) k_ncs_ev(const __grid_constant__ StepArgs a) {
   pdl_wait();
   DevState* gst = a.st;
-  const Tabs<R> tb{reinterpret_cast<const R*>(a.tables), reinterpret_cast<const R*>(a.tables) + kOffRA};
+  const Tabs<R> tb = tabs_global<R>(a.tables);
   const unsigned long long nrec = min(gst->cursor[1], a.rec_cap[1]);
   const unsigned int epoch = gst->epoch;
   const NcsRec<R>* evlog = reinterpret_cast<const NcsRec<R>*>(a.rec[1]);
@@ -1580,7 +1641,7 @@ __global__ void __launch_bounds__(kMlpRows) k_ncs_ev_mlp(const __grid_constant__
   pdl_wait();
   __shared__ MlpSmem sm;
   DevState* gst = a.st;
-  const Tabs<float> tb{reinterpret_cast<const float*>(a.tables), reinterpret_cast<const float*>(a.tables) + kOffRA};
+  const Tabs<float> tb = tabs_global<float>(a.tables);
   const unsigned long long nrec = min(gst->cursor[1], a.rec_cap[1]);
   const unsigned int epoch = gst->epoch;
   const NcsRec<float>* evlog = reinterpret_cast<const NcsRec<float>*>(a.rec[1]);

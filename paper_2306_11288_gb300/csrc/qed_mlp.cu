@@ -55,7 +55,7 @@ __device__ float mix_target(const Tabs<float>& tb, float chi, float s, float t) 
 // sample i: features and the regression target (ln u - base) / 8
 __global__ void k_mlp_gen(const float* tables, unsigned long long seed, unsigned long long first,
                           unsigned long long n, float4* out) {
-  const Tabs<float> tb{tables, tables + kOffRA};
+  const Tabs<float> tb = tabs_global<float>(tables);
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long g = first + i;
@@ -80,7 +80,7 @@ __global__ void k_mlp_gen(const float* tables, unsigned long long seed, unsigned
 
 // table-sampler target for given (ln chi, s, r) (test and error-measurement entry)
 __global__ void k_mlp_target(const float* tables, const float* in, float* out, unsigned long long n) {
-  const Tabs<float> tb{tables, tables + kOffRA};
+  const Tabs<float> tb = tabs_global<float>(tables);
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const float lnchi = in[3 * i], s = in[3 * i + 1];

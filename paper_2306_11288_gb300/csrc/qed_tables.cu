@@ -403,6 +403,40 @@ __global__ void k_to_float(const double* a, float* b, size_t n) {
     b[i] = (float)a[i];
 }
 
+// Mixed path: the cubic of the 4-point Lagrange interpolant on each node interval, from the
+// FP64 node values y(i-1), y(i), y(i+1), y(i+2), in powers of f = X - i (the Lagrange
+// weights of nodes -1, 0, 1, 2 expanded in f), rounded to float.
+__device__ void lagrange_cubic(double ym, double y0, double y1, double y2, float* c) {
+  c[0] = (float)y0;
+  c[1] = (float)(-ym / 3.0 - 0.5 * y0 + y1 - y2 / 6.0);
+  c[2] = (float)(0.5 * ym - y0 + 0.5 * y1);
+  c[3] = (float)((y2 - ym) / 6.0 + 0.5 * (y0 - y1));
+}
+
+__global__ void k_coef(const double* d, float* f) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < kNV - 3) {   // VB: M_par - M_perp
+    const int i = t + 1;
+    double y[4];
+    for (int k = 0; k < 4; ++k) y[k] = d[kOffMP + i - 1 + k] - d[kOffMQ + i - 1 + k];
+    lagrange_cubic(y[0], y[1], y[2], y[3], f + kOffCoefVB + 4 * (size_t)t);
+  }
+  if (t < kNBX - 3) {  // NBW T0, T3
+    const int i = t + 1;
+    const double* a = d + kOffT0 + i - 1;
+    const double* b = d + kOffT3 + i - 1;
+    lagrange_cubic(a[0], a[1], a[2], a[3], f + kOffCoefT + 8 * (size_t)t);
+    lagrange_cubic(b[0], b[1], b[2], b[3], f + kOffCoefT + 8 * (size_t)t + 4);
+  }
+  if (t < kNR - 3) {   // NCS A, B
+    const int i = t + 1;
+    const double* a = d + kOffRA + i - 1;
+    const double* b = d + kOffRB + i - 1;
+    lagrange_cubic(a[0], a[1], a[2], a[3], f + kOffCoefN + 8 * (size_t)t);
+    lagrange_cubic(b[0], b[1], b[2], b[3], f + kOffCoefN + 8 * (size_t)t + 4);
+  }
+}
+
 // Gauss-Legendre nodes on [-1,1] by Newton iteration on P_n (host)
 static void gauss_legendre(int n, double* x, double* w) {
   for (int i = 0; i < n; ++i) {
@@ -457,6 +491,7 @@ qed_status build_tables(double* d64, float* d32, cudaStream_t st) {
   k_nbw<<<kNBX, 256, 0, st>>>(d64, scratch);
   k_vb<<<kNV, 256, 0, st>>>(d64);
   k_to_float<<<256, 256, 0, st>>>(d64, d32, kTableLen);
+  k_coef<<<(kNV + 255) / 256, 256, 0, st>>>(d64, d32);
   QCHK(cudaGetLastError());
   QCHK(cudaStreamSynchronize(st));
   QCHK(cudaFree(kn));
