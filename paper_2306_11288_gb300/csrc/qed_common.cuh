@@ -58,14 +58,17 @@ constexpr size_t kSmemRateLen = kOffCY - kOffRA;
 // and four FMAs.  Appended to the float copy of the tables (16-byte aligned):
 //   VB:  the difference M_par - M_perp (the only combination the photon pass uses), [kNV-3][4];
 //   NBW: T0 and T3 of one interval side by side, [kNBX-3][2][4];
-//   NCS: A and B of one interval side by side, [kNR-3][2][4].
+//   NCS: A and B of one interval side by side, [kNR-3][2][4];
+//   radiative pusher: q, psi1..3 / chi^3 of one interval side by side, [kNR-3][4][4]
+//   (read through L1/L2, not staged).
 constexpr size_t kOffCoefVB = (kTableLen + 3) / 4 * 4;
 constexpr size_t kOffCoefT = kOffCoefVB + 4 * (size_t)(kNV - 3);
 constexpr size_t kOffCoefN = kOffCoefT + 8 * (size_t)(kNBX - 3);
-constexpr size_t kTab32Len = kOffCoefN + 8 * (size_t)(kNR - 3);
+constexpr size_t kOffCoefRR = kOffCoefN + 8 * (size_t)(kNR - 3);
+constexpr size_t kTab32Len = kOffCoefRR + 16 * (size_t)(kNR - 3);
 // staged to shared memory by the photon pass (VB and NBW) and by the lepton pass (NCS)
 constexpr size_t kCoefPhLen = kOffCoefN - kOffCoefVB;
-constexpr size_t kCoefLepLen = kTab32Len - kOffCoefN;
+constexpr size_t kCoefLepLen = kOffCoefRR - kOffCoefN;
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) ------------------------------------------
 struct U4 { uint32_t a, b, c, d; };

@@ -407,10 +407,19 @@ struct Tabs {
   __device__ __forceinline__ void rr_funcs(R chi, R& qf, R& p1, R& p2, R& p3) const {
     const R X = (f_log(chi) - R(kRLo)) * R((kNR - 1) / (kRHi - kRLo));
     const R chi3 = chi * chi * chi;
-    qf = chi < R(kChiMin) ? R(1) : lagrange4(g + kOffRR, kNR, X);
-    p1 = chi3 * lagrange4(g + kOffRR + kNR, kNR, X);
-    p2 = chi3 * lagrange4(g + kOffRR + 2 * kNR, kNR, X);
-    p3 = chi3 * lagrange4(g + kOffRR + 3 * kNR, kNR, X);
+    if constexpr (sizeof(R) == 4) {
+      float f;
+      const float4* c = reinterpret_cast<const float4*>(g + kOffCoefRR) + 4 * coef_row(X, kNR, f);
+      qf = chi < R(kChiMin) ? R(1) : coef_cubic(c[0], f);
+      p1 = chi3 * coef_cubic(c[1], f);
+      p2 = chi3 * coef_cubic(c[2], f);
+      p3 = chi3 * coef_cubic(c[3], f);
+    } else {
+      qf = chi < R(kChiMin) ? R(1) : lagrange4(g + kOffRR, kNR, X);
+      p1 = chi3 * lagrange4(g + kOffRR + kNR, kNR, X);
+      p2 = chi3 * lagrange4(g + kOffRR + 2 * kNR, kNR, X);
+      p3 = chi3 * lagrange4(g + kOffRR + 3 * kNR, kNR, X);
+    }
   }
 };
 

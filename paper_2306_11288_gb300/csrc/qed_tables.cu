@@ -428,12 +428,16 @@ __global__ void k_coef(const double* d, float* f) {
     lagrange_cubic(a[0], a[1], a[2], a[3], f + kOffCoefT + 8 * (size_t)t);
     lagrange_cubic(b[0], b[1], b[2], b[3], f + kOffCoefT + 8 * (size_t)t + 4);
   }
-  if (t < kNR - 3) {   // NCS A, B
+  if (t < kNR - 3) {   // NCS A, B; radiative pusher q, psi1..3
     const int i = t + 1;
     const double* a = d + kOffRA + i - 1;
     const double* b = d + kOffRB + i - 1;
     lagrange_cubic(a[0], a[1], a[2], a[3], f + kOffCoefN + 8 * (size_t)t);
     lagrange_cubic(b[0], b[1], b[2], b[3], f + kOffCoefN + 8 * (size_t)t + 4);
+    for (int k = 0; k < 4; ++k) {
+      const double* q = d + kOffRR + (size_t)k * kNR + i - 1;
+      lagrange_cubic(q[0], q[1], q[2], q[3], f + kOffCoefRR + 16 * (size_t)t + 4 * k);
+    }
   }
 }
 
