@@ -320,7 +320,12 @@ qed_status qed_get_timing(qed_ctx *ctx, double ms[3], uint64_t *steps);
  *          [256 t], t = ln(level of the half distribution) in [-38, 0];
  *        5 VB M_par then M_perp, [2][1024] on ln chi_g in [ln 1e-3, ln 1e3];
  *        6 radiative pusher q(chi), psi1/chi^3, psi2/chi^3, psi3/chi^3, [4][512] on the
- *          grid of 1.
+ *          grid of 1;
+ *        7 the mixed path's float interval cubics of the 1-D tables, returned as doubles:
+ *          VB M_par - M_perp [1021][4], NBW T0, T3 [253][2][4], NCS A/chi, B/chi
+ *          [509][2][4], radiative pusher (the four tables of 6) [509][4][4]; row r holds
+ *          the 4-point Lagrange interpolant of node interval i = r + 1 as c0..c3 with
+ *          p(f) = c0 + f (c1 + f (c2 + f c3)), f = X - i (X in grid units).
  * *len receives the element count; host may be NULL to query it; otherwise cap must be
  * >= the count.  Errors: QED_ERR_INVALID_ARG (bad which, cap too small). */
 qed_status qed_copy_table(qed_ctx *ctx, int which, double *host, uint64_t cap, uint64_t *len, void *stream);

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "qed_common.cuh"
 #include "qed_internal.h"
@@ -564,12 +565,20 @@ extern "C" qed_status qed_copy_table(qed_ctx* c, int which, double* host, uint64
     case 4: off = kOffBY; n = 4 * (size_t)kNBX * kNBT; break;
     case 5: off = kOffMP; n = 2 * (size_t)kNV; break;
     case 6: off = kOffRR; n = 4 * (size_t)kNR; break;
-    default: FAIL(QED_ERR_INVALID_ARG, "qed_copy_table: which must be 0..6");
+    case 7: off = kOffCoefVB; n = kTab32Len - kOffCoefVB; break;
+    default: FAIL(QED_ERR_INVALID_ARG, "qed_copy_table: which must be 0..7");
   }
   *len = n;
   if (!host) return QED_OK;
   if (cap < n) FAIL(QED_ERR_INVALID_ARG, "qed_copy_table: cap %llu < %llu", (unsigned long long)cap,
                     (unsigned long long)n);
+  if (which == 7) {   // float block of the mixed path
+    std::vector<float> tmp(n);
+    CK(cudaMemcpyAsync(tmp.data(), c->tab32 + off, n * sizeof(float), cudaMemcpyDeviceToHost, S(stream)));
+    CK(cudaStreamSynchronize(S(stream)));
+    for (size_t i = 0; i < n; ++i) host[i] = (double)tmp[i];
+    return QED_OK;
+  }
   CK(cudaMemcpyAsync(host, c->tab64 + off, n * sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
   CK(cudaStreamSynchronize(S(stream)));
   return QED_OK;

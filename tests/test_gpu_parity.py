@@ -105,6 +105,32 @@ def test_tables_match_oracle(orc, ctx):
             assert rel.max() < 1e-11, (name, rel.max(), int(rel.argmax()))
 
 
+def test_interval_cubics_pass_through_the_oracle_nodes(orc, ctx):
+    """The mixed path holds each 1-D table as the cubic of every node interval; a cubic is
+    fixed by four points, so each row must reproduce the oracle's four nodes around its
+    interval (f = -1, 0, 1, 2) up to the float rounding of its coefficients."""
+    blk = q.qed_copy_table(ctx, 7)
+    ncs, nbw, vb, rr = orc.table(1).reshape(2, -1), orc.table(3).reshape(2, -1), orc.table(5).reshape(2, -1), \
+        orc.table(6).reshape(4, -1)
+    layout = [("vb", [vb[0] - vb[1]]), ("nbw", [nbw[0], nbw[1]]), ("ncs", [ncs[0], ncs[1]]),
+              ("radiative pusher", [rr[0], rr[1], rr[2], rr[3]])]
+    off = 0
+    fs = np.array([-1.0, 0.0, 1.0, 2.0])
+    powers = np.stack([fs ** 0, fs, fs ** 2, fs ** 3], 1)          # [4 f][4 coefficients]
+    for name, tables in layout:
+        n = len(tables[0])
+        rows = n - 3
+        c = blk[off:off + rows * 4 * len(tables)].reshape(rows, len(tables), 4)
+        off += rows * 4 * len(tables)
+        for k, y in enumerate(tables):
+            nodes = np.stack([y[r:r + 4] for r in range(rows)])      # y(i-1) .. y(i+2), i = r + 1
+            vals = c[:, k, :] @ powers.T                             # p(-1), p(0), p(1), p(2)
+            scale = np.abs(nodes).max(1, keepdims=True) + 1e-300
+            err = (np.abs(vals - nodes) / scale).max()
+            assert err < 2e-6, (name, k, err)
+    assert off == len(blk)
+
+
 def test_c1_plane_wave_fp64_full_crossing(orc, ctx):
     """Config 1 at 2000 electrons over the full 450-step crossing: NCS + T-BMT."""
     wl = workloads.c1(n=2000, seed=11)
