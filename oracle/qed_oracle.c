@@ -23,9 +23,10 @@
  *   radiative pusher ...... q, psi1..3 vs scipy quadrature and Mellin small-chi forms;
  *                           one LL step radiates the Larmor power; Sokolov-Ternov
  *                           build-up; MC mean = MLL + radiative T-BMT (Sec. III C)
- *   field models .......... Maxwell-like checks of the analytic fields (B = k x E)
- * parity unpinned: the exact shape of the paraxial Gaussian (a synthetic input model;
- * both sides implement the same first-order formula).
+ *   field models .......... B = k x E; the paraxial Gaussian satisfies the paraxial wave
+ *                           equation of a beam along -z, is flat and Gaussian at its
+ *                           focus, carries the same transverse power at every z, and
+ *                           keeps |E_perp| constant when circular
  */
 #include "qed_oracle.h"
 
