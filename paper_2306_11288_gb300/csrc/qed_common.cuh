@@ -69,6 +69,8 @@ constexpr size_t kTab32Len = kOffCoefRR + 16 * (size_t)(kNR - 3);
 // staged to shared memory by the photon pass (VB and NBW) and by the lepton pass (NCS)
 constexpr size_t kCoefPhLen = kOffCoefN - kOffCoefVB;
 constexpr size_t kCoefLepLen = kOffCoefRR - kOffCoefN;
+static_assert(kOffCoefVB % 4 == 0 && kOffCoefT % 4 == 0 && kOffCoefN % 4 == 0 && kOffCoefRR % 4 == 0,
+              "the interval cubics are read as float4");
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) ------------------------------------------
 struct U4 { uint32_t a, b, c, d; };

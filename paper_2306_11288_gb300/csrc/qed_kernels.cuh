@@ -913,6 +913,10 @@ struct DepShared {
   int bnd[5];           // imin, imax, jmin, jmax of the tile's nearest nodes; largest factor
   int J[3 * DepWin<T>::v];
 };
+// the depositing lepton pass: window + staged tables + tile bookkeeping within 48 KB of
+// static shared memory (1 KB left for the rest)
+static_assert(sizeof(DepShared<float>) + sizeof(float) * kCoefLepLen + 1024 <= 48 * 1024, "mixed deposit smem");
+static_assert(sizeof(DepShared<double>) + sizeof(double) * kSmemRateLen + 1024 <= 48 * 1024, "FP64 deposit smem");
 
 template <typename T>
 __device__ __forceinline__ void deposit_tile(const qed_fields& f, const DepMove<T>& m, DepShared<T>& sh) {
