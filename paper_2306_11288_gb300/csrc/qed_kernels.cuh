@@ -192,24 +192,35 @@ __device__ __forceinline__ int find_ens(const unsigned int* off, int n, unsigned
   return lo;
 }
 
-// block-wide bounds of (i, j) over the threads with on = true, into b[0..3] = imin, imax,
-// jmin, jmax (shared), and the largest of the non-negative values m (as int bits, which
-// order non-negative floats) into b[4]: one warp reduction and one shared atomic per warp
-// and bound
-__device__ __forceinline__ void block_bounds(bool on, int i, int j, float m, int* b) {
+// block-wide bounds over the threads with on = true, into shared b[]: b[0..3] = imin, imax,
+// jmin, jmax of (i, j); b[4 + k] = the largest of the non-negative values m[k], k < kM (as
+// int bits, which order non-negative floats); b[4 + kM] = the smallest positive of the
+// non-negative value p (+inf when none is positive).  One warp reduction and one shared
+// atomic per warp and bound.
+template <int kM>
+__device__ __forceinline__ void block_bounds(bool on, int i, int j, const float (&m)[kM], float p, int* b) {
+  constexpr int kInfBits = 0x7f800000;
   if (threadIdx.x == 0) {
-    b[0] = 0x7fffffff; b[1] = -0x7fffffff; b[2] = 0x7fffffff; b[3] = -0x7fffffff; b[4] = 0;
+    b[0] = 0x7fffffff; b[1] = -0x7fffffff; b[2] = 0x7fffffff; b[3] = -0x7fffffff;
+#pragma unroll
+    for (int k = 0; k < kM; ++k) b[4 + k] = 0;
+    b[4 + kM] = kInfBits;
   }
   __syncthreads();
   const int imin = __reduce_min_sync(0xffffffffu, on ? i : 0x7fffffff);
   const int imax = __reduce_max_sync(0xffffffffu, on ? i : -0x7fffffff);
   const int jmin = __reduce_min_sync(0xffffffffu, on ? j : 0x7fffffff);
   const int jmax = __reduce_max_sync(0xffffffffu, on ? j : -0x7fffffff);
-  const int mmax = __reduce_max_sync(0xffffffffu, on ? __float_as_int(m) : 0);
+  int mm[kM];
+#pragma unroll
+  for (int k = 0; k < kM; ++k) mm[k] = __reduce_max_sync(0xffffffffu, on ? __float_as_int(m[k]) : 0);
+  const int pmin = __reduce_min_sync(0xffffffffu, on && p > 0.0f ? __float_as_int(p) : kInfBits);
   if ((threadIdx.x & 31) == 0) {
     atomicMin(b, imin); atomicMax(b + 1, imax);
     atomicMin(b + 2, jmin); atomicMax(b + 3, jmax);
-    atomicMax(b + 4, mmax);
+#pragma unroll
+    for (int k = 0; k < kM; ++k) atomicMax(b + 4 + k, mm[k]);
+    atomicMin(b + 4 + kM, pmin);
   }
   __syncthreads();
 }
@@ -900,18 +911,24 @@ __device__ __forceinline__ void esirkepov_terms(const DepMove<T>& m, Add add) {
 // do not fit the window add every term to the grid directly.
 // The window sums in fixed point: integer shared-memory atomics run at about three times
 // the rate of float ones on this GPU, and integer sums do not depend on the order of the
-// adds.  Every term is a charge factor (cx, cy or cz) times a shape sum of magnitude at
-// most 1.  With c the tile's largest factor, c < 2^e, and the scale s = 2^(22 - e), a term
-// is at most 2^22 in units of 1/s, and one cell and component collects at most 256 terms
+// adds.  Each component has its own bound on a lepton's terms: a Jx term is cx times a
+// cumulative sum of shape differences, whose magnitude is at most the move |X1 - X0| (its
+// derivative in X is a linear B-spline, at most 1) times a weight of at most 1, so
+// |term| <= |cx (X1 - X0)|; likewise |cy (Y1 - Y0)| for Jy, and |cz| for Jz (the averaged
+// shape product is at most 1).  With b the tile's largest bound, b < 2^e, and the scale
+// s = 2^(22 - e), a term is at most 2^22 units, and one cell collects at most 256 terms
 // (one per lepton of the tile): below 2^30, inside int32.  Rounding a term to a multiple
-// of 1/s = 2^(e - 22) < 2c 2^-22 costs about one float ulp of the tile's largest term.
+// of 1/s < 2b 2^-22 costs about one float ulp of the tile's largest possible term.  For
+// the lighter leptons of a tile whose weights spread widely that is coarse, so a tile whose
+// largest charge factor exceeds 16 times its smallest sums the window in float instead.
 // Window cells: with the staged rate tables the block's static shared memory stays below
 // 48 KB (mixed: 16 KB of NCS interval cubics + 31 KB of window; FP64: 28 KB + 19 KB).
 template <typename T> struct DepWin { static constexpr int v = sizeof(T) == 4 ? 2600 : 1600; };
 template <typename T>
 struct DepShared {
-  int bnd[5];           // imin, imax, jmin, jmax of the tile's nearest nodes; largest factor
-  int J[3 * DepWin<T>::v];
+  int bnd[9];           // imin, imax, jmin, jmax of the tile's nearest nodes; largest term
+                        // bound per component; largest and smallest positive |cx|
+  int J[3 * DepWin<T>::v];   // int32 fixed point, or float (same bits for zero)
 };
 // the depositing lepton pass: window + staged tables + tile bookkeeping within 48 KB of
 // static shared memory (1 KB left for the rest)
@@ -922,8 +939,10 @@ template <typename T>
 __device__ __forceinline__ void deposit_tile(const qed_fields& f, const DepMove<T>& m, DepShared<T>& sh) {
   const int nx = f.nx, ny = f.ny, per = f.periodic;
   float* const gJ[3] = {f.gJx, f.gJy, f.gJz};
-  const float cmax = (float)fmax(fabs((double)m.cx), fmax(fabs((double)m.cy), fabs((double)m.cz)));
-  block_bounds(m.on, m.i0, m.j0, cmax, sh.bnd);
+  // per lepton: the bound of its terms of each component, and |cx| (its |q w| / (dy dt))
+  const float bnd_m[4] = {(float)(fabs(m.cx) * fabs(m.X1 - m.X0)), (float)(fabs(m.cy) * fabs(m.Y1 - m.Y0)),
+                          (float)fabs(m.cz), (float)fabs(m.cx)};
+  block_bounds<4>(m.on, m.i0, m.j0, bnd_m, bnd_m[3], sh.bnd);
   const int imin = sh.bnd[0], imax = sh.bnd[1], jmin = sh.bnd[2], jmax = sh.bnd[3];
   if (imax < imin) {            // nothing to deposit in this tile
     __syncthreads();
@@ -933,18 +952,32 @@ __device__ __forceinline__ void deposit_tile(const qed_fields& f, const DepMove<
   if (ww * wh <= DepWin<T>::v) {
     const int w = (int)ww, h = (int)wh, wi0 = imin - 2, wj0 = jmin - 2, nc = w * h;
     for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) sh.J[k] = 0;
-    // the tile's scale s = 2^(22 - e) with 2^e > cmax (frexpf: cmax = f 2^e, f < 1)
-    int e = 0;
-    frexpf(__int_as_float(sh.bnd[4]), &e);
-    e = e < -100 ? -100 : e;
-    const float s = ldexpf(1.0f, 22 - e), inv_s = ldexpf(1.0f, e - 22);
+    // fixed point unless the tile's charge factors spread by more than 16 (block-uniform)
+    const bool fixed = __int_as_float(sh.bnd[7]) <= 16.0f * __int_as_float(sh.bnd[8]);
+    float* const Jf = reinterpret_cast<float*>(sh.J);
+    // per component the scale s = 2^(22 - e) with 2^e > its bound (frexpf: b = f 2^e, f < 1)
+    float s[3], inv_s[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      int e = 0;
+      frexpf(__int_as_float(sh.bnd[4 + k]), &e);
+      e = e < -100 ? -100 : e;
+      s[k] = fixed ? ldexpf(1.0f, 22 - e) : 1.0f;
+      inv_s[k] = fixed ? ldexpf(1.0f, e - 22) : 1.0f;
+    }
     __syncthreads();
     if (m.on) {
-      DepMove<T> ms = m;
-      ms.cx = m.cx * (T)s; ms.cy = m.cy * (T)s; ms.cz = m.cz * (T)s;
-      esirkepov_terms<T>(ms, [&](int comp, int i, int j, float v) {
-        atomicAdd(&sh.J[comp * nc + (j - wj0) * w + (i - wi0)], __float2int_rn(v));
-      });
+      if (fixed) {
+        DepMove<T> ms = m;
+        ms.cx = m.cx * (T)s[0]; ms.cy = m.cy * (T)s[1]; ms.cz = m.cz * (T)s[2];
+        esirkepov_terms<T>(ms, [&](int comp, int i, int j, float v) {
+          atomicAdd(&sh.J[comp * nc + (j - wj0) * w + (i - wi0)], __float2int_rn(v));
+        });
+      } else {
+        esirkepov_terms<T>(m, [&](int comp, int i, int j, float v) {
+          atomicAdd(&Jf[comp * nc + (j - wj0) * w + (i - wi0)], v);
+        });
+      }
     }
     __syncthreads();
     // one warp per window row, lanes along the row
@@ -959,8 +992,8 @@ __device__ __forceinline__ void deposit_tile(const qed_fields& f, const DepMove<
         const int k = lj * w + li;
 #pragma unroll
         for (int comp = 0; comp < 3; ++comp) {
-          const int v = sh.J[comp * nc + k];
-          if (v != 0) atomicAdd(gJ[comp] + o, (float)v * inv_s);
+          const int v = sh.J[comp * nc + k];   // zero bits in both forms
+          if (v != 0) atomicAdd(gJ[comp] + o, fixed ? (float)v * inv_s[comp] : __int_as_float(v));
         }
       }
     }

@@ -139,6 +139,42 @@ def test_deposit_matches_oracle_and_conserves_charge(orc, ctx, prec, periodic, o
     sim.close()
 
 
+@pytest.mark.parametrize("prec", [q.QED_PREC_F64, q.QED_PREC_MIXED])
+@pytest.mark.parametrize("heavy", [1.0e4, 3.0])
+def test_deposit_keeps_light_particles_of_a_mixed_weight_tile(orc, ctx, prec, heavy):
+    """One tile of 256 electrons in a 16 x 8-cell patch: light ones (w = 1) everywhere, a
+    few of weight `heavy` in its right quarter.  Where no heavy stencil reaches, the current
+    must match the oracle's to 1e-5 of the light particles' own scale: a tile whose weights
+    spread by 1e4 must not round the light terms to the heavy ones' resolution."""
+    nx, ny, dx, dy, dt = 64, 48, 0.3, 0.25, 0.11
+    rng = np.random.default_rng(17)
+    n = 256
+    i0, j0 = 20, 20
+    d = _leptons(n, rng, ((i0 * dx, (i0 + 16) * dx), (j0 * dy, (j0 + 8) * dy)), 0.5)
+    d["w"] = np.ones(n)
+    hv = rng.choice(n, 24, replace=False)
+    d["x"][hv] = rng.uniform((i0 + 13) * dx, (i0 + 16) * dx, len(hv))
+    d["w"][hv] = heavy
+    d = _cell_sorted(d, dx, dy)
+    wl = {"e": d, "pos": workloads.empty(), "ph": workloads.empty(True), "dt": dt, "seed": 1, "next_id": n}
+    sim = q.PicSimulation(wl, nx, ny, dx, dy, periodic=0, prec=prec, ctx=ctx)
+    q.qed_step(sim.ctx, sim.e.handle, sim.pos.handle, sim.ph.handle, sim.fields, sim.t, sim.dt, sim.seed,
+               sim.step_no, q.QED_F_DEPOSIT, sim.stats.data_ptr())
+    J = sim.field_arrays()
+    og = oracle.YeeGrid(nx, ny, dx, dy, periodic=0)
+    osim = oracle.PicSim(orc, wl, og)
+    og.advance_b = lambda dt: None
+    og.advance_e = lambda dt: None
+    osim.run(1, 0)
+    light = np.s_[:, : i0 + 9]      # heavy stencils start at column i0 + 13 - 3
+    for k in ("Jx", "Jy", "Jz"):
+        scale = np.abs(og.a[k][light]).max()
+        assert scale > 0
+        err = np.abs(J[k][light] - og.a[k][light]).max() / scale
+        assert err < 1e-5, (k, err)
+    sim.close()
+
+
 def _plasma(nx, ny, dx, dy, ppc, n0, amp, seed):
     Lx = nx * dx
     k = 2 * math.pi / Lx
