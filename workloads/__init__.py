@@ -91,7 +91,10 @@ def c3_grid(nx=4096, ny=2048, a0=150.0, ncrit=100.0, seed=3):
     along +x whose centre has reached a slab at x_s = 3/4 of the box (plasma frequency
     sqrt(ncrit) omega0): in front of the slab the incident field plus its reflection (pi
     phase, the mirror image of the part beyond x_s); inside, decay as exp(-(x-x_s) w_p).
-    A single frozen snapshot; Ez = Bx = By = 0 (2D TE-like, z squeezed)."""
+    A single frozen snapshot, taken an eighth of a period after the instant at which the
+    standing wave in front of the slab has no electric field (x_s is a whole number of
+    wavelengths), so that E and B are both present; Ez = Bx = By = 0 (2D TE-like, z
+    squeezed)."""
     dx = TWO_PI / 32.0
     dy = dx
     xs = 0.75 * nx * dx
@@ -114,8 +117,9 @@ def c3_grid(nx=4096, ny=2048, a0=150.0, ncrit=100.0, seed=3):
 
     def field(xp, yp):
         tr = np.exp(-((yp[:, None] - yc) / wy) ** 2)
-        inc = profile(xp)[None, :] * np.cos(xp)[None, :]
-        refl = -profile(2 * xs - xp)[None, :] * np.cos(2 * xs - xp)[None, :]
+        ph0 = 0.25 * math.pi       # the carrier an eighth of a period on
+        inc = profile(xp)[None, :] * np.cos(xp - ph0)[None, :]
+        refl = -profile(2 * xs - xp)[None, :] * np.cos(2 * xs - xp - ph0)[None, :]
         vac = xp[None, :] < xs
         inside = np.exp(-np.clip(xp - xs, 0, None) * wp)[None, :]
         e = np.where(vac, inc + refl, (inc + refl) * inside)
