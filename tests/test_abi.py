@@ -35,6 +35,23 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(q.ABI_FUNCTIONS) == set(names)
 
 
+def test_header_is_plain_c(tmp_path):
+    """include/qed.h compiles as C99 (pedantic) and as C++: the boundary uses no C++ or
+    torch types, and a C program can link against the library by its declarations alone."""
+    import shutil
+    import subprocess
+    src = tmp_path / "use.c"
+    src.write_text('#include "qed.h"\nint main(void) { qed_ctx *c = 0; (void)c; return (int)QED_OK; }\n')
+    for cc, extra in (("gcc", ["-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror"]),
+                      ("g++", ["-std=c++17", "-Wall", "-Werror", "-x", "c++"])):
+        exe = shutil.which(cc)
+        if exe is None:
+            pytest.skip(f"{cc} not available")
+        r = subprocess.run([exe, *extra, "-fsyntax-only", "-I", os.path.join(ROOT, "include"), str(src)],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, (cc, r.stderr)
+
+
 def test_sm103a_build_flags():
     assert "arch=compute_103a,code=sm_103a" in qbuild.ARCH
     # the build recorded ptxas output for every translation unit, without spills
