@@ -28,6 +28,8 @@ F_NCS, F_NBW, F_VB, F_SPIN, F_NO_RECOIL, F_DROP_PHOTONS = 1, 2, 4, 8, 16, 32
 F_LL, F_MLL, F_MBMT = 128, 256, 512   # radiative pusher: LL, quantum-corrected LL, radiative T-BMT
 F_DEPOSIT = 1024                      # leptons deposit their current (Esirkepov)
 FIELD_NONE, FIELD_UNIFORM, FIELD_PLANE, FIELD_GAUSS, FIELD_GRID2D = 0, 1, 2, 3, 4
+# the decisions of a step, in the near-tie log (qed_oracle.h OR_D_*)
+DECISIONS = ("ncs", "ncs_collapse", "ncs_comp", "ncs_spin", "ncs_stokes", "nbw", "nbw_comp", "nbw_spin")
 
 
 def build(force: bool = False) -> str:
@@ -37,8 +39,11 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not fresh:
         tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        # OpenMP (optional: the particle loops of a step across host cores); plain build
+        # when the compiler has no OpenMP runtime
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _OUT)
     return _OUT
 
@@ -68,7 +73,7 @@ class Grid(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("n_ncs", C.c_uint64 * 2), ("n_nbw", C.c_uint64), ("n_range", C.c_uint64),
-                ("n_drop", C.c_uint64), ("n_near", C.c_uint64)]
+                ("n_drop", C.c_uint64), ("n_near", C.c_uint64), ("n_coarse", C.c_uint64)]
 
 
 def lib():
@@ -82,7 +87,12 @@ def lib():
             L.or_set_next_id.argtypes = [C.c_void_p, u64]
             L.or_get_next_id.argtypes = [C.c_void_p]
             L.or_get_next_id.restype = u64
-            L.or_near_log.argtypes = [C.c_void_p, C.POINTER(u64), C.POINTER(C.c_uint32), pd, u64]
+            L.or_near_log.argtypes = [C.c_void_p, C.POINTER(u64), C.POINTER(C.c_uint32),
+                                      C.POINTER(C.c_uint32), pd, u64]
+            L.or_near_log.restype = u64
+            L.or_set_near_tol.argtypes = [C.c_void_p, d]
+            L.or_set_threads.argtypes = [C.c_void_p, C.c_int]
+            L.or_set_threads.restype = C.c_int
             L.or_step.argtypes = [C.c_void_p, C.POINTER(Particles), C.POINTER(Particles),
                                   C.POINTER(Particles), C.POINTER(Fields), d, d, u64,
                                   C.c_uint32, C.c_uint32, C.POINTER(Stats)]
@@ -207,16 +217,28 @@ class Oracle:
                        float(t), float(dt), int(seed), int(step), int(flags), C.byref(st))
         e.sync(); pos.sync(); ph.sync()
         return {"n_ncs_e": st.n_ncs[0], "n_ncs_p": st.n_ncs[1], "n_nbw": st.n_nbw,
-                "n_range": st.n_range, "n_drop": st.n_drop, "n_near": st.n_near}
+                "n_range": st.n_range, "n_drop": st.n_drop, "n_near": st.n_near, "n_coarse": st.n_coarse}
 
-    def near_log(self, cap=65536):
+    def set_threads(self, n: int) -> int:
+        """Threads of the particle loops of a step (OpenMP); returns the count in effect."""
+        return int(self.L.or_set_threads(self.ctx, int(n)))
+
+    def set_near_tol(self, tol: float):
+        """Log every decision whose draw lies within ``tol`` relative of its threshold."""
+        self.L.or_set_near_tol(self.ctx, float(tol))
+
+    def near_log(self, cap=1 << 20):
+        """(ids, steps, kinds, margins) of the logged near-tie decisions (kinds: DECISIONS)."""
         ids = np.zeros(cap, dtype=np.uint64)
         steps = np.zeros(cap, dtype=np.uint32)
+        kinds = np.zeros(cap, dtype=np.uint32)
         m = np.zeros(cap)
-        self.L.or_near_log(self.ctx, ids.ctypes.data_as(C.POINTER(C.c_uint64)),
-                           steps.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(m), cap)
-        k = int((m > 0).sum())
-        return ids[:k], steps[:k], m[:k]
+        n = int(self.L.or_near_log(self.ctx, ids.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                   steps.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                   kinds.ctypes.data_as(C.POINTER(C.c_uint32)), _dp(m), cap))
+        if n > cap:
+            raise RuntimeError(f"near-tie log overflow: {n} entries, {cap} kept")
+        return ids[:n], steps[:n], kinds[:n], m[:n]
 
     # --- pieces -------------------------------------------------------------------
     def ktable(self, x):

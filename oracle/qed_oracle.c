@@ -2,7 +2,10 @@
  * qed_oracle.c -- FP64 CPU oracle of the spin/polarization-resolved SF-QED step of
  * Wan et al., arXiv:2306.11288.  TEST INFRASTRUCTURE ONLY (see qed_oracle.h).
  *
- * Plain, slow, single-threaded, compiled with -ffp-contract=off.  Every function
+ * Plain, slow, compiled with -ffp-contract=off; single-threaded unless or_set_threads asks
+ * for an OpenMP loop over the particles of a step (each particle's outcome goes to its own
+ * slot and births are appended in index order afterwards, so the results do not depend on
+ * the thread count).  Every function
  * names the passage of the paper it follows.  Where the paper is silent, garbled or
  * self-contradictory, the reading taken is stated at the point of use; the full list
  * is in the repository's design notes ("readings").
@@ -33,6 +36,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---- constants (CODATA 2018; the paper fixes none of them) ------------------- */
 static const double OR_PI = 3.14159265358979323846;
@@ -73,8 +79,10 @@ struct or_ctx {
   double mpar[NV], mperp[NV];                   /* VB M_par, M_perp               */
   double rr[4][NR];                             /* q, psi1/chi^3, psi2/chi^3, psi3/chi^3 */
   uint64_t next_id;
+  double near_tol;                              /* log decisions with |r - thr| < near_tol thr */
+  int threads;                                  /* particle-loop threads of or_step (OpenMP) */
   uint64_t nlog, logcap;
-  uint64_t *log_id; uint32_t *log_step; double *log_margin;
+  uint64_t *log_id; uint32_t *log_step, *log_kind; double *log_margin;
 };
 
 /* ======================================================================= *
@@ -619,23 +627,40 @@ or_ctx *or_ctx_create(void) {
     or_vb_exact(exp(V_LO + i * hv), m);
     c->mpar[i] = m[0]; c->mperp[i] = m[1];
   }
-  c->logcap = 1 << 16;
+  c->near_tol = 1e-6;
+  c->threads = 1;
+  c->logcap = 1 << 20;
   c->log_id = (uint64_t *)malloc(sizeof(uint64_t) * c->logcap);
   c->log_step = (uint32_t *)malloc(sizeof(uint32_t) * c->logcap);
+  c->log_kind = (uint32_t *)malloc(sizeof(uint32_t) * c->logcap);
   c->log_margin = (double *)malloc(sizeof(double) * c->logcap);
   return c;
 }
 
 void or_ctx_destroy(or_ctx *c) {
   if (!c) return;
-  free(c->log_id); free(c->log_step); free(c->log_margin);
+  free(c->log_id); free(c->log_step); free(c->log_kind); free(c->log_margin);
   free(c);
 }
 void or_set_next_id(or_ctx *c, uint64_t id) { c->next_id = id; c->nlog = 0; }
 uint64_t or_get_next_id(const or_ctx *c) { return c->next_id; }
-void or_near_log(or_ctx *c, uint64_t *ids, uint32_t *steps, double *margins, uint64_t cap) {
-  uint64_t n = c->nlog < cap ? c->nlog : cap;
-  for (uint64_t i = 0; i < n; ++i) { ids[i] = c->log_id[i]; steps[i] = c->log_step[i]; margins[i] = c->log_margin[i]; }
+void or_set_near_tol(or_ctx *c, double tol) { c->near_tol = tol; }
+int or_set_threads(or_ctx *c, int n) {
+#ifdef _OPENMP
+  c->threads = n < 1 ? 1 : n;
+#else
+  (void)n;
+  c->threads = 1;
+#endif
+  return c->threads;
+}
+uint64_t or_near_log(or_ctx *c, uint64_t *ids, uint32_t *steps, uint32_t *kinds, double *margins, uint64_t cap) {
+  uint64_t n = c->nlog < c->logcap ? c->nlog : c->logcap;
+  n = n < cap ? n : cap;
+  for (uint64_t i = 0; i < n; ++i) {
+    ids[i] = c->log_id[i]; steps[i] = c->log_step[i]; kinds[i] = c->log_kind[i]; margins[i] = c->log_margin[i];
+  }
+  return c->nlog;
 }
 
 const double *or_table(const or_ctx *c, int which, uint64_t *len) {
@@ -986,13 +1011,24 @@ void or_nbw_G(const or_ctx *c, double delta, double omega, double chig, const do
 typedef struct { double x[3], p[3], s[3], w; } or_lep_birth;
 typedef struct { double x[3], k[3], xi[3], th, w; } or_ph_birth;
 
-static void or_log_near(or_ctx *c, uint64_t id, uint32_t step, double r, double P, or_stats *st) {
-  if (P <= 0) return;
-  double m = fabs(r - P) / P;
-  if (m < 1e-6) {
+/* Near-tie log: every discrete decision "r < thr" of a step (r a uniform draw, thr its
+ * threshold) whose draw lies within near_tol relative of the threshold, |r - thr| < near_tol
+ * thr, is recorded as (id, step, kind, |r - thr|/thr).  A second implementation that
+ * computes thr with rounding errors of relative size e can take a different branch only
+ * where this margin is below e. */
+static void or_note(or_ctx *c, uint64_t id, uint32_t step, uint32_t kind, double r, double thr, or_stats *st) {
+  if (!(thr > 0.0)) return;
+  double m = fabs(r - thr) / thr;
+  if (m < c->near_tol) {
     if (st) st->n_near++;
-    if (c->nlog < c->logcap) {
-      c->log_id[c->nlog] = id; c->log_step[c->nlog] = step; c->log_margin[c->nlog] = m;
+#ifdef _OPENMP
+#pragma omp critical(or_near_log)
+#endif
+    {
+      if (c->nlog < c->logcap) {
+        c->log_id[c->nlog] = id; c->log_step[c->nlog] = step; c->log_kind[c->nlog] = kind;
+        c->log_margin[c->nlog] = m;
+      }
       c->nlog++;
     }
   }
@@ -1048,11 +1084,15 @@ static int or_photon(or_ctx *c, or_particles *ph, uint64_t i, const or_fields *f
       double P = OR_ALPHA / (sqrt(3.0) * OR_PI * OR_XIL * om) * (T[0] - xi[2] * T[1]) * dt;
       double r[2];
       or_uniforms(seed, ph->id[i], step, 3u, r);
-      or_log_near(c, ph->id[i], step, r[0], P, st);
+      or_note(c, ph->id[i], step, OR_D_NBW, r[0], P, st);
+      /* one event per particle per step (reading of the independence of events within a
+         step): count the decisions where that is coarse */
+      if (P > 0.1 && st) st->n_coarse++;
       if (r[0] < P) {
         /* energy split: mixture over xi3' = +-1 components */
         double w0 = 0.5 * (1.0 + xi[2]) * (T[0] - T[1]);
         int comp = (r[1] * (T[0] - xi[2] * T[1]) < w0) ? 0 : 1;
+        or_note(c, ph->id[i], step, OR_D_NBW_COMP, r[1], w0 / (T[0] - xi[2] * T[1]), st);
         double r2[2];
         or_uniforms(seed, ph->id[i], step, 4u, r2);
         double l = r2[0];
@@ -1101,6 +1141,11 @@ static int or_photon(or_ctx *c, or_particles *ph, uint64_t i, const or_fields *f
         for (int q = 0; q < 4; ++q) {
           acc += Pk[q];
           if (rr < acc) { o = q; break; }
+        }
+        double cum = 0;
+        for (int q = 0; q < 3; ++q) {   /* the three cumulative thresholds of the pick */
+          cum += Pk[q];
+          or_note(c, ph->id[i], step, OR_D_NBW_SPIN, r2[1], cum / tot, st);
         }
         double sp = (o < 2) ? 1.0 : -1.0, sm = (o % 2 == 0) ? 1.0 : -1.0;
         double pp = sqrt(ep * ep - 1.0), pm = sqrt(em * em - 1.0);
@@ -1268,7 +1313,8 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
       double P = (Wa - s * Wb) * dt;
       double r[2];
       or_uniforms(seed, L->id[i], step, 0u, r);
-      or_log_near(c, L->id[i], step, r[0], P, st);
+      or_note(c, L->id[i], step, OR_D_NCS, r[0], P, st);
+      if (P > 0.1 && st) st->n_coarse++;
       if (r[0] < P) {
         double rm[2], rs[2];
         or_uniforms(seed, L->id[i], step, 1u, rm);
@@ -1276,6 +1322,7 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
         /* photon energy: exact two-component mixture of Eq. Wspin2 at s = S.zeta */
         double wplus = 0.5 * (1.0 + s) * (AB[0] - AB[1]);
         int comp = (rm[0] * (AB[0] - s * AB[1]) < wplus) ? 0 : 1;
+        or_note(c, L->id[i], step, OR_D_NCS_COMP, rm[0], wplus / (AB[0] - s * AB[1]), st);
         double l = rm[1];
         double tt = (l > 0.0) ? log(l) - log1p(-l) : CT_LO;
         if (tt < CT_LO) tt = CT_LO;
@@ -1299,6 +1346,7 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
         double Sf[3];
         if (gm2 > 0.0) {
           double sgn = (rs[0] < 0.5 * (1.0 + gm2 / c0)) ? 1.0 : -1.0;
+          or_note(c, L->id[i], step, OR_D_NCS_SPIN, rs[0], 0.5 * (1.0 + gm2 / c0), st);
           for (int k = 0; k < 3; ++k) Sf[k] = sgn * g[k] / gm2;
         } else {
           for (int k = 0; k < 3; ++k) Sf[k] = S[k];
@@ -1309,6 +1357,7 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
         double xi[3] = {0, 0, 0};
         if (fm > 0.0) {
           double sg = (rs[1] < 0.5 * (1.0 + fm / F[0])) ? 1.0 : -1.0;
+          or_note(c, L->id[i], step, OR_D_NCS_STOKES, rs[1], 0.5 * (1.0 + fm / F[0]), st);
           for (int k = 0; k < 3; ++k) xi[k] = sg * F[k + 1] / fm;
         }
         for (int k = 0; k < 3; ++k) S[k] = Sf[k];
@@ -1339,6 +1388,7 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
         for (int k = 0; k < 3; ++k) Sb[k] = (S[k] * (1.0 - Wa * dt) + Wb * dt * z[k]) / den;
         double m = norm3(Sb);
         double sg = (r[1] < 0.5 * (1.0 + m)) ? 1.0 : -1.0;
+        or_note(c, L->id[i], step, OR_D_NCS_COLLAPSE, r[1], 0.5 * (1.0 + m), st);
         for (int k = 0; k < 3; ++k) S[k] = sg * Sb[k] / m;
       }
     }
@@ -1359,13 +1409,61 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
 int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, const or_fields *f, double t, double dt,
             uint64_t seed, uint32_t step, uint32_t flags, or_stats *st) {
   uint64_t nph = ph ? ph->n : 0, ne = e ? e->n : 0, np = pos ? pos->n : 0;
+  /* every particle's outcome goes to its own slot (index i), so the particle loops may run
+     in any order or in parallel; births are then appended in index order below */
   or_lep_birth *be = (or_lep_birth *)malloc(sizeof(or_lep_birth) * (nph + 1));
   or_lep_birth *bp = (or_lep_birth *)malloc(sizeof(or_lep_birth) * (nph + 1));
   or_ph_birth *bg = (or_ph_birth *)malloc(sizeof(or_ph_birth) * (ne + np + 1));
+  unsigned char *dflag = (unsigned char *)calloc(nph + 1, 1);
+  unsigned char *eflag = (unsigned char *)calloc(ne + np + 1, 1);
+  /* threads: optional, never with deposition (the current sums into one shared grid) */
+  int nt = (c->threads > 1 && !(flags & OR_F_DEPOSIT)) ? c->threads : 1;
+  or_stats *ts = (or_stats *)calloc((size_t)nt, sizeof(or_stats));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt) if (nt > 1)
+#endif
+  {
+    int me = 0;
+#ifdef _OPENMP
+    me = omp_get_thread_num();
+#endif
+    or_stats *mst = st ? &ts[me] : NULL;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 256)
+#endif
+    for (int64_t i = 0; i < (int64_t)nph; ++i)
+      dflag[i] = (unsigned char)or_photon(c, ph, (uint64_t)i, f, t, dt, seed, step, flags, &be[i], &bp[i], mst);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 256)
+#endif
+    for (int64_t i = 0; i < (int64_t)(ne + np); ++i) {
+      int is_e = i < (int64_t)ne;
+      or_particles *L = is_e ? e : pos;
+      uint64_t j = is_e ? (uint64_t)i : (uint64_t)i - ne;
+      eflag[i] = (unsigned char)or_lepton(c, L, j, is_e ? -1.0 : 1.0, f, t, dt, seed, step, flags, &bg[i], mst,
+                                          is_e ? 0 : 1);
+    }
+  }
+  if (st) {
+    for (int k = 0; k < nt; ++k) {
+      st->n_ncs[0] += ts[k].n_ncs[0]; st->n_ncs[1] += ts[k].n_ncs[1]; st->n_nbw += ts[k].n_nbw;
+      st->n_range += ts[k].n_range; st->n_drop += ts[k].n_drop; st->n_near += ts[k].n_near;
+      st->n_coarse += ts[k].n_coarse;
+    }
+  }
+  free(ts);
+  /* decays and emissions in index order: pair births (photon order), NCS photons (e- then
+     e+ order) */
   uint64_t nnbw = 0, nncs = 0;
   uint64_t *dec = (uint64_t *)malloc(sizeof(uint64_t) * (nph + 1));
   for (uint64_t i = 0; i < nph; ++i)
-    if (or_photon(c, ph, i, f, t, dt, seed, step, flags, &be[nnbw], &bp[nnbw], st)) dec[nnbw++] = i;
+    if (dflag[i]) {
+      be[nnbw] = be[i]; bp[nnbw] = bp[i];
+      dec[nnbw++] = i;
+    }
+  for (uint64_t i = 0; i < ne + np; ++i)
+    if (eflag[i]) bg[nncs++] = bg[i];
+  free(dflag); free(eflag);
   /* removal of decayed photons: with M = n - (decays), the k-th decayed slot below M
      receives the k-th surviving photon at or above M (both in index order) */
   if (ph) {
@@ -1384,10 +1482,6 @@ int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, con
     ph->n = M;
   }
   free(dec);
-  for (uint64_t i = 0; i < ne; ++i)
-    if (or_lepton(c, e, i, -1.0, f, t, dt, seed, step, flags, &bg[nncs], st, 0)) nncs++;
-  for (uint64_t i = 0; i < np; ++i)
-    if (or_lepton(c, pos, i, 1.0, f, t, dt, seed, step, flags, &bg[nncs], st, 1)) nncs++;
   /* append */
   uint64_t id = c->next_id;
   for (uint64_t k = 0; k < nnbw; ++k) {

@@ -82,8 +82,19 @@ typedef struct {
   uint64_t n_nbw;          /* pair creations                                   */
   uint64_t n_range;        /* chi clamped at a table's upper edge              */
   uint64_t n_drop;         /* births dropped for lack of capacity              */
-  uint64_t n_near;         /* decisions with |r-P| < 1e-6 P (logged)           */
+  uint64_t n_near;         /* decisions within the near-tie tolerance (logged) */
+  uint64_t n_coarse;       /* decisions with probability W dt or T dt above 0.1 */
 } or_stats;
+
+/* kinds of the discrete decisions of a step (near-tie log) */
+enum { OR_D_NCS = 0,          /* emission: r < W dt (Sec. III C)                     */
+       OR_D_NCS_COLLAPSE = 1, /* no-emission spin sign: r < (1 + |S_bar|)/2          */
+       OR_D_NCS_COMP = 2,     /* spin component of the energy mixture (Eq. Wspin2)   */
+       OR_D_NCS_SPIN = 3,     /* final spin sign along the SQA of Eq. F0             */
+       OR_D_NCS_STOKES = 4,   /* photon pure-state sign: r < (1 + |F|/F0)/2          */
+       OR_D_NBW = 5,          /* pair creation: r < T dt (Sec. III D)                */
+       OR_D_NBW_COMP = 6,     /* xi3' component of the energy mixture                */
+       OR_D_NBW_SPIN = 7 };   /* one of the three cumulative thresholds of the 4-way pick */
 
 typedef struct or_ctx or_ctx;
 
@@ -92,8 +103,16 @@ or_ctx *or_ctx_create(void);
 void or_ctx_destroy(or_ctx *c);
 void or_set_next_id(or_ctx *c, uint64_t id);
 uint64_t or_get_next_id(const or_ctx *c);
-/* near-tie log: (id, step, margin) of decisions within 1e-6 relative */
-void or_near_log(or_ctx *c, uint64_t *ids, uint32_t *steps, double *margins, uint64_t cap);
+/* Near-tie log: every decision "r < thr" of or_step with |r - thr| < tol thr is recorded
+ * as (id, step, kind, margin = |r - thr|/thr); tol defaults to 1e-6.  or_near_log copies up
+ * to cap entries (in the order the decisions were taken) and returns the number logged
+ * since the last or_set_next_id (which clears the log). */
+void or_set_near_tol(or_ctx *c, double tol);
+/* Threads of the particle loops of or_step (OpenMP; ignored with OR_F_DEPOSIT, whose
+ * current sums into one grid).  Results are the same for any count.  Returns the count
+ * in effect (1 when the oracle was built without OpenMP). */
+int or_set_threads(or_ctx *c, int n);
+uint64_t or_near_log(or_ctx *c, uint64_t *ids, uint32_t *steps, uint32_t *kinds, double *margins, uint64_t cap);
 
 int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph,
             const or_fields *f, double t, double dt, uint64_t seed, uint32_t step,
