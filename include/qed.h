@@ -42,9 +42,12 @@ typedef enum {
 } qed_status;
 
 /* bits of the device status word (qed_read_status) */
-#define QED_STATUS_CAPACITY 1u
-#define QED_STATUS_TIMEOUT 2u
-#define QED_STATUS_TABLE_RANGE 4u
+#define QED_STATUS_CAPACITY 1u     /* births dropped: a particle array was full             */
+#define QED_STATUS_TIMEOUT 2u      /* a bounded device wait gave up                          */
+#define QED_STATUS_TABLE_RANGE 4u  /* chi above a table's range was clamped                  */
+#define QED_STATUS_LOG_FULL 8u     /* a tile's events were not logged (event log full).  The
+                                      logs hold one event per particle of capacity, the most
+                                      a step can produce, so this bit marks a library fault */
 
 typedef enum { QED_ELECTRON = 0, QED_POSITRON = 1, QED_PHOTON = 2 } qed_species;
 
@@ -165,6 +168,9 @@ typedef struct {
   uint64_t n_drop;       /* births dropped for lack of capacity                */
   uint64_t n_steps;      /* steps accumulated                                  */
   uint64_t n_processed;  /* particle-steps: live e-, e+, photons at each step start */
+  uint64_t n_coarse;     /* decisions whose probability W dt (NCS) or T dt (NBW) exceeded
+                            0.1: the step allows one event per particle, which is a coarse
+                            description of such a step -- a smaller dt is advisable      */
 } qed_step_stats;
 
 typedef struct qed_ctx qed_ctx;             /* tables, id counter, scratch, status   */
@@ -279,16 +285,18 @@ qed_status qed_step_host(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed
  * runs while its stream is captured into a CUDA graph, or an application whose device
  * memory is all owned by its own allocator.  The paper has no counterpart of this call.
  * It runs exactly the kernels of qed_step, but keeps their per-step scratch (per-tile event
- * counts and prefixes, the event logs, the list of decayed photon slots) in one
- * file-scope device array of the library (about 5.7 MiB, held by every process that
- * loads the library on every device it uses) instead of the context's buffers, and
- * calls no cudaMalloc or cudaFree.  Limit: every given particle set must have capacity
- * <= 65536; larger sets are rejected with QED_ERR_INVALID_ARG (use qed_step).
- * The first call on a device looks the array's address up (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture on the device.
- * Every call shares the array and leaves its contents behind; each call clears the
- * event logs it needs first.  Calls whose work overlaps on the GPU (other streams,
- * other threads, other contexts) race on the array: order them on one stream.
+ * counts and prefixes, the event logs sized for one event per particle, the list of
+ * decayed photon slots) in one file-scope device array of the library (about 14.3 MiB,
+ * held by every process that loads the library on every device it uses) instead of the
+ * context's buffers, and calls no cudaMalloc or cudaFree.  Limit: every given particle
+ * set must have capacity <= 65536; larger sets are rejected with QED_ERR_INVALID_ARG (use
+ * qed_step).  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current and keeps it for the process; make that
+ * first call before any stream capture on the device, and do not use the call after a
+ * cudaDeviceReset (the kept address would be stale).  Every call, on every context of the
+ * process, shares the array and leaves its contents behind; a step reads only entries it
+ * has written, so nothing needs clearing.  Calls whose work overlaps on the GPU (other
+ * streams, other threads, other contexts) race on the array: order them on one stream.
  * The context, its tables and the particle sets are created as for qed_step.
  * Arguments, order of processes, ids and errors are those of qed_step.  Async. */
 qed_status qed_step_static(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed_particles *ph,

@@ -25,7 +25,7 @@ QED_F_MLP = 64
 QED_F_LL, QED_F_MLL, QED_F_MBMT = 128, 256, 512
 QED_F_DEPOSIT = 1024
 QED_FDTD_B, QED_FDTD_E = 0, 1
-QED_STATUS_CAPACITY, QED_STATUS_TIMEOUT, QED_STATUS_TABLE_RANGE = 1, 2, 4
+QED_STATUS_CAPACITY, QED_STATUS_TIMEOUT, QED_STATUS_TABLE_RANGE, QED_STATUS_LOG_FULL = 1, 2, 4, 8
 FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
 
 ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particles_count",
@@ -62,7 +62,8 @@ class qed_grid2d(C.Structure):
 
 class qed_step_stats(C.Structure):
     _fields_ = [("n_ncs", C.c_uint64 * 2), ("n_nbw", C.c_uint64), ("n_range", C.c_uint64),
-                ("n_drop", C.c_uint64), ("n_steps", C.c_uint64), ("n_processed", C.c_uint64)]
+                ("n_drop", C.c_uint64), ("n_steps", C.c_uint64), ("n_processed", C.c_uint64),
+                ("n_coarse", C.c_uint64)]
 
 
 class qed_diag_spec(C.Structure):
@@ -509,7 +510,7 @@ class Simulation:
         self.t = float(wl.get("t0", 0.0))
         self.seed = int(wl["seed"])
         self.step_no = int(wl.get("step0", 0))
-        self.stats = torch.zeros(7, dtype=torch.int64, device="cuda")
+        self.stats = torch.zeros(8, dtype=torch.int64, device="cuda")
         qed_set_next_id(self.ctx, int(wl["next_id"]))
         qed_read_status(self.ctx, clear=True)
 
@@ -528,7 +529,7 @@ class Simulation:
     def counters(self) -> dict:
         s = self.stats.cpu().numpy()
         return {"n_ncs_e": int(s[0]), "n_ncs_p": int(s[1]), "n_nbw": int(s[2]), "n_range": int(s[3]),
-                "n_drop": int(s[4]), "n_steps": int(s[5]), "n_processed": int(s[6])}
+                "n_drop": int(s[4]), "n_steps": int(s[5]), "n_processed": int(s[6]), "n_coarse": int(s[7])}
 
     def status(self, clear=False) -> int:
         return qed_read_status(self.ctx, clear)

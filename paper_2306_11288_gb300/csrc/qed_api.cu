@@ -144,15 +144,15 @@ extern "C" qed_status qed_destroy(qed_ctx* c) {
 static unsigned long long tiles_of(unsigned long long n) { return (n + kTile - 1) / kTile; }
 
 // (Re)sizes the step scratch for the largest capacities seen on this context:
-// per-tile event counts and prefixes, the two event logs (worst case the FP64 record
-// size), and the ranked hole list.  Logs hold up to 1/8 of the photon capacity (decays)
-// and 1/2 of the lepton capacity (emissions) per step; beyond that a step flags
-// QED_STATUS_CAPACITY.
+// per-tile event counts and prefixes, the two event logs (the FP64 record size) and the
+// ranked hole list.  The logs are sized for the worst case -- every live photon decays and
+// every live lepton emits in one step (at most one event per particle per step) -- so a
+// step never drops an event.
 static qed_status grow_scratch(qed_ctx* c, cudaStream_t s) {
   const unsigned long long tp = tiles_of(c->cap_seen[2]) + 1;
   const unsigned long long tl = tiles_of(c->cap_seen[0]) + tiles_of(c->cap_seen[1]) + 1;
-  const unsigned long long rn = c->cap_seen[2] / 8 + 4096;
-  const unsigned long long rl = (c->cap_seen[0] + c->cap_seen[1]) / 2 + 4096;
+  const unsigned long long rn = c->cap_seen[2] > 0 ? c->cap_seen[2] : 1;
+  const unsigned long long rl = c->cap_seen[0] + c->cap_seen[1] > 0 ? c->cap_seen[0] + c->cap_seen[1] : 1;
   const unsigned long long want_t[2] = {tp, tl}, want_r[2] = {rn, rl};
   const size_t rbytes[2] = {nbw_rec_bytes(QED_PREC_F64), ncs_rec_bytes(QED_PREC_F64)};
   bool sync_done = false;
@@ -326,10 +326,20 @@ void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos,
   E.ff.inv_zr = f->w0 > 0.0 ? (float)(2.0 / (f->w0 * f->w0)) : 0.0f;
   E.ff.inv_w02 = f->w0 > 0.0 ? (float)(1.0 / (f->w0 * f->w0)) : 0.0f;
   if (f->kind == QED_FIELD_GRID2D && f->dx > 0.0 && f->dy > 0.0) {
-    E.ff.gix = (float)(1.0 / f->dx);
-    E.ff.giy = (float)(1.0 / f->dy);
-    E.ff.gox = (float)(f->x0 / f->dx);
-    E.ff.goy = (float)(f->y0 / f->dy);
+    // float splits hi + lo of the grid constants: the mixed path forms cell coordinates as
+    // an integer node plus a float offset from them (no FP64 arithmetic on the device)
+    auto split = [](double v, float& h, float& l) {
+      h = (float)v;
+      l = (float)(v - (double)h);
+    };
+    split(1.0 / f->dx, E.ff.gix, E.ff.gix_lo);
+    split(1.0 / f->dy, E.ff.giy, E.ff.giy_lo);
+    const double ox = f->x0 / f->dx, oy = f->y0 / f->dy;
+    const double gx = std::floor(ox), gy = std::floor(oy);
+    E.ff.gox_i = (int)gx;
+    E.ff.goy_i = (int)gy;
+    split(ox - gx, E.ff.gox, E.ff.gox_lo);
+    split(oy - gy, E.ff.goy, E.ff.goy_lo);
   }
 }
 }  // namespace qedk

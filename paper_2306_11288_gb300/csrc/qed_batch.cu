@@ -264,8 +264,9 @@ extern "C" qed_status qed_batch_create(qed_ctx* ctx, const qed_ensemble* ens, in
     b->occ[0][0] = stream_occupancy<float, false>(0); b->occ[0][1] = stream_occupancy<float, false>(1);
     b->occ[1][0] = stream_occupancy<float, true>(0); b->occ[1][1] = stream_occupancy<float, true>(1);
   }
-  b->rec_cap[0] = cap_ph / 8 + 4096;
-  b->rec_cap[1] = cap_l / 2 + 4096;
+  // worst case: every photon decays, every lepton emits (one event per particle per step)
+  b->rec_cap[0] = cap_ph > 0 ? cap_ph : 1;
+  b->rec_cap[1] = cap_l > 0 ? cap_l : 1;
   const size_t rbytes[2] = {nbw_rec_bytes(QED_PREC_F64), ncs_rec_bytes(QED_PREC_F64)};
   const unsigned long long tiles[2] = {tp, tl};
   if (e == cudaSuccess) e = cudaMalloc(&b->d_ens, sizeof(EnsArgs) * n_ens);

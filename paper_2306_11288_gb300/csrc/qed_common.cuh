@@ -292,7 +292,7 @@ struct DevState {
   unsigned long long n_nbw;          // this step: pairs created (ranked decays)
   unsigned long long n_ncs_tot;      // this step: ranked emissions
   unsigned long long cursor[2];      // this step: entries written to the NBW / NCS logs
-  unsigned long long ev[6];          // this step: ncs_e, ncs_p, spare, range, drop, spare
+  unsigned long long ev[6];          // this step: ncs_e, ncs_p, coarse (P > 0.1), range, drop, spare
   unsigned int done;                 // finished-block counter of the last kernel
   unsigned int epoch;                // stamp of this step's log entries
   unsigned int status;               // QED_STATUS_* bits (sticky)

@@ -38,7 +38,10 @@ struct SpeciesArgs {
 // float copies of per-step constants for the mixed path (no FP64 arithmetic in kernels)
 struct FloatConsts {
   float dt, inv_len, t_rel, t_mod, a0, w0, zf, zr, inv_zr, inv_w02;
-  float gix, giy, gox, goy;           // grid: 1/dx, 1/dy, x0/dx, y0/dy
+  // grid: 1/dx = gix + gix_lo and 1/dy (float splits); x0/dx = gox_i + gox + gox_lo and
+  // y0/dy likewise (integer part and float split of the fraction)
+  float gix, gix_lo, giy, giy_lo, gox, gox_lo, goy, goy_lo;
+  int gox_i, goy_i;
 };
 
 // the arguments of one ensemble (a set of e-, e+, photons in one field)

@@ -94,19 +94,47 @@ __device__ __forceinline__ R tsc_gather(const float* g, int nx, int ny, int peri
   return acc;
 }
 
-// Mixed path: the same TSC gather with the cell coordinates in float (no FP64 arithmetic).
-// The cell coordinate carries an absolute error of about 2^-24 of its value (below 3e-4
-// of a cell on a 4096-cell axis); the TSC shape is continuous with a continuous slope
-// across cell boundaries, so this moves the gathered field by that much times its
-// gradient, whichever stencil the rounding selects.
-__device__ __forceinline__ int tsc_axis(float X, float w[3]) {
-  const float f = floorf(X + 0.5f);
-  const float d = X - f;
+// Mixed path: the same TSC gather without FP64 arithmetic.  A position is carried to the
+// grid as a cell coordinate X = I + a, I an integer node and a a float offset (|a| <~ 1),
+// formed from the double position split into two floats by bit operations and from float
+// splits of 1/dx and x0/dx: a is exact to its own float rounding (~1e-7 of a cell) however
+// large X is.  (A plain float X = float(x) / dx would carry 2^-24 of X: 2.4e-4 of a cell at
+// X = 4096, which next to a steep field, such as the evanescent field inside a dense slab,
+// moves the gathered field by ~1e-3 of itself.)
+//
+// the low 29 mantissa bits of x that d2f_bits drops: x = d2f_bits(x) + d2f_lo(x), the low
+// part rounded to float (integer operations and one conversion)
+__device__ __forceinline__ float d2f_lo(double x) {
+  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+  const int se = (int)((hi >> 20) & 0x7FFu) - 1023 - 52 + 127;   // float exponent bits of 2^(e - 52)
+  const float v = __uint2float_rn(lo & 0x1FFFFFFFu) * (se > 0 ? __int_as_float(se << 23) : 0.0f);
+  return (hi & 0x80000000u) ? -v : v;
+}
+struct Cell {
+  int I;     // integer part
+  float a;   // offset from I
+};
+// X = (x - x0)/dx with 1/dx = ih + il and x0/dx = G + oh + ol
+__device__ __forceinline__ Cell cell_of(double x, float ih, float il, int G, float oh, float ol) {
+  const float xh = d2f_bits(x), xl = d2f_lo(x);
+  const float fi = floorf(xh * ih);
+  float a = fmaf(xh, ih, -fi);   // xh ih - fi, one rounding
+  a = fmaf(xh, il, a);
+  a = fmaf(xl, ih, a);
+  a = (a - oh) - ol;
+  return Cell{(int)fi - G, a};
+}
+// TSC weights on the grid shifted by `shift` cells (0: nodes, 0.5: half-cell positions) and
+// the first of the three nodes
+__device__ __forceinline__ int tsc_axis(Cell c, float shift, float w[3]) {
+  const float t = c.a - shift;
+  const float f = floorf(t + 0.5f);
+  const float d = t - f;
   const float lo = 0.5f - d, hi = 0.5f + d;
   w[0] = 0.5f * lo * lo;
   w[1] = 0.75f - d * d;
   w[2] = 0.5f * hi * hi;
-  return (int)f - 1;
+  return c.I + (int)f - 1;
 }
 // kPair: on grids with an even row length (and an 8-byte aligned component), read each
 // stencil row as one aligned pair of nodes and one single node, 6 loads per component
@@ -280,10 +308,11 @@ __device__ __forceinline__ EB<R> gather(const EnsArgs& E, const EnsTime& tm, dou
     r.B.x = r.E.y;
     r.B.y = -r.E.x;
   } else if (f.kind == QED_FIELD_GRID2D && sizeof(R) == 4) {
-    const float X = d2f_bits(x) * E.ff.gix - E.ff.gox, Y = d2f_bits(y) * E.ff.giy - E.ff.goy;
+    const Cell cx = cell_of(x, E.ff.gix, E.ff.gix_lo, E.ff.gox_i, E.ff.gox, E.ff.gox_lo);
+    const Cell cy = cell_of(y, E.ff.giy, E.ff.giy_lo, E.ff.goy_i, E.ff.goy, E.ff.goy_lo);
     float wx0[3], wx1[3], wy0[3], wy1[3];
-    const int i0 = tsc_axis(X, wx0), ih = tsc_axis(X - 0.5f, wx1);
-    const int j0 = tsc_axis(Y, wy0), jh = tsc_axis(Y - 0.5f, wy1);
+    const int i0 = tsc_axis(cx, 0.0f, wx0), ih = tsc_axis(cx, 0.5f, wx1);
+    const int j0 = tsc_axis(cy, 0.0f, wy0), jh = tsc_axis(cy, 0.5f, wy1);
     r.E.x = (R)tsc_sum<kPair>(f.gEx, f.nx, f.ny, f.periodic, ih, j0, wx1, wy0);
     r.E.y = (R)tsc_sum<kPair>(f.gEy, f.nx, f.ny, f.periodic, i0, jh, wx0, wy1);
     r.E.z = (R)tsc_sum<kPair>(f.gEz, f.nx, f.ny, f.periodic, i0, j0, wx0, wy0);
@@ -577,7 +606,8 @@ struct NcsRec {
 
 // In-tile ranks of flagged threads and one reservation in the event log per tile.
 // Returns the thread's slot in the log, or ~0 when the tile's events were not logged
-// (log full: QED_STATUS_CAPACITY).  tile_cnt[tile] receives the logged count.
+// (log full: QED_STATUS_LOG_FULL; the logs are sized for one event per particle, so this
+// is a safeguard).  tile_cnt[tile] receives the logged count.
 struct TileShared {
   unsigned int wc[kTile / 32];
   unsigned long long base;
@@ -606,7 +636,7 @@ __device__ __forceinline__ unsigned long long tile_log(bool flag, unsigned int t
     }
     const unsigned long long base = atomicAdd(cursor, (unsigned long long)run);
     const int ok = base + run <= cap;
-    if (!ok) atomicOr(status, QED_STATUS_CAPACITY);
+    if (!ok) atomicOr(status, QED_STATUS_LOG_FULL);
     sh.base = base;
     sh.ok = ok;
     tile_cnt[tile] = ok ? run : 0u;
@@ -792,6 +822,8 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
           const R Pd = R(kAlpha / (1.7320508075688772935 * kPi * kXiL)) * inv_om * (T0 - xi.z * T3) * dt;
           const URand<R> u = urand<R, !kB>(E, id, tm.step, 3u);
           decay = u.u0 < Pd;
+          // one event per photon per step is coarse where T dt > 0.1 (rare: no ballot)
+          if (Pd > R(0.1)) atomicAdd(&st->ev[2], 1ull);
           rmix = u.u1;
         }
       }
@@ -842,21 +874,26 @@ __device__ __forceinline__ void tsc5(T X, int base, int shift, T S[5]) {
   S[3 + shift] = T(0.5) * hi * hi;
 }
 
-// A lepton's move for the deposition, in cell units, and its charge factors
+// A lepton's move for the deposition, in cell units relative to the node (ib, jb), and its
+// charge factors
 template <typename T>
 struct DepMove {
-  T X0, Y0, X1, Y1;     // old and new position (cells)
+  T X0, Y0, X1, Y1;     // old and new position (cells, relative to node ib, jb)
   T cx, cy, cz;         // -q w/(dy dt), -q w/(dx dt), q w vz/(dx dy)
-  int i0, j0;           // old nearest node
+  int ib, jb;           // node the coordinates are relative to (FP64 path: 0)
+  int i0, j0;           // old nearest node (absolute)
   bool on;              // live and within one cell per axis
 };
 
 template <typename T>
-__device__ __forceinline__ void dep_move(DepMove<T>& m, T X0, T Y0, T X1, T Y1, T cx, T cy, T cz) {
+__device__ __forceinline__ void dep_move(DepMove<T>& m, T X0, T Y0, T X1, T Y1, T cx, T cy, T cz, int ib = 0,
+                                         int jb = 0) {
   m.X0 = X0; m.Y0 = Y0; m.X1 = X1; m.Y1 = Y1; m.cx = cx; m.cy = cy; m.cz = cz;
-  m.i0 = (int)floor(X0 + T(0.5));
-  m.j0 = (int)floor(Y0 + T(0.5));
-  const int di = (int)floor(X1 + T(0.5)) - m.i0, dj = (int)floor(Y1 + T(0.5)) - m.j0;
+  m.ib = ib; m.jb = jb;
+  const int il = (int)floor(X0 + T(0.5)), jl = (int)floor(Y0 + T(0.5));
+  m.i0 = ib + il;
+  m.j0 = jb + jl;
+  const int di = (int)floor(X1 + T(0.5)) - il, dj = (int)floor(Y1 + T(0.5)) - jl;
   m.on = di >= -1 && di <= 1 && dj >= -1 && dj <= 1;   // beyond the solver's CFL: not deposited
 }
 
@@ -866,13 +903,14 @@ __device__ __forceinline__ void dep_move(DepMove<T>& m, T X0, T Y0, T X1, T Y1, 
 // carry no current (their cumulative sums vanish), so they are not visited.
 template <typename T, typename Add>
 __device__ __forceinline__ void esirkepov_terms(const DepMove<T>& m, Add add) {
-  const int i0 = m.i0, j0 = m.j0;
-  const int di = (int)floor(m.X1 + T(0.5)) - i0, dj = (int)floor(m.Y1 + T(0.5)) - j0;
+  const int i0 = m.i0, j0 = m.j0;                 // absolute node indices of the adds
+  const int il = i0 - m.ib, jl = j0 - m.jb;       // the same nodes in the move's local frame
+  const int di = (int)floor(m.X1 + T(0.5)) - il, dj = (int)floor(m.Y1 + T(0.5)) - jl;
   T S0x[5], S1x[5], S0y[5], S1y[5];
-  tsc5<T>(m.X0, i0, 0, S0x);
-  tsc5<T>(m.X1, i0, di, S1x);
-  tsc5<T>(m.Y0, j0, 0, S0y);
-  tsc5<T>(m.Y1, j0, dj, S1y);
+  tsc5<T>(m.X0, il, 0, S0x);
+  tsc5<T>(m.X1, il, di, S1x);
+  tsc5<T>(m.Y0, jl, 0, S0y);
+  tsc5<T>(m.Y1, jl, dj, S1y);
   const int cl = 1 + (di < 0 ? di : 0), ch = 3 + (di > 0 ? di : 0);
   const int bl = 1 + (dj < 0 ? dj : 0), bh = 3 + (dj > 0 ? dj : 0);
   // unrolled over the 5 stencil nodes (register arrays), predicated on the support
@@ -1113,11 +1151,14 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
       } else {
         const R c = dt * inv_g1;
         if constexpr (kDep) {
-          // cell coordinates in float (as the gather), the move from the float displacement
-          const float X0 = d2f_bits(x) * E.ff.gix - E.ff.gox, Y0 = d2f_bits(y) * E.ff.giy - E.ff.goy;
+          // cell coordinates as in the gather (node + float offset), the move from the float
+          // displacement that the position update adds
+          const Cell cx = cell_of(x, E.ff.gix, E.ff.gix_lo, E.ff.gox_i, E.ff.gox, E.ff.gox_lo);
+          const Cell cy = cell_of(y, E.ff.giy, E.ff.giy_lo, E.ff.goy_i, E.ff.goy, E.ff.goy_lo);
           const float qw = (float)q * (float)ld<R>(L.w, i), idt = 1.0f / (float)dt;
-          dep_move<R>(dm, X0, Y0, X0 + (float)(c * pn.x) * E.ff.gix, Y0 + (float)(c * pn.y) * E.ff.giy,
-                      -qw * E.ff.giy * idt, -qw * E.ff.gix * idt, qw * (float)(c * pn.z) * idt * E.ff.gix * E.ff.giy);
+          dep_move<R>(dm, cx.a, cy.a, cx.a + (float)(c * pn.x) * E.ff.gix, cy.a + (float)(c * pn.y) * E.ff.giy,
+                      -qw * E.ff.giy * idt, -qw * E.ff.gix * idt, qw * (float)(c * pn.z) * idt * E.ff.gix * E.ff.giy,
+                      cx.I, cy.I);
         }
         x = add_pos(x, c * pn.x); y = add_pos(y, c * pn.y); z = add_pos(z, c * pn.z);
       }
@@ -1157,6 +1198,8 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
           const R Wa = pref * A, Wb = pref * B;
           const R Pe = (Wa - s * Wb) * dt;
           const URand<R> u = urand<R, !kB>(E, id, tm.step, 0u);
+          // one event per lepton per step is coarse where W dt > 0.1 (rare: no ballot)
+          if (Pe > R(0.1)) atomicAdd(&st->ev[2], 1ull);
           if (u.u0 < Pe) {
             emit = true;   // completed by k_ncs_ev
           } else {
@@ -1536,6 +1579,7 @@ __device__ __forceinline__ void close_step(const StepArgs& a, bool births) {
       E.user_stats->n_range += v->ev[3];
       E.user_stats->n_drop += v->ev[4];
       E.user_stats->n_steps += 1;
+      E.user_stats->n_coarse += v->ev[2];
     }
     if (v->ev[3]) atomicOr(&gst->status, QED_STATUS_TABLE_RANGE);
     for (int q = 0; q < 6; ++q) v->ev[q] = 0;

@@ -18,8 +18,9 @@ namespace qedk {
 constexpr unsigned long long kStaticMaxCap = 65536;   // capacity limit per species
 constexpr unsigned long long kStTilesPh = (kStaticMaxCap + kTile - 1) / kTile + 1;
 constexpr unsigned long long kStTilesLep = 2 * ((kStaticMaxCap + kTile - 1) / kTile) + 1;
-constexpr unsigned long long kStRecNbw = kStaticMaxCap / 8 + 4096;
-constexpr unsigned long long kStRecNcs = (2 * kStaticMaxCap) / 2 + 4096;
+// event logs for the worst case: every photon decays, every e- and e+ emits
+constexpr unsigned long long kStRecNbw = kStaticMaxCap;
+constexpr unsigned long long kStRecNcs = 2 * kStaticMaxCap;
 constexpr size_t kAlign = 256;
 constexpr size_t rnd(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 // layout of the array (byte offsets); logs are sized for the FP64 record layout
@@ -31,7 +32,7 @@ constexpr size_t kSoHoles = kSoPreLep + rnd(4 * kStTilesLep);
 constexpr size_t kSoLogNbw = kSoHoles + rnd(4 * kStRecNbw);
 constexpr size_t kNbwRecMax = 96, kNcsRecMax = 64;   // bytes per record, bounds checked at run time
 constexpr size_t kSoLogNcs = kSoLogNbw + rnd(kNbwRecMax * kStRecNbw);
-constexpr size_t kStaticBytes = kSoLogNcs + rnd(kNcsRecMax * kStRecNcs);   // about 5.7 MiB
+constexpr size_t kStaticBytes = kSoLogNcs + rnd(kNcsRecMax * kStRecNcs);   // about 14.3 MiB
 
 // One array per process and device, shared by every call and every context.
 static __device__ __align__(256) unsigned char g_step_scratch[kStaticBytes];
@@ -133,13 +134,10 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
   if (r != QED_OK) return r;
   unsigned char* b = static_cast<unsigned char*>(base);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // the logs keep the previous call's entries: clear them so that none can be mistaken
-  // for an entry of this step (the step reads only entries it wrote, this is a safeguard)
-  cudaError_t ce = cudaMemsetAsync(b + kSoLogNbw, 0, kStaticBytes - kSoLogNbw, s);
-  if (ce != cudaSuccess) {
-    set_error("qed_step_static: cudaMemsetAsync: %s", cudaGetErrorString(ce));
-    return QED_ERR_CUDA;
-  }
+  // Nothing is cleared: the array keeps the previous call's contents, and a step reads
+  // only entries it has written itself -- every tile's count (the streaming passes write
+  // one per tile, events or not), the first `cursor` log records (a log holds the worst
+  // case, so every reserved record is written) and the ranked decay slots.
   StepArgs a;
   memset(&a, 0, sizeof(a));
   fill_ensemble(a.e0, e, pos, ph, f, t, seed, step, c->st, dev_stats);

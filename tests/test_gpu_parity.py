@@ -1,14 +1,18 @@
 """GPU (sm_103a) vs oracle parity through the C ABI, on identical seeded inputs.
 
 FP64 path: event counts and ids bit-exact; per-particle momenta, spins, Stokes and
-positions within 1e-10 relative.  Mixed path: 2e-5 per particle over short runs and
-spectra/polarisation/pair yield within 3 sigma of the oracle's statistical error."""
+positions within 1e-10 relative.  Mixed path: every electron within 2e-5 (momentum, spin,
+position) over a 200-step run, except those with a logged near-tie decision (the rule of
+``parity_rules``); photon spectra, photon Stokes parameters in a detection basis, pair
+yield and positron spin within 3 sigma of the statistical error (independent seeds), on
+the plane-wave workload and on the focused-pulse workload with every process on."""
 import math
 
 import numpy as np
 import pytest
 
 import oracle
+import parity_rules
 import workloads
 
 torch = pytest.importorskip("torch")
@@ -137,6 +141,7 @@ def test_c1_plane_wave_fp64_full_crossing(orc, ctx):
     sim, osim, ost = _run_both(orc, ctx, wl, 450, q.QED_F_NCS | q.QED_F_SPIN)
     c = sim.counters()
     assert c["n_ncs_e"] == ost["n_ncs_e"] and c["n_ncs_e"] > 1000
+    assert c["n_coarse"] == ost["n_coarse"] == 0   # W dt stays well below 0.1 at dt = T0/200
     assert sim.status() == 0
     d = _compare_all(sim, osim, 1e-10, 1e-10)
     print("max diffs", d)
@@ -208,6 +213,34 @@ def test_capacity_overflow_flags_and_matches(orc, ctx):
     _compare(gs["e"], os_["e"], "e", 1e-10, 1e-10)
 
 
+def test_mass_decay_step_logs_every_event_fp64(orc, ctx):
+    """30 % of 200,000 photons decay in one step (chi_gamma = 1, dt = 0.3 / rate; the
+    geometry of the oracle's one-step NBW statistics): one event per photon is the most a
+    step can log, and the logs hold that many, so nothing is dropped -- pair count, ids
+    and every particle agree with the oracle (FP64, 1e-10) and the status word stays 0."""
+    xil, alpha = 2.42631023867e-6, 7.2973525693e-3
+    om, chig, N = 4000.0, 1.0, 200_000
+    E0 = chig / (xil * om * 2)
+    xi = np.array([0.3, -0.4, 0.5])
+    ph = {"x": np.zeros(N), "y": np.zeros(N), "z": np.zeros(N), "px": np.full(N, om), "py": np.zeros(N),
+          "pz": np.zeros(N), "s1": np.full(N, xi[0]), "s2": np.full(N, xi[1]), "s3": np.full(N, xi[2]),
+          "theta": np.zeros(N), "w": np.ones(N), "id": np.arange(N, dtype=np.uint64)}
+    T = orc.nbw_rates(chig)
+    rate = alpha / (math.sqrt(3) * math.pi * xil * om) * (T[0] + xi[2] * T[1])
+    empty = {k: np.zeros(0) for k in ("x", "y", "z", "px", "py", "pz", "s1", "s2", "s3", "w")}
+    empty["id"] = np.zeros(0, dtype=np.uint64)
+    wl = {"e": empty, "pos": dict(empty), "ph": ph, "dt": 0.3 / rate, "seed": 17, "next_id": N,
+          "field": {"kind": "uniform", "E": (0, E0, 0), "B": (0, 0, -E0)}}
+    caps = {"cap_e": N, "cap_p": N, "cap_ph": N}
+    sim, osim, ost = _run_both(orc, ctx, wl, 1, q.QED_F_NBW | q.QED_F_VB, caps=caps)
+    c = sim.counters()
+    assert c["n_nbw"] == ost["n_nbw"] and 0.28 * N < c["n_nbw"] < 0.32 * N
+    assert sim.status() == 0
+    # every decision had T dt = 0.3 > 0.1: counted as a coarse step on both sides
+    assert c["n_coarse"] == ost["n_coarse"] == N
+    _compare_all(sim, osim, 1e-10, 1e-10)
+
+
 def test_uniform_field_grid_matches_analytic_gather(orc, ctx):
     """Config-3 style TSC gather: a uniform grid field reproduces the field exactly and
     the FP64 step matches the oracle on a small synthetic grid."""
@@ -243,42 +276,52 @@ def test_grid_gather_independent_of_particle_order(ctx, periodic):
 
 # ---------------------------------------------------------------------------------------
 def test_mixed_precision_short_run_per_particle(orc, ctx):
-    """Mixed path: per-particle 2e-5 against the FP64 oracle over a short run (particles
-    whose emission decision fell within 1e-6 of its threshold are excluded)."""
+    """Mixed path against the FP64 oracle over 200 steps of config 1 (NCS + T-BMT): every
+    electron within 2e-5 in momentum (relative), in each spin component and in position,
+    except electrons with a decision whose draw lay within the mixed-path bound of its
+    threshold at some step (their trajectories branch there); no other exception."""
     wl = workloads.c1(n=4000, seed=12)
-    wl["e"]["z"] = wl["e"]["z"] + 0.0
     sim = q.Simulation(wl, prec=q.QED_PREC_MIXED, ctx=ctx)
     osim = oracle.Sim(orc, wl)
+    orc.set_near_tol(parity_rules.LOG_TOL)
     steps = 200
-    sim.run(steps, q.QED_F_NCS | q.QED_F_SPIN)
-    osim.run(steps, q.QED_F_NCS | q.QED_F_SPIN)
-    ids, _, _ = orc.near_log()
+    try:
+        sim.run(steps, q.QED_F_NCS | q.QED_F_SPIN)
+        ost = osim.run(steps, q.QED_F_NCS | q.QED_F_SPIN)
+        margins = parity_rules.near_margins(orc)
+    finally:
+        orc.set_near_tol(parity_rules.NEAR_FP64)
+    assert ost["n_ncs_e"] > 1000
     gs, os_ = sim.state(), osim.state()
     ge, oe = _by_id(gs["e"]), _by_id(os_["e"])
     assert np.array_equal(ge["id"], oe["id"])
     pg = np.stack([ge["px"], ge["py"], ge["pz"]], 1)
     po = np.stack([oe["px"], oe["py"], oe["pz"]], 1)
-    rel = np.linalg.norm(pg - po, axis=1) / np.linalg.norm(po, axis=1)
-    bad = rel > 2e-5
-    # a mismatched emission decision changes a particle completely; those must be near-ties
-    frac = bad.mean()
-    assert frac < 0.01, f"{bad.sum()} particles beyond 2e-5 (near-ties logged: {len(ids)})"
-    ok = ~bad
-    sg = np.stack([ge["s1"], ge["s2"], ge["s3"]], 1)[ok]
-    so = np.stack([oe["s1"], oe["s2"], oe["s3"]], 1)[ok]
-    assert np.median(np.abs(sg - so).max(1)) < 2e-5
+    dp = np.linalg.norm(pg - po, axis=1) / np.linalg.norm(po, axis=1)
+    ds = np.abs(np.stack([ge[k] - oe[k] for k in ("s1", "s2", "s3")], 1)).max(1)
+    dx = np.abs(np.stack([(ge[k] - oe[k]) / (np.abs(oe[k]) + 1.0) for k in ("x", "y", "z")], 1)).max(1)
+    bad = (dp > 2e-5) | (ds > 2e-5) | (dx > 2e-5)
+    ex, unexplained, worst = parity_rules.exemptions(ge["id"][bad], margins, mixed=True)
+    print(f"mixed 200-step run: {len(ex)} of {len(dp)} electrons exempted (largest margin {worst:.2e}); "
+          f"max dp {dp[~bad].max():.2e}, ds {ds[~bad].max():.2e}, dx {dx[~bad].max():.2e}")
+    assert not unexplained, f"electrons beyond 2e-5 without a near-tie (id, margin): {unexplained[:10]}"
+    assert len(ex) <= 0.01 * len(dp)
 
 
 def _spectrum(ph, bins):
     om = np.sqrt(ph["px"] ** 2 + ph["py"] ** 2 + ph["pz"] ** 2)
     h, _ = np.histogram(om, bins=bins, weights=ph["w"])
     h3, _ = np.histogram(om, bins=bins, weights=ph["w"] * ph["s3"])
-    return h, h3
+    h33, _ = np.histogram(om, bins=bins, weights=ph["w"] * ph["s3"] ** 2)
+    return h, h3, h33
 
 
 def test_mixed_precision_spectra_within_3_sigma(orc, ctx):
-    """Mixed path vs FP64 oracle (independent seeds): photon spectrum, mean xi3 and
-    electron spin polarisation per bin agree within 3 sigma after the full crossing."""
+    """Mixed path vs FP64 oracle (independent seeds) after the full config-1 crossing:
+    photon counts per energy bin within 3 sigma (Poisson; at chi ~ 0.2 an emission takes a
+    small fraction of the electron's energy, so one electron's emissions are nearly
+    independent), and the mean xi3 of every bin with more than 200 photons within 3 sigma
+    of its standard error (sample variance of xi3 in the bin)."""
     n = 4000
     wl = workloads.c1(n=n, seed=14)
     sim = q.Simulation(wl, prec=q.QED_PREC_MIXED, ctx=ctx)
@@ -288,11 +331,85 @@ def test_mixed_precision_spectra_within_3_sigma(orc, ctx):
     osim.run(450, q.QED_F_NCS | q.QED_F_SPIN)
     g, o = sim.state()["ph"], osim.state()["ph"]
     bins = np.geomspace(1.0, 2000.0, 13)
-    hg, h3g = _spectrum(g, bins)
-    ho, h3o = _spectrum(o, bins)
-    sig = np.sqrt(hg + ho + 1e-9)
-    assert np.all(np.abs(hg - ho) <= 3.5 * sig + 2), (hg, ho)
+    hg, h3g, h33g = _spectrum(g, bins)
+    ho, h3o, h33o = _spectrum(o, bins)
+    m = (hg > 0) | (ho > 0)
+    pull = (hg - ho)[m] / np.sqrt(hg + ho)[m]
+    print("photon spectrum pulls", np.round(pull, 2))
+    assert np.all(np.abs(pull) <= 3.0), (hg, ho)
     m = (hg > 200) & (ho > 200)
     xg, xo = h3g[m] / hg[m], h3o[m] / ho[m]
-    err = np.sqrt(1.0 / hg[m] + 1.0 / ho[m])
-    assert np.all(np.abs(xg - xo) <= 3.5 * err)
+    var_g = (h33g[m] / hg[m] - xg ** 2) / hg[m]
+    var_o = (h33o[m] / ho[m] - xo ** 2) / ho[m]
+    pull3 = (xg - xo) / np.sqrt(var_g + var_o)
+    print("mean xi3 pulls", np.round(pull3, 2))
+    assert np.all(np.abs(pull3) <= 3.0)
+
+
+# ---------------------------------------------------------------------------------------
+# Focused-pulse workload with every process on: the observables of the paper's read-out
+# (Sec. IV: spectra, Stokes parameters in a detection basis after Eq. (rotation), pair
+# yield, mean positron spin), mixed GPU path against the oracle with independent seeds.
+N_BATCH, E_PER_BATCH, C2_STEPS = 10, 4000, 200
+SPEC_LO, SPEC_HI, SPEC_NX = 10.0, 3.0e4, 8
+
+
+def _observables(ph, pos, spec_fn):
+    """Per-run observables: photon weight per ln-energy bin, Stokes means in the detection
+    basis x (all photons), positron count and mean spin."""
+    sp = spec_fn(ph)
+    bins, tot = sp["bins"][0], sp["total"]
+    out = {"spec": bins[:, 0], "xi": tot[1:4] / tot[0], "n_ph": tot[0]}
+    out["pairs"] = float(len(pos["id"]))
+    s = np.stack([pos["s1"], pos["s2"], pos["s3"]], 1)
+    out["pos_S"] = s.mean(0) if len(s) else np.zeros(3)
+    return out
+
+
+def _batch_stats(runs):
+    """Mean and standard error of every observable over independent runs."""
+    out = {}
+    for k in runs[0]:
+        a = np.array([np.atleast_1d(r[k]) for r in runs], dtype=np.float64)
+        out[k] = (a.mean(0), a.std(0, ddof=1) / math.sqrt(len(runs)))
+    return out
+
+
+def test_mixed_focused_pulse_observables_within_3_sigma(orc, ctx):
+    """Config 2 through the focus (NCS + NBW + VB + T-BMT) on the mixed GPU path and on the
+    oracle, each as 10 independent runs of 4000 electrons (GPU seeds 100.., oracle seeds
+    200..): photon weight per ln-energy bin, the mean Stokes parameters xi1..3 of all photons
+    in the detection basis (x, y) (qed_diag on the GPU, the oracle's read-out on the CPU),
+    the number of pairs, and the mean positron spin.  The error of each observable is the
+    standard error over its runs (photons and pairs of one electron are correlated, so
+    Poisson errors would be too small); every pull within 3 sigma, with no added slack."""
+    spec = q.diag_spec(q.QED_DIAG_SPECTRUM, SPEC_NX, 1, SPEC_LO, SPEC_HI, ref=(1.0, 0.0, 0.0))
+    g_runs, o_runs = [], []
+    for b in range(N_BATCH):
+        wl = _c2_at_focus(E_PER_BATCH, seed=100 + b)
+        sim = q.Simulation(wl, prec=q.QED_PREC_MIXED, ctx=ctx)
+        sim.run(C2_STEPS, ALL)
+        assert sim.status() == 0
+        pos = sim.state()["pos"]
+        g_runs.append(_observables(None, pos, lambda _ph, s=sim: q.diag(s.ph, spec)))
+        sim.close()
+        wlo = _c2_at_focus(E_PER_BATCH, seed=200 + b)
+        osim = oracle.Sim(orc, wlo)
+        osim.run(C2_STEPS, ALL)
+        st = osim.state()
+        from oracle import diag as odiag
+        o_runs.append(_observables(st["ph"], st["pos"], lambda ph: odiag.diag(
+            ph, odiag.SPECTRUM, SPEC_NX, 1, SPEC_LO, SPEC_HI, ref=(1.0, 0.0, 0.0), photon=True)))
+    G, O = _batch_stats(g_runs), _batch_stats(o_runs)
+    checked = 0
+    for k in ("spec", "xi", "n_ph", "pairs", "pos_S"):
+        (mg, eg), (mo, eo) = G[k], O[k]
+        sig = np.sqrt(eg ** 2 + eo ** 2)
+        use = sig > 0
+        if k == "spec":   # bins with a few hundred photons per run
+            use &= (mg > 200) & (mo > 200)
+        pull = (mg - mo)[use] / sig[use]
+        print(k, "gpu", np.round(mg, 4), "oracle", np.round(mo, 4), "pulls", np.round(pull, 2))
+        assert np.all(np.abs(pull) <= 3.0), (k, mg, mo, sig)
+        checked += int(use.sum())
+    assert G["pairs"][0][0] > 100 and checked >= 12
