@@ -27,9 +27,11 @@ _lib = None
 F_NCS, F_NBW, F_VB, F_SPIN, F_NO_RECOIL, F_DROP_PHOTONS = 1, 2, 4, 8, 16, 32
 F_LL, F_MLL, F_MBMT = 128, 256, 512   # radiative pusher: LL, quantum-corrected LL, radiative T-BMT
 F_DEPOSIT = 1024                      # leptons deposit their current (Esirkepov)
+F_BREMS, F_BH = 2048, 4096            # bremsstrahlung, Bethe-Heitler pairs in matter
 FIELD_NONE, FIELD_UNIFORM, FIELD_PLANE, FIELD_GAUSS, FIELD_GRID2D = 0, 1, 2, 3, 4
 # the decisions of a step, in the near-tie log (qed_oracle.h OR_D_*)
-DECISIONS = ("ncs", "ncs_collapse", "ncs_comp", "ncs_spin", "ncs_stokes", "nbw", "nbw_comp", "nbw_spin")
+DECISIONS = ("ncs", "ncs_collapse", "ncs_comp", "ncs_spin", "ncs_stokes", "nbw", "nbw_comp", "nbw_spin",
+             "brems", "bh")
 
 
 def build(force: bool = False) -> str:
@@ -73,7 +75,13 @@ class Grid(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("n_ncs", C.c_uint64 * 2), ("n_nbw", C.c_uint64), ("n_range", C.c_uint64),
-                ("n_drop", C.c_uint64), ("n_near", C.c_uint64), ("n_coarse", C.c_uint64)]
+                ("n_drop", C.c_uint64), ("n_near", C.c_uint64), ("n_coarse", C.c_uint64),
+                ("n_brems", C.c_uint64 * 2), ("n_bh", C.c_uint64)]
+
+
+class Medium(C.Structure):
+    _fields_ = [("Z", C.c_int), ("n", C.c_double), ("k_min", C.c_double), ("axis", C.c_int),
+                ("lo", C.c_double), ("hi", C.c_double)]
 
 
 def lib():
@@ -116,6 +124,18 @@ def lib():
             L.or_fdtd_b.argtypes = [C.POINTER(Grid), d]
             L.or_fdtd_e.argtypes = [C.POINTER(Grid), d]
             L.or_charge_tsc.argtypes = [C.POINTER(Grid), d, d, pd, pd, pd, u64, pd]
+            L.or_set_medium.argtypes = [C.c_void_p, C.POINTER(Medium)]
+            L.or_screening.argtypes = [d, d, pd]
+            L.or_coulomb_f.argtypes = [C.c_int]
+            L.or_coulomb_f.restype = d
+            L.or_brems_D.argtypes = [C.c_int, d, d]
+            L.or_brems_D.restype = d
+            L.or_pair_D.argtypes = [C.c_int, d, d]
+            L.or_pair_D.restype = d
+            L.or_medium_sigma.argtypes = [C.c_void_p, C.c_int, d]
+            L.or_medium_sigma.restype = d
+            L.or_medium_sample.argtypes = [C.c_void_p, C.c_int, d, d]
+            L.or_medium_sample.restype = d
             L.or_table.argtypes = [C.c_void_p, C.c_int, C.POINTER(u64)]
             L.or_table.restype = pd
             _lib = L
@@ -217,7 +237,8 @@ class Oracle:
                        float(t), float(dt), int(seed), int(step), int(flags), C.byref(st))
         e.sync(); pos.sync(); ph.sync()
         return {"n_ncs_e": st.n_ncs[0], "n_ncs_p": st.n_ncs[1], "n_nbw": st.n_nbw,
-                "n_range": st.n_range, "n_drop": st.n_drop, "n_near": st.n_near, "n_coarse": st.n_coarse}
+                "n_range": st.n_range, "n_drop": st.n_drop, "n_near": st.n_near, "n_coarse": st.n_coarse,
+                "n_brems_e": st.n_brems[0], "n_brems_p": st.n_brems[1], "n_bh": st.n_bh}
 
     def set_threads(self, n: int) -> int:
         """Threads of the particle loops of a step (OpenMP); returns the count in effect."""
@@ -286,6 +307,21 @@ class Oracle:
                         _dp(vp), _dp(Sp), _dp(Sm), _dp(o))
         return o
 
+    def set_medium(self, medium):
+        """medium: dict(Z, n, k_min, axis, lo, hi) or None (Sec. III E matter)."""
+        if medium is None:
+            self.L.or_set_medium(self.ctx, None)
+            return
+        m = Medium(int(medium["Z"]), float(medium["n"]), float(medium["k_min"]), int(medium.get("axis", 2)),
+                   float(medium.get("lo", -1e300)), float(medium.get("hi", 1e300)))
+        self.L.or_set_medium(self.ctx, C.byref(m))
+
+    def medium_sigma(self, which, E):
+        return self.L.or_medium_sigma(self.ctx, int(which), float(E))
+
+    def medium_sample(self, which, E, r):
+        return self.L.or_medium_sample(self.ctx, int(which), float(E), float(r))
+
     def table(self, which):
         n = C.c_uint64()
         p = self.L.or_table(self.ctx, int(which), C.byref(n))
@@ -310,6 +346,24 @@ def besselk_scaled(x):
     o = np.zeros(3)
     lib().or_besselk_scaled(float(x), _dp(o))
     return o
+
+
+def screening(g, e):
+    o = np.zeros(4)
+    lib().or_screening(float(g), float(e), _dp(o))
+    return o
+
+
+def coulomb_f(Z):
+    return lib().or_coulomb_f(int(Z))
+
+
+def brems_D(Z, E, y):
+    return lib().or_brems_D(int(Z), float(E), float(y))
+
+
+def pair_D(Z, k, x):
+    return lib().or_pair_D(int(Z), float(k), float(x))
 
 
 def scorer_gi_prime(y):

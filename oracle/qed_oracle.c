@@ -48,6 +48,8 @@ static const double OR_AE = 1.15965218128e-3;       /* g/2 - 1 of the electron  
 static const double OR_CHI_MIN = 1e-4, OR_CHI_MAX = 1e3;     /* chi_e range        */
 static const double OR_CHIG_MIN = 1e-2, OR_CHIG_MAX = 1e3;   /* chi_gamma, NBW     */
 static const double OR_VB_MIN = 1e-3, OR_VB_MAX = 1e3;       /* chi_gamma, VB      */
+/* classical electron radius (CODATA 2018, 2.8179403262e-15 m) in units of 1/k0 = 1 um/(2 pi) */
+#define OR_R0N (2.8179403262e-9 * 2.0 * 3.14159265358979323846)
 
 /* ---- table grids (a specification both implementations follow) -------------- */
 #define NK 1024
@@ -69,6 +71,10 @@ static const double OR_VB_MIN = 1e-3, OR_VB_MAX = 1e3;       /* chi_gamma, VB   
 #define NV 1024
 #define V_LO (-6.907755278982137)
 #define V_HI (6.907755278982137)
+#define NMG 256                        /* medium tables: energy rows, ln E on [ln 2, ln 2e6] */
+#define MG_LO 0.69314718055994531    /* ln 2 */
+#define MG_HI 14.508657738524219     /* ln 2e6 */
+#define NMS 512                        /* medium tables: cumulative nodes in s on [0, 1]     */
 
 struct or_ctx {
   double kv[3][NK], kd[3][NK];                  /* scaled K13, K23, IntK13 + d/dlnx */
@@ -79,6 +85,9 @@ struct or_ctx {
   double mpar[NV], mperp[NV];                   /* VB M_par, M_perp               */
   double rr[4][NR];                             /* q, psi1/chi^3, psi2/chi^3, psi3/chi^3 */
   uint64_t next_id;
+  int has_medium;                               /* bremsstrahlung / pair tables present  */
+  or_medium med;
+  double mb[NMG][NMS], mp[NMG][NMS];            /* cumulative brems (y) and pair (x) cross-sections */
   double near_tol;                              /* log decisions with |r - thr| < near_tol thr */
   int threads;                                  /* particle-loop threads of or_step (OpenMP) */
   uint64_t nlog, logcap;
@@ -672,6 +681,7 @@ const double *or_table(const or_ctx *c, int which, uint64_t *len) {
     case 4: *len = 4 * NBX * NBT; return &c->by[0][0][0];
     case 5: *len = 2 * NV; return c->mpar;
     case 6: *len = 4 * NR; return &c->rr[0][0];
+    case 7: *len = 2 * NMG * NMS; return &c->mb[0][0];   /* mb then mp (contiguous) */
   }
   *len = 0;
   return NULL;
@@ -1006,6 +1016,160 @@ void or_nbw_G(const or_ctx *c, double delta, double omega, double chig, const do
 }
 
 /* ======================================================================= *
+ *  High-energy bremsstrahlung and Bethe-Heitler pair production in matter *
+ *  (Sec. III E).                                                           *
+ *  Differential cross-sections of Tsai (Rev. Mod. Phys. 46, 815 (1974)):   *
+ *    brems:  dsigma/dy = alpha r0^2 D_b / y, y = omega / E,                *
+ *      D_b = (4/3 - 4/3 y + y^2) A + (2/3)(1 - y) B          (the paper's  *
+ *      printed cross-section),                                             *
+ *    pairs:  dsigma/dx = alpha r0^2 D_p, x = E+ / k,                       *
+ *      D_p = (1 - 4/3 x(1-x)) A - (2/3) x(1-x) B   (the same amplitudes    *
+ *      with the pair's energies: E^2 + E'^2 - 2/3 E E' -> E+^2 + E-^2 +    *
+ *      2/3 E+ E-, the paper's "similar process"),                          *
+ *    A = Z^2 (phi1 - 4/3 ln Z - 4 f) + Z (psi1 - 8/3 ln Z),                *
+ *    B = Z^2 (phi1 - phi2) + Z (psi1 - psi2),                              *
+ *  with Tsai's screening functions phi1,2(gamma), psi1,2(eps) (his Eqs.    *
+ *  3.38-3.41, Thomas-Fermi atoms, Z >= 5), gamma = 100 m k/(E E' Z^1/3),   *
+ *  eps = 100 m k/(E E' Z^2/3), and the Coulomb correction f(Z).  D < 0,    *
+ *  where the fits leave their range (no screening, near the end points),   *
+ *  is taken as 0.                                                           *
+ *  Event per step (Sec. III E): P = 1 - exp(-n sigma(E) ds), ds = v dt;    *
+ *  energy fraction from r sigma(E) = sigma(y, E) (cumulative).  Tables     *
+ *  (a specification shared with the GPU path): rows at NMG energies, ln E  *
+ *  uniform on [ln 2, ln 2e6] (m c^2); each row the cumulative integral at  *
+ *  NMS nodes of s in [0, 1], s uniform in ln(v/(1-v)) from v_lo to v_hi    *
+ *  (brems v = y in [k_min/E, 1 - 1/E], pairs v = x in [1/k, 1 - 1/k]),     *
+ *  each node interval by 8-point Gauss-Legendre.                           *
+ * ======================================================================= */
+void or_screening(double g, double e, double out[4]) {
+  out[0] = 20.863 - 2.0 * log(1.0 + (0.55846 * g) * (0.55846 * g)) -
+           4.0 * (1.0 - 0.6 * exp(-0.9 * g) - 0.4 * exp(-1.5 * g));
+  out[1] = out[0] - (2.0 / 3.0) / (1.0 + 6.5 * g + 6.0 * g * g);
+  out[2] = 28.340 - 2.0 * log(1.0 + (3.621 * e) * (3.621 * e)) -
+           4.0 * (1.0 - 0.7 * exp(-8.0 * e) - 0.3 * exp(-29.2 * e));
+  out[3] = out[2] - (2.0 / 3.0) / (1.0 + 40.0 * e + 400.0 * e * e);
+}
+
+double or_coulomb_f(int Z) {
+  double a2 = (OR_ALPHA * Z) * (OR_ALPHA * Z);
+  return a2 * (1.0 / (1.0 + a2) + 0.20206 - 0.0369 * a2 + 0.0083 * a2 * a2 - 0.002 * a2 * a2 * a2);
+}
+
+/* A and B at screening argument d = m k/(E E') */
+static void or_med_AB(int Z, double d, double *A, double *B) {
+  double z13 = cbrt((double)Z), lz = log((double)Z), s[4];
+  or_screening(100.0 * d / z13, 100.0 * d / (z13 * z13), s);
+  double f = or_coulomb_f(Z), z2 = (double)Z * Z;
+  *A = z2 * (s[0] - 4.0 / 3.0 * lz - 4.0 * f) + Z * (s[2] - 8.0 / 3.0 * lz);
+  *B = z2 * (s[0] - s[1]) + Z * (s[2] - s[3]);
+}
+
+double or_brems_D(int Z, double E, double y) {
+  if (!(y > 0.0) || !(y < 1.0)) return 0.0;
+  double A, B;
+  or_med_AB(Z, y / (E * (1.0 - y)), &A, &B);
+  double D = (4.0 / 3.0 - 4.0 / 3.0 * y + y * y) * A + (2.0 / 3.0) * (1.0 - y) * B;
+  return D > 0.0 ? D : 0.0;
+}
+
+double or_pair_D(int Z, double k, double x) {
+  if (!(x > 0.0) || !(x < 1.0)) return 0.0;
+  double A, B, xx = x * (1.0 - x);
+  or_med_AB(Z, 1.0 / (k * xx), &A, &B);
+  double D = (1.0 - 4.0 / 3.0 * xx) * A - (2.0 / 3.0) * xx * B;
+  return D > 0.0 ? D : 0.0;
+}
+
+/* the variable of coordinate s of a row at energy E (which: 0 brems y, 1 pairs x) and the
+   Jacobian of the cross-section in s.  s is uniform in t = ln(v / (1 - v)) between the
+   end points v_lo and v_hi: logarithmic at both ends (y -> k_min/E, y -> 1 - 1/E;
+   x -> 1/k, x -> 1 - 1/k), where the braces vary fastest.  With dv = v (1 - v) dt:
+   brems D/y dy = D (1 - y) dt, pairs D dx = D x (1 - x) dt. */
+static double or_med_var(int which, double E, double kmin, double s, double *jac) {
+  double vlo = which == 0 ? kmin / E : 1.0 / E, vhi = 1.0 - 1.0 / E;
+  double tlo = log(vlo / (1.0 - vlo)), thi = log(vhi / (1.0 - vhi));
+  double t = tlo + s * (thi - tlo);
+  double v = 1.0 / (1.0 + exp(-t)), w = 1.0 / (1.0 + exp(t));   /* v and 1 - v */
+  *jac = (thi - tlo) * (which == 0 ? w : v * w);
+  return v;
+}
+
+/* cumulative table of one process: C[i][j] = integral over s in [0, s_j] */
+static void or_build_medium(int Z, double kmin, int which, double *C) {
+  double hE = (MG_HI - MG_LO) / (NMG - 1), hs = 1.0 / (NMS - 1);
+  for (int i = 0; i < NMG; ++i) {
+    double E = exp(MG_LO + i * hE);
+    double *row = C + (size_t)i * NMS;
+    row[0] = 0.0;
+    int open = which == 0 ? (kmin / E < 1.0 - 1.0 / E) : (E > 2.0);
+    for (int j = 1; j < NMS; ++j) {
+      double acc = 0.0;
+      if (open) {
+        for (int q = 0; q < 8; ++q) {
+          double s = (j - 1) * hs + 0.5 * hs * (GL8X[q] + 1.0), jac;
+          double v = or_med_var(which, E, kmin, s, &jac);
+          double D = which == 0 ? or_brems_D(Z, E, v) : or_pair_D(Z, E, v);
+          acc += GL8W[q] * D * jac;
+        }
+        acc *= 0.5 * hs;
+      }
+      row[j] = row[j - 1] + acc;
+    }
+  }
+}
+
+void or_set_medium(or_ctx *c, const or_medium *m) {
+  if (!m) { c->has_medium = 0; return; }
+  c->med = *m;
+  or_build_medium(m->Z, m->k_min, 0, &c->mb[0][0]);
+  or_build_medium(m->Z, m->k_min, 1, &c->mp[0][0]);
+  c->has_medium = 1;
+}
+
+/* row interpolation of a table at ln E: the total sigma(E) (returned) and, for r in [0,1),
+   the node coordinate s with (1-w) C_i(s) + w C_i+1(s) = r sigma(E) (piecewise linear) */
+static double or_med_lookup(const double *C, double lnE, double r, double *s_out, int *range) {
+  double t = (lnE - MG_LO) / ((MG_HI - MG_LO) / (NMG - 1));
+  if (t > NMG - 1) { t = NMG - 1; if (range) *range = 1; }
+  if (t < 0) return 0.0;
+  int i = (int)floor(t);
+  if (i > NMG - 2) i = NMG - 2;
+  double w = t - i;
+  const double *a = C + (size_t)i * NMS, *b = a + NMS;
+  double tot = (1.0 - w) * a[NMS - 1] + w * b[NMS - 1];
+  if (s_out && tot > 0.0) {
+    double target = r * tot;
+    int lo = 0, hi = NMS - 1;
+    while (hi - lo > 1) {
+      int mid = (lo + hi) / 2;
+      double cm = (1.0 - w) * a[mid] + w * b[mid];
+      if (cm <= target) lo = mid; else hi = mid;
+    }
+    double c0 = (1.0 - w) * a[lo] + w * b[lo], c1 = (1.0 - w) * a[lo + 1] + w * b[lo + 1];
+    double f = c1 > c0 ? (target - c0) / (c1 - c0) : 0.0;
+    *s_out = (lo + f) / (NMS - 1);
+  }
+  return tot;
+}
+
+double or_medium_sigma(const or_ctx *c, int which, double E) {
+  if (!c->has_medium || !(E > 0.0)) return 0.0;
+  return or_med_lookup(which == 0 ? &c->mb[0][0] : &c->mp[0][0], log(E), 0.0, NULL, NULL);
+}
+
+/* the sampled variable (y or x) for energy E and uniform r */
+double or_medium_sample(const or_ctx *c, int which, double E, double r) {
+  double s = 0.0, jac;
+  or_med_lookup(which == 0 ? &c->mb[0][0] : &c->mp[0][0], log(E), r, &s, NULL);
+  return or_med_var(which, E, c->med.k_min, s, &jac);
+}
+
+static int or_in_medium(const or_ctx *c, const double x[3]) {
+  double v = x[c->med.axis];
+  return v >= c->med.lo && v < c->med.hi;
+}
+
+/* ======================================================================= *
  *  Birth records                                                           *
  * ======================================================================= */
 typedef struct { double x[3], p[3], s[3], w; } or_lep_birth;
@@ -1160,6 +1324,36 @@ static int or_photon(or_ctx *c, or_particles *ph, uint64_t i, const or_fields *f
       }
     }
   }
+  /* Bethe-Heitler pair creation in matter (Sec. III E), if the photon did not decay by
+     NBW: P = 1 - exp(-n sigma(k) c dt), the positron's energy fraction x from the
+     cumulative cross-section; the pair moves along the photon, born at its x^n.  The
+     pair's spins are not resolved: S = 0, the unpolarised (mixed) state. */
+  if (!decayed && (flags & OR_F_BH) && c->has_medium && om > 2.0 && or_in_medium(c, x)) {
+    int range = 0;
+    double sig = or_med_lookup(&c->mp[0][0], log(om), 0.0, NULL, &range);
+    if (range && st) st->n_range++;
+    double P = -expm1(-c->med.n * OR_ALPHA * OR_R0N * OR_R0N * sig * dt);
+    double r[2];
+    or_uniforms(seed, ph->id[i], step, 6u, r);
+    or_note(c, ph->id[i], step, OR_D_BH, r[0], P, st);
+    if (P > 0.1 && st) st->n_coarse++;
+    if (r[0] < P) {
+      double xf = or_medium_sample(c, 1, om, r[1]);
+      double ep = xf * om;
+      if (ep < 1.0) ep = 1.0;
+      if (ep > om - 1.0) ep = om - 1.0;
+      double em = om - ep;
+      double pp = sqrt(ep * ep - 1.0), pm = sqrt(em * em - 1.0);
+      for (int q = 0; q < 3; ++q) {
+        bp->x[q] = x[q]; be->x[q] = x[q];
+        bp->p[q] = pp * n[q]; be->p[q] = pm * n[q];
+        bp->s[q] = 0.0; be->s[q] = 0.0;
+      }
+      bp->w = be->w = ph->w[i];
+      decayed = 1;
+      if (st) st->n_bh++;
+    }
+  }
   if (!decayed) {
     for (int q = 0; q < 3; ++q) x[q] += dt * n[q];
     ph->x[i] = x[0]; ph->y[i] = x[1]; ph->z[i] = x[2];
@@ -1288,7 +1482,7 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
   /* current of the move x^n -> x^{n+1} (Sec. II C), with v_z of the same p^{n+1/2} */
   if ((flags & OR_F_DEPOSIT) && f->kind == OR_FIELD_GRID2D && f->gJx)
     or_deposit(f, q * L->w[i], xo, x, pn[2] / g1, dt);
-  int emitted = 0;
+  int emitted = 0, ncs_event = 0;
   if (flags & OR_F_NCS) {
     double pmag = norm3(pn);
     if (pmag <= 0.0) pmag = 1e-300;   /* at rest: chi = 0 below, no QED */
@@ -1380,6 +1574,7 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
           }
         }
         if (st) st->n_ncs[species]++;
+        ncs_event = 1;
       } else {
         /* no emission: posterior mean spin (reading: W and f are u-integrated,
            f = -Wb zeta), then collapse with P(+) = (1 + |S|)/2 */
@@ -1391,6 +1586,45 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
         or_note(c, L->id[i], step, OR_D_NCS_COLLAPSE, r[1], 0.5 * (1.0 + m), st);
         for (int k = 0; k < 3; ++k) S[k] = sg * Sb[k] / m;
       }
+    }
+  }
+  /* Bremsstrahlung in matter (Sec. III E), if no NCS event this step (one event per
+     particle per step): P = 1 - exp(-n sigma(E) v dt) at the energy of p^{n+1/2} and the
+     position x^n; photon energy omega = y E from the cumulative cross-section, along p;
+     the lepton keeps its direction with energy E - omega (the nucleus takes the
+     momentum balance); the photon is unpolarised (xi = 0) and born at x^{n+1}; the
+     lepton spin is not changed (the process is not spin-resolved). */
+  if (!ncs_event && (flags & OR_F_BREMS) && c->has_medium && or_in_medium(c, xo)) {
+    int range = 0;
+    double pmag = norm3(pn);
+    double sig = or_med_lookup(&c->mb[0][0], log(g1), 0.0, NULL, &range);
+    if (range && st) st->n_range++;
+    double P = -expm1(-c->med.n * OR_ALPHA * OR_R0N * OR_R0N * sig * (pmag / g1) * dt);
+    double r[2];
+    or_uniforms(seed, L->id[i], step, 5u, r);
+    or_note(c, L->id[i], step, OR_D_BREMS, r[0], P, st);
+    if (P > 0.1 && st) st->n_coarse++;
+    if (r[0] < P && pmag > 0.0) {
+      double yv = or_medium_sample(c, 0, g1, r[1]);
+      double om = yv * g1;
+      double gf = g1 - om;
+      if (gf < 1.0) gf = 1.0;
+      double nv[3] = {pn[0] / pmag, pn[1] / pmag, pn[2] / pmag};
+      if (!(flags & OR_F_NO_RECOIL)) {
+        double pf = sqrt(gf * gf - 1.0);
+        for (int k = 0; k < 3; ++k) pn[k] = pf * nv[k];
+        if (!(flags & OR_F_DROP_PHOTONS)) {
+          for (int k = 0; k < 3; ++k) {
+            bph->x[k] = x[k];
+            bph->k[k] = om * nv[k];
+            bph->xi[k] = 0.0;
+          }
+          bph->th = 0.0;
+          bph->w = L->w[i];
+          emitted = 1;
+        }
+      }
+      if (st) st->n_brems[species]++;
     }
   }
   L->x[i] = x[0]; L->y[i] = x[1]; L->z[i] = x[2];
@@ -1449,6 +1683,7 @@ int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, con
       st->n_ncs[0] += ts[k].n_ncs[0]; st->n_ncs[1] += ts[k].n_ncs[1]; st->n_nbw += ts[k].n_nbw;
       st->n_range += ts[k].n_range; st->n_drop += ts[k].n_drop; st->n_near += ts[k].n_near;
       st->n_coarse += ts[k].n_coarse;
+      st->n_brems[0] += ts[k].n_brems[0]; st->n_brems[1] += ts[k].n_brems[1]; st->n_bh += ts[k].n_bh;
     }
   }
   free(ts);

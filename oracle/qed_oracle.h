@@ -32,6 +32,8 @@ extern "C" {
 #define OR_F_MLL      256u   /* quantum-corrected LL: q(chi) F_RR,classical (Sec. III A) */
 #define OR_F_MBMT     512u   /* radiative T-BMT (Eq. spin1); needs OR_F_SPIN        */
 #define OR_F_DEPOSIT 1024u   /* leptons deposit their current (Esirkepov, Sec. II C)  */
+#define OR_F_BREMS   2048u   /* bremsstrahlung of leptons in matter (Sec. III E)       */
+#define OR_F_BH      4096u   /* Bethe-Heitler pair creation by photons in matter (III E) */
 
 /* --- particle arrays (structure of arrays, caller-owned) -------------------- */
 typedef struct {
@@ -84,7 +86,20 @@ typedef struct {
   uint64_t n_drop;         /* births dropped for lack of capacity              */
   uint64_t n_near;         /* decisions within the near-tie tolerance (logged) */
   uint64_t n_coarse;       /* decisions with probability W dt or T dt above 0.1 */
+  uint64_t n_brems[2];     /* bremsstrahlung events of e-, e+                   */
+  uint64_t n_bh;           /* Bethe-Heitler pairs                               */
 } or_stats;
+
+/* Matter for bremsstrahlung and Bethe-Heitler pairs (Sec. III E): atoms of charge Z
+ * (Tsai's screening functions are for Z >= 5) at n atoms per normalised volume (k0^-3),
+ * filling the slab lo <= x[axis] < hi; photons below k_min (m c^2) are not produced. */
+typedef struct {
+  int Z;
+  double n;
+  double k_min;
+  int axis;
+  double lo, hi;
+} or_medium;
 
 /* kinds of the discrete decisions of a step (near-tie log) */
 enum { OR_D_NCS = 0,          /* emission: r < W dt (Sec. III C)                     */
@@ -94,7 +109,9 @@ enum { OR_D_NCS = 0,          /* emission: r < W dt (Sec. III C)                
        OR_D_NCS_STOKES = 4,   /* photon pure-state sign: r < (1 + |F|/F0)/2          */
        OR_D_NBW = 5,          /* pair creation: r < T dt (Sec. III D)                */
        OR_D_NBW_COMP = 6,     /* xi3' component of the energy mixture                */
-       OR_D_NBW_SPIN = 7 };   /* one of the three cumulative thresholds of the 4-way pick */
+       OR_D_NBW_SPIN = 7,     /* one of the three cumulative thresholds of the 4-way pick */
+       OR_D_BREMS = 8,        /* bremsstrahlung: r < 1 - exp(-n sigma v dt) (Sec. III E) */
+       OR_D_BH = 9 };         /* Bethe-Heitler pair: r < 1 - exp(-n sigma c dt)        */
 
 typedef struct or_ctx or_ctx;
 
@@ -135,6 +152,19 @@ double or_ncs_invcdf(const or_ctx *c, int comp, double chi, double t); /* ln u *
 void or_nbw_rates(const or_ctx *c, double chig, double out[2]);     /* T0, T3   */
 double or_nbw_invcdf(const or_ctx *c, int comp, double chig, double t); /* ln d */
 void or_vb_m(const or_ctx *c, double chig, double out[2]);          /* M_par, M_perp */
+/* matter (Sec. III E): set the medium (builds its tables; NULL removes it) */
+void or_set_medium(or_ctx *c, const or_medium *m);
+/* Tsai's screening functions phi1, phi2 (gamma), psi1, psi2 (eps); Coulomb correction */
+void or_screening(double g, double e, double out[4]);
+double or_coulomb_f(int Z);
+/* braces of the cross-sections: dsigma/dy = alpha r0^2 D_b / y (y = omega/E, E total
+   lepton energy), dsigma/dx = alpha r0^2 D_p (x = E+/k) */
+double or_brems_D(int Z, double E, double y);
+double or_pair_D(int Z, double k, double x);
+/* total cross-section (units alpha r0^2; which 0 brems above k_min, 1 pairs) at energy E
+   by the tables, and the sampled y or x for a uniform r */
+double or_medium_sigma(const or_ctx *c, int which, double E);
+double or_medium_sample(const or_ctx *c, int which, double E, double r);
 /* radiative pusher functions at chi (Sec. III A, B): out = {q, psi1, psi2, psi3} */
 void or_rr_funcs(const or_ctx *c, double chi, double out[4]);
 double or_scorer_gi_prime(double y);
@@ -148,7 +178,8 @@ void or_nbw_G(const or_ctx *c, double delta, double omega, double chig,
               const double ap[3], const double bp[3], const double vp[3],
               const double Sp[3], const double Sm[3], double G[4]);
 /* raw table access for pins: which = 0 K, 1 ncs rate, 2 ncs inv, 3 nbw rate,
-   4 nbw inv, 5 vb, 6 radiative pusher (q, psi1/chi^3, psi2/chi^3, psi3/chi^3) */
+   4 nbw inv, 5 vb, 6 radiative pusher (q, psi1/chi^3, psi2/chi^3, psi3/chi^3),
+   7 medium: brems cumulative [256][512] then pair cumulative [256][512] */
 const double *or_table(const or_ctx *c, int which, uint64_t *len);
 
 #ifdef __cplusplus
