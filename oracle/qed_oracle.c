@@ -1525,16 +1525,23 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
         double omr = 1.0 / (1.0 + u), rr = u / (1.0 + u);
         double om = rr * g1;
         /* emission spin: SQA from F0 as a linear function of S_f (Eq. F0);
-           P(+) = (1 + |g|/c0)/2 */
-        double F[4], Fm[4];
-        double e3[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+           P(+) = (1 + |g|/c0)/2.  F0 = c0 + g.S_f is affine in S_f; g_k is read off as
+           (F0(L e_k) - F0(-L e_k)) / 2L with L = 2^30, where c0 cancels exactly: with a
+           unit S_f the difference F0(e_k) - c0 would carry the rounding of c0, which for
+           an unpolarised lepton (S_i = 0, |g| ~ u c0) and a soft photon is ~1e-16/u of
+           |g| in the direction of the axis */
+        double F[4], Fp[4], Fm[4];
+        const double Lb = 1073741824.0;
         double mz[3] = {0, 0, 0};
         or_ncs_F(c, u, chi, n, a, S, mz, F);
         double c0 = F[0];
         double g[3];
         for (int k = 0; k < 3; ++k) {
-          or_ncs_F(c, u, chi, n, a, S, e3[k], Fm);
-          g[k] = Fm[0] - c0;
+          double ep[3] = {0, 0, 0}, em[3] = {0, 0, 0};
+          ep[k] = Lb; em[k] = -Lb;
+          or_ncs_F(c, u, chi, n, a, S, ep, Fp);
+          or_ncs_F(c, u, chi, n, a, S, em, Fm);
+          g[k] = (Fp[0] - Fm[0]) / (2.0 * Lb);
         }
         double gm2 = norm3(g);
         double Sf[3];
