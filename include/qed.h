@@ -93,6 +93,22 @@ typedef enum { QED_PREC_F64 = 0, QED_PREC_MIXED = 1 } qed_precision;
  * are not deposited.  Float atomics: the summation order, and so the last bits of J, vary
  * from run to run.  Single-ensemble steps only (qed_batch_create rejects it). */
 #define QED_F_DEPOSIT 1024u
+/* Matter (Sec. III E; needs a medium, qed_set_medium): direct Monte Carlo of
+ *   QED_F_BREMS: bremsstrahlung of e- and e+ inside the medium, if the lepton had no NCS
+ *                event in the step (one event per particle per step): P = 1 - exp(-n sigma(E)
+ *                v dt) at the energy of p^{n+1/2} and the position x^n; photon energy
+ *                omega = y E from the cumulative cross-section (r sigma(E) = sigma(y, E)),
+ *                along p, unpolarised (xi = 0), born at x^{n+1}; the lepton keeps its
+ *                direction with energy E - omega (the nucleus takes the momentum balance)
+ *                and its spin (the process is not spin-resolved);
+ *   QED_F_BH   : Bethe-Heitler pair creation by photons inside the medium that did not
+ *                decay by NBW: P = 1 - exp(-n sigma(k) c dt); positron energy x k from the
+ *                cumulative cross-section, electron k - x k, both along the photon, born at
+ *                its x^n with S = 0 (unpolarised).
+ * Cross-sections: Tsai's, with his screening functions for Z >= 5 (see qed_set_medium).
+ * Not with the radiative pusher flags; single-ensemble steps only. */
+#define QED_F_BREMS 2048u
+#define QED_F_BH 4096u
 
 /* Structure-of-arrays view of one species, caller-owned device memory.  Element i of
  * every array describes particle i.  Element types follow qed_precision (above):
@@ -171,6 +187,8 @@ typedef struct {
   uint64_t n_coarse;     /* decisions whose probability W dt (NCS) or T dt (NBW) exceeded
                             0.1: the step allows one event per particle, which is a coarse
                             description of such a step -- a smaller dt is advisable      */
+  uint64_t n_brems[2];   /* bremsstrahlung events of e-, e+ (QED_F_BREMS)         */
+  uint64_t n_bh;         /* Bethe-Heitler pairs (QED_F_BH)                        */
 } qed_step_stats;
 
 typedef struct qed_ctx qed_ctx;             /* tables, id counter, scratch, status   */
@@ -243,6 +261,36 @@ qed_status qed_get_next_id(qed_ctx *ctx, uint64_t *next_id, void *stream);
 qed_status qed_step(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed_particles *ph,
                     const qed_fields *f, double t, double dt, uint64_t seed, uint32_t step,
                     uint32_t flags, qed_step_stats *dev_stats, void *stream);
+
+/* Matter for QED_F_BREMS and QED_F_BH (paper Sec. III E, high-energy bremsstrahlung and
+ * the Bethe-Heitler pair creation that "follows a similar process"): atoms of charge Z at
+ * n atoms per normalised volume (1/k0^3; for a solid of density rho in g/cm^3 and molar
+ * mass A: n = rho N_A / A (1e-4 / 2 pi)^3), filling the slab lo <= x[axis] < hi (normalised
+ * units; axis 0, 1, 2 = x, y, z); photons below k_min (m c^2) are not produced.
+ * Cross-sections (Tsai, Rev. Mod. Phys. 46, 815 (1974), the paper's reference):
+ *   brems  dsigma/dy = alpha r0^2 / y [(4/3 - 4/3 y + y^2) A + (2/3)(1 - y) B], y = omega/E,
+ *   pairs  dsigma/dx = alpha r0^2 [(1 - 4/3 x(1-x)) A - (2/3) x(1-x) B], x = E+/k,
+ *   A = Z^2 (phi1 - 4/3 ln Z - 4 f) + Z (psi1 - 8/3 ln Z), B = Z^2 (phi1 - phi2) + Z (psi1 - psi2)
+ * with Tsai's screening functions phi1,2, psi1,2 for Thomas-Fermi atoms (valid for Z >= 5)
+ * and the Coulomb correction f(Z); where the fits leave their range (no screening near the
+ * end points, low energies) a negative brace counts as zero.  Builds the cumulative tables
+ * on the device (FP64; 256 energies from 1 to 1e6 MeV x 512 nodes uniform in the logit
+ * of the energy fraction) and keeps them on the context; syncs `stream`.  m NULL removes
+ * the medium.  Errors: QED_ERR_INVALID_ARG (Z outside [5, 100], n or k_min not positive,
+ * axis outside 0..2, lo >= hi), QED_ERR_NOT_INITIALIZED, QED_ERR_CUDA. */
+typedef struct {
+  int Z;
+  double n;
+  double k_min;
+  int axis;
+  double lo, hi;
+} qed_medium;
+qed_status qed_set_medium(qed_ctx *ctx, const qed_medium *m, void *stream);
+/* Diagnostics: the medium's FP64 tables to host memory (syncs): brems rows then pair rows,
+ * [2][256 energies][512 nodes], each row the cumulative cross-section (units alpha r0^2)
+ * from the low end of the energy fraction.  *len receives 2 * 256 * 512; host may be NULL
+ * to query it.  Errors: QED_ERR_INVALID_ARG (no medium set, cap too small). */
+qed_status qed_copy_medium_table(qed_ctx *ctx, double *host, uint64_t cap, uint64_t *len, void *stream);
 
 /* Field solver (Sec. II B): one half of the Yee leapfrog on a 2D3V grid (async).
  *   which = QED_FDTD_B: B -= dt curl E   (Faraday);

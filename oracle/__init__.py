@@ -405,6 +405,7 @@ class Sim:
         self.seed = int(wl["seed"])
         self.step_no = int(wl.get("step0", 0))
         orc.set_next_id(int(wl["next_id"]))
+        orc.set_medium(wl.get("medium"))
 
     def run(self, nsteps, flags):
         tot = {}

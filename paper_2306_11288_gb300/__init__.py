@@ -24,6 +24,7 @@ QED_F_NCS, QED_F_NBW, QED_F_VB, QED_F_SPIN, QED_F_NO_RECOIL, QED_F_DROP_PHOTONS 
 QED_F_MLP = 64
 QED_F_LL, QED_F_MLL, QED_F_MBMT = 128, 256, 512
 QED_F_DEPOSIT = 1024
+QED_F_BREMS, QED_F_BH = 2048, 4096
 QED_FDTD_B, QED_FDTD_E = 0, 1
 QED_STATUS_CAPACITY, QED_STATUS_TIMEOUT, QED_STATUS_TABLE_RANGE, QED_STATUS_LOG_FULL = 1, 2, 4, 8
 FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
@@ -35,7 +36,8 @@ ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particle
                  "qed_batch_step", "qed_batch_run", "qed_batch_clock", "qed_batch_get_config",
                  "qed_batch_set_config", "qed_batch_tune", "qed_batch_destroy", "qed_mlp_train",
                  "qed_mlp_set_params", "qed_mlp_get_params", "qed_mlp_eval", "qed_mlp_target", "qed_fdtd_advance",
-                 "qed_sort_cells", "qed_philox_blocks", "qed_last_error")
+                 "qed_sort_cells", "qed_philox_blocks", "qed_set_medium", "qed_copy_medium_table",
+                 "qed_last_error")
 MLP_PARAMS = 4481
 QED_DIAG_SPECTRUM, QED_DIAG_DETECTOR = 0, 1
 
@@ -63,7 +65,12 @@ class qed_grid2d(C.Structure):
 class qed_step_stats(C.Structure):
     _fields_ = [("n_ncs", C.c_uint64 * 2), ("n_nbw", C.c_uint64), ("n_range", C.c_uint64),
                 ("n_drop", C.c_uint64), ("n_steps", C.c_uint64), ("n_processed", C.c_uint64),
-                ("n_coarse", C.c_uint64)]
+                ("n_coarse", C.c_uint64), ("n_brems", C.c_uint64 * 2), ("n_bh", C.c_uint64)]
+
+
+class qed_medium(C.Structure):
+    _fields_ = [("Z", C.c_int), ("n", C.c_double), ("k_min", C.c_double), ("axis", C.c_int),
+                ("lo", C.c_double), ("hi", C.c_double)]
 
 
 class qed_diag_spec(C.Structure):
@@ -131,6 +138,8 @@ def lib():
         L.qed_mlp_target.argtypes = [vp, vp, vp, u64, vp]
         L.qed_fdtd_advance.argtypes = [C.POINTER(qed_grid2d), C.c_int, d, vp]
         L.qed_sort_cells.argtypes = [vp, vp, C.POINTER(qed_fields), vp]
+        L.qed_set_medium.argtypes = [vp, C.POINTER(qed_medium), vp]
+        L.qed_copy_medium_table.argtypes = [vp, C.POINTER(C.c_double), u64, C.POINTER(u64), vp]
         L.qed_last_error.restype = C.c_char_p
         for name in ABI_FUNCTIONS:
             if name != "qed_last_error":
@@ -474,6 +483,26 @@ def fields_from_spec(spec: dict, grid=None) -> qed_fields:
     return f
 
 
+def qed_set_medium(ctx, medium, stream=None):
+    """medium: dict(Z, n, k_min, axis, lo, hi) (Sec. III E matter) or None to remove it."""
+    if medium is None:
+        _check(lib().qed_set_medium(ctx, None, _stream(stream)), "qed_set_medium")
+        return
+    m = qed_medium(int(medium["Z"]), float(medium["n"]), float(medium["k_min"]), int(medium.get("axis", 2)),
+                   float(medium.get("lo", -1e300)), float(medium.get("hi", 1e300)))
+    _check(lib().qed_set_medium(ctx, C.byref(m), _stream(stream)), "qed_set_medium")
+
+
+def qed_copy_medium_table(ctx, stream=None):
+    import numpy as np
+    n = C.c_uint64()
+    _check(lib().qed_copy_medium_table(ctx, None, 0, C.byref(n), _stream(stream)), "qed_copy_medium_table")
+    out = np.zeros(n.value)
+    _check(lib().qed_copy_medium_table(ctx, out.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n),
+                                       _stream(stream)), "qed_copy_medium_table")
+    return out
+
+
 def qed_sort_cells(ctx, handle, grid: qed_fields, stream=None):
     _check(lib().qed_sort_cells(ctx, handle, C.byref(grid), _stream(stream)), "qed_sort_cells")
 
@@ -510,8 +539,10 @@ class Simulation:
         self.t = float(wl.get("t0", 0.0))
         self.seed = int(wl["seed"])
         self.step_no = int(wl.get("step0", 0))
-        self.stats = torch.zeros(8, dtype=torch.int64, device="cuda")
+        self.stats = torch.zeros(11, dtype=torch.int64, device="cuda")
         qed_set_next_id(self.ctx, int(wl["next_id"]))
+        if wl.get("medium") is not None:
+            qed_set_medium(self.ctx, wl["medium"])
         qed_read_status(self.ctx, clear=True)
 
     def run(self, nsteps, flags, stream=None):
@@ -529,7 +560,8 @@ class Simulation:
     def counters(self) -> dict:
         s = self.stats.cpu().numpy()
         return {"n_ncs_e": int(s[0]), "n_ncs_p": int(s[1]), "n_nbw": int(s[2]), "n_range": int(s[3]),
-                "n_drop": int(s[4]), "n_steps": int(s[5]), "n_processed": int(s[6]), "n_coarse": int(s[7])}
+                "n_drop": int(s[4]), "n_steps": int(s[5]), "n_processed": int(s[6]), "n_coarse": int(s[7]),
+                "n_brems_e": int(s[8]), "n_brems_p": int(s[9]), "n_bh": int(s[10])}
 
     def status(self, clear=False) -> int:
         return qed_read_status(self.ctx, clear)

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqed_gb300.so")
-SOURCES = ["qed_api.cu", "qed_tables.cu", "qed_step.cu", "qed_static.cu", "qed_diag.cu", "qed_batch.cu", "qed_mlp.cu", "qed_fdtd.cu", "qed_sort.cu"]
+SOURCES = ["qed_api.cu", "qed_tables.cu", "qed_step.cu", "qed_static.cu", "qed_diag.cu", "qed_batch.cu", "qed_mlp.cu",
+           "qed_fdtd.cu", "qed_sort.cu", "qed_medium.cu"]
 HEADERS = ["qed_common.cuh", "qed_internal.h", "qed_kernels.cuh", "qed_mlp.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

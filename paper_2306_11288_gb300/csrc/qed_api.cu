@@ -133,6 +133,7 @@ extern "C" qed_status qed_destroy(qed_ctx* c) {
     if (c->tev[k]) cudaEventDestroy(c->tev[k]);
   if (c->diag_buf) cudaFree(c->diag_buf);
   if (c->sort_buf) cudaFree(c->sort_buf);
+  if (c->med_buf) cudaFree(c->med_buf);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
   if (c->side) cudaStreamDestroy(c->side);
@@ -301,6 +302,18 @@ void philox_key_schedule(uint64_t seed, unsigned int rk[20]) {
   }
 }
 
+void set_medium_args(StepArgs& a, const qed_ctx* c) {
+  if (!c->has_medium) return;
+  const double* C = static_cast<const double*>(c->med_buf);
+  a.med_c = C;
+  a.med_tot = reinterpret_cast<const float*>(C + 2 * (size_t)kNmg * kNms);
+  a.med_nar2 = c->med.n * kAlpha * kR0n * kR0n;
+  a.med_lo = c->med.lo;
+  a.med_hi = c->med.hi;
+  a.med_kmin = c->med.k_min;
+  a.med_axis = c->med.axis;
+}
+
 void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos, const qed_particles* ph,
                    const qed_fields* f, double t, uint64_t seed, uint32_t step, DevState* st,
                    qed_step_stats* stats) {
@@ -351,6 +364,8 @@ qed_status check_flag_bits(uint32_t flags, const char* who) {
     FAIL(QED_ERR_INVALID_ARG, "%s: the radiative pusher (LL, MLL, MBMT) and the NCS Monte Carlo count the same "
          "radiation: choose one", who);
   if ((flags & QED_F_LL) && (flags & QED_F_MLL)) FAIL(QED_ERR_INVALID_ARG, "%s: QED_F_LL and QED_F_MLL exclude each other", who);
+  if ((flags & (QED_F_BREMS | QED_F_BH)) && (flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT)))
+    FAIL(QED_ERR_INVALID_ARG, "%s: the matter processes run with the Monte Carlo step, not with the radiative pusher", who);
   return QED_OK;
 }
 
@@ -431,6 +446,9 @@ static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos
   if (r_ != QED_OK) return r_;
   r_ = check_deposit(flags, f, "qed_step");
   if (r_ != QED_OK) return r_;
+  if ((flags & (QED_F_BREMS | QED_F_BH)) && !c->has_medium)
+    FAIL(QED_ERR_INVALID_ARG, "qed_step: QED_F_BREMS / QED_F_BH need a medium (qed_set_medium)");
+  if ((flags & QED_F_BH) && (!e || !pos)) FAIL(QED_ERR_INVALID_ARG, "qed_step: Bethe-Heitler pairs need e- and e+ sets");
   const unsigned long long tp = ph ? tiles_of(ph->cap) : 0;
   const unsigned long long tl = (e ? tiles_of(e->cap) : 0) + (pos ? tiles_of(pos->cap) : 0);
   if (tp > c->tile_cap[0] || tl > c->tile_cap[1] || !c->rec[0] || !c->rec[1])
@@ -461,6 +479,7 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
     a.rec_cap[k] = c->rec_cap[k];
   }
   a.holes = c->holes;
+  set_medium_args(a, c);
   const int pi = prec == QED_PREC_F64 ? 0 : 1;
   // per-kernel timing runs the passes one after the other, so that each duration is the
   // kernel's own (no overlap of the lepton pass with the photon chain)

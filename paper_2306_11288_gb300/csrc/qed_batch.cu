@@ -213,6 +213,8 @@ extern "C" qed_status qed_batch_create(qed_ctx* ctx, const qed_ensemble* ens, in
     const qed_status rf = check_flag_bits(flags, "qed_batch_create");
     if (rf != QED_OK) return rf;
     if (flags & QED_F_DEPOSIT) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: current deposition is for single steps");
+    if (flags & (QED_F_BREMS | QED_F_BH))
+      BFAIL(QED_ERR_INVALID_ARG, "qed_batch_create: the matter processes are for single steps");
   }
   int prec = -1;
   unsigned long long tp = 1, tl = 1, cap_ph = 0, cap_l = 0;

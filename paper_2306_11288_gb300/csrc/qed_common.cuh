@@ -15,6 +15,15 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 2.0 * kPi;
 constexpr double kAlpha = 7.2973525693e-3;
 constexpr double kXiL = 2.42631023867e-6;     // hbar omega0 / (m c^2)
+// classical electron radius (CODATA 2018, 2.8179403262e-15 m) in units of 1/k0 = 1 um / (2 pi)
+constexpr double kR0n = 2.8179403262e-9 * 6.283185307179586477;
+// medium tables (bremsstrahlung, Bethe-Heitler pairs): kNmg rows at ln E uniform on
+// [ln 2, ln 2e6], kNms cumulative nodes per row; then the row totals as floats
+constexpr int kNmg = 256;
+constexpr int kNms = 512;
+constexpr double kMgLo = 0.69314718055994531;    // ln 2
+constexpr double kMgHi = 14.508657738524219;     // ln 2e6
+constexpr size_t kMedBytes = 2 * (size_t)kNmg * kNms * sizeof(double) + 2 * kNmg * sizeof(float);
 constexpr double kAe = 1.15965218128e-3;      // g/2 - 1
 constexpr double kChiMin = 1e-4, kChiMax = 1e3;
 constexpr double kChigMin = 1e-2, kChigMax = 1e3;
@@ -292,7 +301,8 @@ struct DevState {
   unsigned long long n_nbw;          // this step: pairs created (ranked decays)
   unsigned long long n_ncs_tot;      // this step: ranked emissions
   unsigned long long cursor[2];      // this step: entries written to the NBW / NCS logs
-  unsigned long long ev[6];          // this step: ncs_e, ncs_p, coarse (P > 0.1), range, drop, spare
+  unsigned long long ev[8];          // this step: ncs_e, ncs_p, coarse (P > 0.1), range, drop, brems e-,
+                                     // brems e+, Bethe-Heitler pairs
   unsigned int done;                 // finished-block counter of the last kernel
   unsigned int epoch;                // stamp of this step's log entries
   unsigned int status;               // QED_STATUS_* bits (sticky)

@@ -85,6 +85,12 @@ struct StepArgs {
   void* rec[2];                      // event logs: NBW decays, NCS emissions
   unsigned long long rec_cap[2];
   unsigned int* holes;               // ranked slots of decayed photons
+  // matter (QED_F_BREMS, QED_F_BH): cumulative tables (brems rows, then pair rows), the
+  // row totals as floats, n alpha r0^2, the slab, k_min
+  const double* med_c;
+  const float* med_tot;
+  double med_nar2, med_lo, med_hi, med_kmin;
+  int med_axis;
 };
 
 // side stream and events of one step.  side == nullptr runs everything on the caller's
@@ -116,9 +122,11 @@ struct qed_ctx;
 namespace qedk {
 // QED_F_MLP needs the mixed path and trained (or set) sampler parameters
 // every flag bit the step kernels know; validation of flag combinations
-constexpr uint32_t kAllFlags = 2047u;
+constexpr uint32_t kAllFlags = 8191u;
 qed_status check_flag_bits(uint32_t flags, const char* who);
 qed_status check_mlp_flag(const qed_ctx* c, uint32_t flags, qed_precision prec, const char* who);
+// the step's medium arguments from the context (nothing if it has no medium)
+void set_medium_args(StepArgs& a, const qed_ctx* c);
 // occupancy-derived persistent grid sizes
 qed_status step_grid_sizes(qed_precision prec, int* nblk);
 size_t nbw_rec_bytes(qed_precision p);
@@ -157,6 +165,9 @@ struct qed_ctx {
   size_t diag_bytes;
   void* sort_buf;                     // qed_sort_cells scratch (keys, indices, one array)
   size_t sort_bytes;
+  void* med_buf;                      // medium tables (qed_set_medium)
+  qed_medium med;
+  int has_medium;
 };
 
 struct qed_particles {

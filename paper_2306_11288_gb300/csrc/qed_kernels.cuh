@@ -588,6 +588,9 @@ __device__ __forceinline__ void count_event(unsigned long long* ctr, bool flag) 
 }
 
 // ---- event logs ------------------------------------------------------------------------
+// bit 31 of NbwRec::ens / NcsRec::species: the event is a matter process (a Bethe-Heitler
+// decay / a bremsstrahlung emission) rather than NBW / NCS; the rank space is shared
+constexpr unsigned int kEvMedium = 0x80000000u;
 template <typename R>
 struct NbwRec {
   unsigned long long i;      // photon slot
@@ -661,6 +664,75 @@ template <typename R> struct OccPh { static constexpr int v = sizeof(R) == 4 ? 3
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// ---- matter (Sec. III E): bremsstrahlung and Bethe-Heitler pairs ----------------------
+// Tables of the medium (qed_medium.cu): brems rows then pair rows, kNmg x kNms cumulative
+// cross-sections (units alpha r0^2), then the row totals as floats.
+__device__ __forceinline__ bool in_medium(const StepArgs& a, double x, double y, double z) {
+  const double v = a.med_axis == 0 ? x : (a.med_axis == 1 ? y : z);
+  return v >= a.med_lo && v < a.med_hi;
+}
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+// total cross-section of process `which` (0 brems, 1 pairs) at ln E: linear in ln E between
+// the rows (FP64 path: the FP64 totals; mixed path: their float copies); zero below the
+// first row, clamped (and counted) above the last
+template <typename R>
+__device__ __forceinline__ R med_sigma(const StepArgs& a, int which, R lnE, bool& range) {
+  R t = (lnE - R(kMgLo)) * R((kNmg - 1) / (kMgHi - kMgLo));
+  if (!(t >= R(0))) return R(0);
+  if (t > R(kNmg - 1)) {
+    t = R(kNmg - 1);
+    range = true;
+  }
+  int i = (int)t;
+  i = i > kNmg - 2 ? kNmg - 2 : i;
+  const R w = t - R(i);
+  R s0, s1;
+  if constexpr (sizeof(R) == 8) {
+    const double* C = a.med_c + (size_t)which * kNmg * kNms;
+    s0 = C[(size_t)i * kNms + kNms - 1];
+    s1 = C[(size_t)(i + 1) * kNms + kNms - 1];
+  } else {
+    const float* T = a.med_tot + which * kNmg;
+    s0 = __ldg(T + i);
+    s1 = __ldg(T + i + 1);
+  }
+  return (R(1) - w) * s0 + w * s1;
+}
+// The energy fraction (brems y, pairs x) at energy E for a uniform r (FP64 on both paths):
+// rows i, i+1 around ln E mixed linearly, the node interval whose cumulative brackets
+// r sigma(E), linear inside it; s -> the fraction uniform in ln(v/(1-v)) between the end
+// points at E (brems [k_min/E, 1 - 1/E], pairs [1/E, 1 - 1/E]).
+static __device__ __noinline__ double med_sample(const StepArgs& a, int which, double E, double r) {
+  const double* C = a.med_c + (size_t)which * kNmg * kNms;
+  double t = (log(E) - kMgLo) / ((kMgHi - kMgLo) / (kNmg - 1));
+  double s = 0.0;
+  if (t >= 0.0) {
+    if (t > kNmg - 1) t = kNmg - 1;
+    int i = (int)floor(t);
+    i = i > kNmg - 2 ? kNmg - 2 : i;
+    const double w = t - i;
+    const double* A = C + (size_t)i * kNms;
+    const double* B = A + kNms;
+    const double tot = (1.0 - w) * A[kNms - 1] + w * B[kNms - 1];
+    if (tot > 0.0) {
+      const double target = r * tot;
+      int lo = 0, hi = kNms - 1;
+      while (hi - lo > 1) {
+        const int m = (lo + hi) / 2;
+        const double cm = (1.0 - w) * A[m] + w * B[m];
+        if (cm <= target) lo = m; else hi = m;
+      }
+      const double c0 = (1.0 - w) * A[lo] + w * B[lo], c1 = (1.0 - w) * A[lo + 1] + w * B[lo + 1];
+      const double f = c1 > c0 ? (target - c0) / (c1 - c0) : 0.0;
+      s = (lo + f) / (kNms - 1);
+    }
+  }
+  const double vlo = which == 0 ? a.med_kmin / E : 1.0 / E, vhi = 1.0 - 1.0 / E;
+  const double tlo = log(vlo / (1.0 - vlo)), thi = log(vhi / (1.0 - vhi));
+  return 1.0 / (1.0 + exp(-(tlo + s * (thi - tlo))));
+}
+
 // ======================================================================================
 // photon streaming pass
 // ======================================================================================
@@ -713,7 +785,7 @@ __device__ __forceinline__ PhTile ph_tile(const StepArgs& a, const unsigned int*
   return t;
 }
 
-template <typename R, bool kB, bool kSm>
+template <typename R, bool kB, bool kSm, bool kMed = false>
 __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(const __grid_constant__ StepArgs a) {
   // single-ensemble launches double-buffer the records in registers; batched launches
   // (whose tile-to-ensemble search needs the registers) load each tile at its top
@@ -828,6 +900,22 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
         }
       }
     }
+    bool bh = false;
+    if constexpr (kMed) {
+      // Bethe-Heitler pair creation in the medium, if the photon did not decay by NBW:
+      // P = 1 - exp(-n sigma(k) c dt) (Sec. III E)
+      if (live && !decay && (a.flags & QED_F_BH) && om > R(2) && in_medium(a, x, y, z)) {
+        const R sig = med_sigma<R>(a, 1, f_log(om), range);
+        const R Pb = -m_expm1(-R(a.med_nar2) * sig * dt);
+        const URand<R> u = urand<R, !kB>(E, id, tm.step, 6u);
+        if (Pb > R(0.1)) atomicAdd(&st->ev[2], 1ull);
+        if (u.u0 < Pb) {
+          decay = true;
+          bh = true;
+          rmix = u.u1;   // the pair's energy split
+        }
+      }
+    }
     if (live) {
       stv<R>(P.s1, i, xi.x); stv<R>(P.s2, i, xi.y); stv<R>(P.s3, i, xi.z);
       stv<R>(P.theta, i, th);
@@ -839,7 +927,8 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
                                              &gst->status, s_tile, &r_in);
     if (slot != ~0ull) {
       NbwRec<R> rec;
-      rec.i = i; rec.tile = tile; rec.r_in = r_in; rec.stamp = epoch; rec.ens = (unsigned int)ens;
+      rec.i = i; rec.tile = tile; rec.r_in = r_in; rec.stamp = epoch;
+      rec.ens = (unsigned int)ens | (bh ? kEvMedium : 0u);   // bit 31: a Bethe-Heitler decay
       rec.x = x; rec.y = y; rec.z = z;
       rec.chig = chig; rec.rmix = rmix; rec.p1x = P1.x; rec.p1y = P1.y; rec.p1z = P1.z;
       evlog[slot] = rec;
@@ -1047,7 +1136,7 @@ __device__ __forceinline__ void deposit_tile(const qed_fields& f, const DepMove<
 // ======================================================================================
 // lepton streaming pass
 // ======================================================================================
-template <typename R, bool kB, bool kSm, bool kRad = false, bool kDep = false>
+template <typename R, bool kB, bool kSm, bool kRad = false, bool kDep = false, bool kMed = false>
 __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::v)
     k_lepton(const __grid_constant__ StepArgs a) {
   __shared__ __align__(16) R s_rates[kSm ? SmemTab<R, false>::n : 1];
@@ -1098,6 +1187,8 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
     if (live) {
       x = L.x[i]; y = L.y[i]; z = L.z[i];
     }
+    bool brems = false, in_med = false;
+    if constexpr (kMed) in_med = live && in_medium(a, x, y, z);   // at x^n
     if (live) {
       V3<R> p = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
       V3<R> S = mk<R>(ld<R>(L.s1, i), ld<R>(L.s2, i), ld<R>(L.s3, i));
@@ -1213,12 +1304,28 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
           }
         }
       }
+      if constexpr (kMed) {
+        // bremsstrahlung in the medium, if no NCS event: P = 1 - exp(-n sigma(E) v dt) at the
+        // energy of p^{n+1/2} (Sec. III E)
+        const R pm2b = dot(pn, pn);
+        if (!emit && in_med && (a.flags & QED_F_BREMS) && pm2b > R(0)) {
+          const R sig = med_sigma<R>(a, 0, f_log(g1), range);
+          const R Pb = -m_expm1(-R(a.med_nar2) * sig * (pm2b * f_rsqrt(pm2b)) * inv_g1 * dt);
+          const URand<R> u = urand<R, !kB>(E, id, tm.step, 5u);
+          if (Pb > R(0.1)) atomicAdd(&st->ev[2], 1ull);
+          if (u.u0 < Pb) {
+            emit = true;
+            brems = true;
+          }
+        }
+      }
       L.x[i] = x; L.y[i] = y; L.z[i] = z;
       stv<R>(L.px, i, pn.x); stv<R>(L.py, i, pn.y); stv<R>(L.pz, i, pn.z);
       stv<R>(L.s1, i, S.x); stv<R>(L.s2, i, S.y); stv<R>(L.s3, i, S.z);
     }
     if constexpr (kDep) deposit_tile<R>(E.f, dm, s_dep);
-    count_event(&st->ev[sp_idx], emit);
+    count_event(&st->ev[sp_idx], emit && !brems);
+    if constexpr (kMed) count_event(&st->ev[5 + sp_idx], brems);
     count_event(&st->ev[3], range);
     unsigned int r_in;
     const unsigned long long slot = tile_log(emit, tile, a.tile_cnt[1], &gst->cursor[1], a.rec_cap[1],
@@ -1226,7 +1333,7 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
     if (slot != ~0ull) {
       NcsRec<R> rec;
       rec.i = i; rec.tile = tile; rec.r_in = r_in; rec.stamp = epoch;
-      rec.species = (unsigned int)sp_idx | ((unsigned int)ens << 1);
+      rec.species = (unsigned int)sp_idx | ((unsigned int)ens << 1) | (brems ? kEvMedium : 0u);   // bit 31: brems
       rec.chi = chi; rec.ax = av.x; rec.ay = av.y; rec.az = av.z;
       evlog[slot] = rec;
     }
@@ -1450,6 +1557,89 @@ __device__ __noinline__ void nbw_event(const NbwRec<R>& rec, const EnsArgs& E, c
   }
 }
 
+// ---- matter events (Sec. III E) ------------------------------------------------------
+// A Bethe-Heitler decay: the positron takes x k (x from the cumulative cross-section with
+// the uniform carried in rec.rmix), the electron k - x k (each at least m c^2), both along
+// the photon, born at its x^n with S = 0 (unpolarised) and the photon's weight.
+template <typename R>
+__device__ __noinline__ void bh_event(const StepArgs& a, const NbwRec<R>& rec, const EnsArgs& E, unsigned long long rank,
+                                      DevState* gst) {
+  DevState* st = E.st;
+  const SpeciesArgs& P = E.sp[2];
+  const unsigned long long ne0 = st->n_live[0], np0 = st->n_live[1], id0 = st->next_id;
+  const unsigned long long i = rec.i;
+  const double kx = (double)ld<R>(P.px, i), ky = (double)ld<R>(P.py, i), kz = (double)ld<R>(P.pz, i);
+  const R wgt = ld<R>(P.w, i);
+  const double om = sqrt(kx * kx + ky * ky + kz * kz);
+  const double nx = kx / om, ny = ky / om, nz = kz / om;
+  const double xf = med_sample(a, 1, om, (double)rec.rmix);
+  double ep = xf * om;
+  ep = ep < 1.0 ? 1.0 : ep;
+  ep = ep > om - 1.0 ? om - 1.0 : ep;
+  const double em = om - ep;
+  const double pmag[2] = {sqrt(em * em - 1.0), sqrt(ep * ep - 1.0)};   // e-, e+
+  const unsigned long long base[2] = {ne0, np0};
+  atomicAdd(&st->ev[7], 1ull);
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    const SpeciesArgs& L = E.sp[sp];
+    const unsigned long long j = base[sp] + rank;
+    if (!L.present || j >= L.cap) {
+      atomicOr(&gst->status, QED_STATUS_CAPACITY);
+      atomicAdd(&st->ev[4], 1ull);
+      continue;
+    }
+    L.x[j] = rec.x; L.y[j] = rec.y; L.z[j] = rec.z;
+    stv<R>(L.px, j, (R)(pmag[sp] * nx)); stv<R>(L.py, j, (R)(pmag[sp] * ny)); stv<R>(L.pz, j, (R)(pmag[sp] * nz));
+    stv<R>(L.s1, j, R(0)); stv<R>(L.s2, j, R(0)); stv<R>(L.s3, j, R(0));
+    stv<R>(L.w, j, wgt);
+    L.id[j] = id0 + 2ull * rank + (unsigned long long)sp;
+  }
+}
+
+// A bremsstrahlung emission: omega = y E (y from the cumulative cross-section with the
+// second uniform of the decision's draw), along p; the lepton keeps its direction with
+// energy E - omega and its spin; the photon is unpolarised (xi = 0, basis angle 0), born
+// at the lepton's x^{n+1}.
+template <typename R>
+__device__ __noinline__ void brems_event(const StepArgs& a, const NcsRec<R>& rec, const EnsArgs& E, unsigned int step,
+                                         unsigned long long rank, bool births, unsigned int flags, DevState* gst) {
+  DevState* st = E.st;
+  const SpeciesArgs& G = E.sp[2];
+  const SpeciesArgs& L = E.sp[rec.species & 1u];
+  const unsigned long long nsurv = st->n_surv;
+  const unsigned long long id0 = st->next_id + 2ull * st->n_nbw;
+  const unsigned long long i = rec.i;
+  const double px = (double)ld<R>(L.px, i), py = (double)ld<R>(L.py, i), pz = (double)ld<R>(L.pz, i);
+  const double pmag = sqrt(px * px + py * py + pz * pz);
+  if (!(pmag > 0.0)) return;
+  const double g1 = sqrt(1.0 + px * px + py * py + pz * pz);
+  const Uni2 u = uniforms(E.seed, L.id[i], step, 5u);
+  const double yv = med_sample(a, 0, g1, u.u1);
+  const double om = yv * g1;
+  double gf = g1 - om;
+  gf = gf < 1.0 ? 1.0 : gf;
+  const double nx = px / pmag, ny = py / pmag, nz = pz / pmag;
+  if (!(flags & QED_F_NO_RECOIL)) {
+    const double pf = sqrt(gf * gf - 1.0);
+    stv<R>(L.px, i, (R)(pf * nx)); stv<R>(L.py, i, (R)(pf * ny)); stv<R>(L.pz, i, (R)(pf * nz));
+  }
+  if (births) {
+    const unsigned long long j = nsurv + rank;
+    if (!G.present || j >= G.cap) {
+      atomicOr(&gst->status, QED_STATUS_CAPACITY);
+      atomicAdd(&st->ev[4], 1ull);
+    } else {
+      G.x[j] = L.x[i]; G.y[j] = L.y[i]; G.z[j] = L.z[i];
+      stv<R>(G.px, j, (R)(om * nx)); stv<R>(G.py, j, (R)(om * ny)); stv<R>(G.pz, j, (R)(om * nz));
+      stv<R>(G.s1, j, R(0)); stv<R>(G.s2, j, R(0)); stv<R>(G.s3, j, R(0));
+      stv<R>(G.theta, j, R(0));
+      stv<R>(G.w, j, ld<R>(L.w, i));
+      G.id[j] = id0 + rank;
+    }
+  }
+}
+
 template <typename R, bool kB>
 __global__ void __launch_bounds__(kTile) k_nbw_ev(const __grid_constant__ StepArgs a) {
   pdl_wait();
@@ -1463,13 +1653,15 @@ __global__ void __launch_bounds__(kTile) k_nbw_ev(const __grid_constant__ StepAr
        kk += (unsigned long long)gridDim.x * blockDim.x) {
     const NbwRec<R> rec = evlog[kk];
     if (rec.stamp != epoch || a.tile_cnt[0][rec.tile] == 0) continue;
-    const EnsArgs& E = ens_of<kB>(a, kB ? (int)rec.ens : 0);
+    const unsigned int ens = rec.ens & ~kEvMedium;
+    const EnsArgs& E = ens_of<kB>(a, kB ? (int)ens : 0);
     const EnsTime tm = time_of<kB>(E);
     // global rank (index of the ranked hole) and rank inside the ensemble
     const unsigned long long grank = (unsigned long long)a.tile_pre[0][rec.tile] + rec.r_in;
-    const unsigned long long rank = kB ? grank - a.map->ev_base[0][rec.ens] : grank;
+    const unsigned long long rank = kB ? grank - a.map->ev_base[0][ens] : grank;
     a.holes[grank] = (unsigned int)rec.i;
-    nbw_event<R>(rec, E, tb, tm.step, rank, gst);
+    if (rec.ens & kEvMedium) bh_event<R>(a, rec, E, rank, gst);
+    else nbw_event<R>(rec, E, tb, tm.step, rank, gst);
   }
 }
 
@@ -1575,14 +1767,17 @@ __device__ __forceinline__ void close_step(const StepArgs& a, bool births) {
       E.user_stats->n_processed += processed;
       E.user_stats->n_ncs[0] += v->ev[0];
       E.user_stats->n_ncs[1] += v->ev[1];
-      E.user_stats->n_nbw += nbw;
+      E.user_stats->n_nbw += nbw - v->ev[7];   // the ranked decays include the Bethe-Heitler pairs
+      E.user_stats->n_brems[0] += v->ev[5];
+      E.user_stats->n_brems[1] += v->ev[6];
+      E.user_stats->n_bh += v->ev[7];
       E.user_stats->n_range += v->ev[3];
       E.user_stats->n_drop += v->ev[4];
       E.user_stats->n_steps += 1;
       E.user_stats->n_coarse += v->ev[2];
     }
     if (v->ev[3]) atomicOr(&gst->status, QED_STATUS_TABLE_RANGE);
-    for (int q = 0; q < 6; ++q) v->ev[q] = 0;
+    for (int q = 0; q < 8; ++q) v->ev[q] = 0;
     v->n_nbw = 0; v->n_surv = 0; v->n_ncs_tot = 0;
     if constexpr (kB) {
       // the ensemble's clock: the same operations as the host forms of a single step
@@ -1710,12 +1905,13 @@ __global__ void __launch_bounds__(kTile) k_ncs_ev(const __grid_constant__ StepAr
        kk += (unsigned long long)gridDim.x * blockDim.x) {
     const NcsRec<R> rec = evlog[kk];
     if (rec.stamp != epoch || a.tile_cnt[1][rec.tile] == 0) continue;
-    const int ens = kB ? (int)(rec.species >> 1) : 0;
+    const int ens = kB ? (int)((rec.species & ~kEvMedium) >> 1) : 0;
     const EnsArgs& E = ens_of<kB>(a, ens);
     const EnsTime tm = time_of<kB>(E);
     const unsigned long long grank = (unsigned long long)a.tile_pre[1][rec.tile] + rec.r_in;
     const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
-    ncs_event<R>(rec, E, tb, tm.step, rank, births, a.flags, gst, false, 0.0f);
+    if (rec.species & kEvMedium) brems_event<R>(a, rec, E, tm.step, rank, births, a.flags, gst);
+    else ncs_event<R>(rec, E, tb, tm.step, rank, births, a.flags, gst, false, 0.0f);
   }
   close_step<kB>(a, births);
 }
@@ -1748,11 +1944,11 @@ __global__ void __launch_bounds__(kMlpRows) k_ncs_ev_mlp(const __grid_constant__
       rec = evlog[kk];
       valid = rec.stamp == epoch && a.tile_cnt[1][rec.tile] != 0;
     }
-    const int ens = valid && kB ? (int)(rec.species >> 1) : 0;
+    const int ens = valid && kB ? (int)((rec.species & ~kEvMedium) >> 1) : 0;
     const EnsArgs& E = ens_of<kB>(a, ens);
     const EnsTime tm = time_of<kB>(E);
     float x[3] = {0.0f, 0.0f, 0.0f}, lnchi = 0.0f, t = 0.0f;
-    if (valid) {
+    if (valid && !(rec.species & kEvMedium)) {
       // the network's inputs: ln chi_e, s = S.zeta, logit of the level uniform
       const SpeciesArgs& L = E.sp[rec.species & 1u];
       const unsigned long long i = rec.i;
@@ -1780,7 +1976,8 @@ __global__ void __launch_bounds__(kMlpRows) k_ncs_ev_mlp(const __grid_constant__
       const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
       // outside the trained chi_e range the table sampler (the fallback) draws the energy
       const bool learned = rec.chi >= kMlpChiLo && rec.chi <= kMlpChiHi;
-      ncs_event<float>(rec, E, tb, tm.step, rank, births, a.flags, gst, learned, mlp_base(lnchi, t) + 8.0f * y);
+      if (rec.species & kEvMedium) brems_event<float>(a, rec, E, tm.step, rank, births, a.flags, gst);
+      else ncs_event<float>(rec, E, tb, tm.step, rank, births, a.flags, gst, learned, mlp_base(lnchi, t) + 8.0f * y);
     }
   }
   mlp_teardown(sm);

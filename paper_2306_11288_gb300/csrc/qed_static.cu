@@ -111,8 +111,12 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
       return QED_ERR_INVALID_ARG;
     }
   }
-  if ((flags & QED_F_NBW) && (!e || !pos)) {
-    set_error("qed_step_static: NBW needs e- and e+ sets");
+  if ((flags & (QED_F_NBW | QED_F_BH)) && (!e || !pos)) {
+    set_error("qed_step_static: NBW and Bethe-Heitler pairs need e- and e+ sets");
+    return QED_ERR_INVALID_ARG;
+  }
+  if ((flags & (QED_F_BREMS | QED_F_BH)) && !c->has_medium) {
+    set_error("qed_step_static: QED_F_BREMS / QED_F_BH need a medium (qed_set_medium)");
     return QED_ERR_INVALID_ARG;
   }
   {
@@ -152,6 +156,7 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
   a.tile_cnt[1] = reinterpret_cast<unsigned int*>(b + kSoCntLep);
   a.tile_pre[1] = reinterpret_cast<unsigned int*>(b + kSoPreLep);
   a.holes = reinterpret_cast<unsigned int*>(b + kSoHoles);
+  set_medium_args(a, c);
   a.rec[0] = b + kSoLogNbw;
   a.rec[1] = b + kSoLogNcs;
   a.rec_cap[0] = kStRecNbw;

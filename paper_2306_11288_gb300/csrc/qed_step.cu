@@ -12,10 +12,15 @@ size_t ncs_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NcsRec
 // the lepton pass reads only particles below the counts of the step start, the pair
 // births of k_nbw_ev go above them, so the two chains are independent until k_ncs_ev.
 // the lepton pass: with the radiative pusher flags its kRad instantiation
+// (the matter processes are their own instantiations, so that the others keep their
+// registers; they exclude the radiative pusher)
 template <typename R>
 static void launch_lepton(const StepArgs& a, int grid, cudaStream_t s) {
   const bool rad = a.flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT), dep = a.flags & QED_F_DEPOSIT;
-  if (rad && dep) k_lepton<R, false, true, true, true><<<grid, kTile, 0, s>>>(a);
+  const bool med = a.flags & QED_F_BREMS;
+  if (med && dep) k_lepton<R, false, true, false, true, true><<<grid, kTile, 0, s>>>(a);
+  else if (med) k_lepton<R, false, true, false, false, true><<<grid, kTile, 0, s>>>(a);
+  else if (rad && dep) k_lepton<R, false, true, true, true><<<grid, kTile, 0, s>>>(a);
   else if (rad) k_lepton<R, false, true, true><<<grid, kTile, 0, s>>>(a);
   else if (dep) k_lepton<R, false, true, false, true><<<grid, kTile, 0, s>>>(a);
   else k_lepton<R, false, true><<<grid, kTile, 0, s>>>(a);
@@ -34,7 +39,8 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     if (ss.tev) cudaEventRecord(ss.tev[5], ss.side);
     cudaEventRecord(ss.join, ss.side);
   }
-  k_photon<R, false, true><<<nb[0], kTile, 0, s>>>(a);
+  if (a.flags & QED_F_BH) k_photon<R, false, true, true><<<nb[0], kTile, 0, s>>>(a);
+  else k_photon<R, false, true><<<nb[0], kTile, 0, s>>>(a);
   if (ss.tev) cudaEventRecord(ss.tev[1], s);
   launch_k(k_scan<false>, 1, kScanThreads, s, pdl, a, 0);
   launch_k(k_nbw_ev<R, false>, nb[2], kTile, s, pdl, a);

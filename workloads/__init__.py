@@ -190,3 +190,38 @@ def c4(n_ens=64, seed=4, cap_each=None):
         sub["name"] = f"c4_ens{k}"
         out.append(sub)
     return out
+
+
+# ---------------------------------------------------------------------------------
+# Matter (Sec. III E): an electron beam through a solid slab, no laser field -- the
+# paper's bremsstrahlung test (1 GeV and 100 MeV electrons onto 5 mm of Au or Al, the
+# field updater off).  Densities of the solid from its mass density and molar mass.
+# ---------------------------------------------------------------------------------
+LENGTH_UNIT_CM = 1e-4 / TWO_PI     # 1/k0 for lambda = 1 um
+SOLIDS = {"Au": (79, 19.32, 196.966570), "Al": (13, 2.699, 26.9815385), "Cu": (29, 8.96, 63.546),
+          "W": (74, 19.3, 183.84), "Pb": (82, 11.35, 207.2)}
+
+
+def medium(name="Au", thickness_mm=5.0, k_min=1.0, axis=2):
+    """The slab 0 <= x[axis] < thickness of solid `name`: atoms per (1/k0)^3; photons below
+    k_min (m c^2) are not produced."""
+    Z, rho, A = SOLIDS[name]
+    n = rho * 6.02214076e23 / A * LENGTH_UNIT_CM ** 3
+    return {"Z": Z, "n": n, "k_min": k_min, "axis": axis, "lo": 0.0, "hi": thickness_mm * 0.1 / LENGTH_UNIT_CM}
+
+
+def slab(n=1_000_000, seed=5, gamma0=2000.0, spread=0.0, name="Au", thickness_mm=5.0, k_min=1.0, dt_um=5.0,
+         depth_mm=0.0):
+    """n electrons (gamma0 = 2000 is 1 GeV) along +z at depth `depth_mm` inside the slab
+    (transverse Gaussian rms 10 um, spins along +y), no field; dt such that c dt = dt_um
+    micrometres; crossing the 5 mm slab takes 1000 steps at 5 um."""
+    rng = np.random.default_rng(seed)
+    g = gamma0 * (1.0 + spread * rng.normal(size=n)) if spread > 0 else np.full(n, gamma0)
+    pz = np.sqrt(np.maximum(g * g - 1.0, 0.0))
+    sig = 10e-4 / LENGTH_UNIT_CM
+    e = {"x": rng.normal(size=n) * sig, "y": rng.normal(size=n) * sig, "z": np.full(n, depth_mm * 0.1 / LENGTH_UNIT_CM),
+         "px": np.zeros(n), "py": np.zeros(n), "pz": pz,
+         "s1": np.zeros(n), "s2": np.ones(n), "s3": np.zeros(n), "w": np.ones(n), "id": _ids(n)}
+    return {"e": e, "pos": empty(), "ph": empty(True), "field": {"kind": "none"},
+            "dt": dt_um * 1e-4 / LENGTH_UNIT_CM, "t0": 0.0, "seed": seed, "next_id": n,
+            "medium": medium(name, thickness_mm, k_min), "name": f"slab_{name}_{thickness_mm:g}mm_g{gamma0:g}_n{n}"}
