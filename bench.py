@@ -336,6 +336,31 @@ def run_rr(q, torch, steps, warmup, flush, kernel_steps):
     return out
 
 
+def run_matter(q, torch, steps, warmup, flush, pre=40, f64_steps=10):
+    """Bremsstrahlung and Bethe-Heitler pairs in matter (Sec. III E): 1e6 electrons of
+    1 GeV entering 5 mm of gold, no field, c dt = 5 um (the paper's Geant4 comparison
+    geometry); `pre` untimed steps populate photons and pairs, then the timing of the
+    headline (L2 flushed before every step).  Mixed and FP64 paths."""
+    import workloads
+    n = 1_000_000
+    wl = workloads.slab(n=n, seed=5)
+    flags = q.QED_F_BREMS | q.QED_F_BH
+    caps = {"cap_e": 3 * n, "cap_p": 2 * n, "cap_ph": 8 * n}
+    out = {"workload": wl["name"], "unit": "particle-steps/s", "pre_steps": pre, "medium": wl["medium"]}
+    for name, prec, nst in (("mixed", q.QED_PREC_MIXED, steps), ("f64", q.QED_PREC_F64, f64_steps)):
+        if nst <= 0:
+            continue
+        sim, info = run_gpu_path(q, torch, wl, prec, nst, warmup, flush, flags, 0, pre=pre, caps=caps)
+        c = sim.counters()
+        out[name] = {"value": info["particles"] / (info["ms"] * 1e-3), "ms_per_step": info["ms"] / nst,
+                     "steps": nst, "status": info["status"], "counts_after": info["final_counts"],
+                     "brems": c["n_brems_e"] + c["n_brems_p"], "pairs": c["n_bh"]}
+        sim.close()
+    if "mixed" in out and "f64" in out:
+        out["speedup_mixed"] = out["mixed"]["value"] / out["f64"]["value"]
+    return out
+
+
 C4_PRE = 150   # the ensembles start 150 steps before the beam centres reach the focus
 
 
@@ -772,6 +797,8 @@ def main():
                     help="timed steps of the self-consistent PIC leg (0: skip)")
     ap.add_argument("--rr-steps", type=int, default=50,
                     help="timed steps of the radiative-pusher leg (0: skip)")
+    ap.add_argument("--matter-steps", type=int, default=50,
+                    help="timed steps of the bremsstrahlung / Bethe-Heitler leg (0: skip)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy block (mixed path vs the oracle sample and the FP64 GPU path)")
     ap.add_argument("--kernel-steps", type=int, default=20,
@@ -805,7 +832,7 @@ def main():
 
     if world > 1:
         # replicas: the headline and e2e on every rank; the single-GPU side legs only at N = 1
-        args.c3_steps = args.c4_steps = args.c5_steps = args.rr_steps = args.pic_steps = 0
+        args.c3_steps = args.c4_steps = args.c5_steps = args.rr_steps = args.pic_steps = args.matter_steps = 0
         args.no_f64 = True
     dist = None
     if world > 1:
@@ -839,6 +866,7 @@ def main():
           if args.c3_steps > 0 else None)
     rr = run_rr(q, torch, args.rr_steps, args.warmup, flush, min(args.kernel_steps, 10)) if args.rr_steps > 0 else None
     pic = run_pic(q, torch, args.pic_steps, args.warmup) if args.pic_steps > 0 else None
+    matter = run_matter(q, torch, args.matter_steps, args.warmup, flush) if args.matter_steps > 0 else None
     c4 = run_c4(q, torch, args.c4_steps, args.warmup) if args.c4_steps > 0 else None
     c5 = run_c5(q, torch, args.c5_steps) if args.c5_steps > 0 else None
     e2e = run_e2e(q, torch, sim, q.QED_PREC_MIXED, args.e2e_steps, flags)
@@ -903,6 +931,7 @@ def main():
         "c4": c4,
         "radiative_pusher": rr,
         "pic": pic,
+        "matter": matter,
         "c5": c5,
         "gpu_launches": 7 * args.steps,   # headline loop; per step: photon, lepton, 2 scans, pairs, refill, NCS
         "clocks": clk.summary(),
