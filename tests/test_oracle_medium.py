@@ -130,7 +130,7 @@ def _slab_run(orc, species, n, energy, target_p):
            "id": np.arange(n, dtype=np.uint64)}
     empty = {k: v[:0] for k, v in one.items()}
     wl = {"e": empty, "pos": empty, "ph": dict(empty, theta=np.zeros(0)), "field": {"kind": "none"}, "dt": dt,
-          "seed": 31, "next_id": n}
+          "seed": 31, "next_id": n, "medium": m}
     if species == "e":
         wl["e"] = one
     else:
@@ -217,7 +217,7 @@ def test_medium_slab_bounds():
     sig = orc.medium_sigma(0, E)
     dt = math.log(2) / (med["n"] * ALPHA * R0N ** 2 * sig)
     sim = oracle.Sim(orc, {"e": one, "pos": empty, "ph": dict(empty, theta=np.zeros(0)), "field": {"kind": "none"},
-                           "dt": dt, "seed": 3, "next_id": n}, cap_ph=n)
+                           "dt": dt, "seed": 3, "next_id": n, "medium": med}, cap_ph=n)
     sim.run(1, oracle.F_BREMS)
     el = sim.state()["e"]
     o = np.argsort(el["id"])
