@@ -334,7 +334,7 @@ qed_status qed_step_host(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed
  * memory is all owned by its own allocator.  The paper has no counterpart of this call.
  * It runs exactly the kernels of qed_step, but keeps their per-step scratch (per-tile event
  * counts and prefixes, the event logs sized for one event per particle, the list of
- * decayed photon slots) in one file-scope device array of the library (about 14.3 MiB,
+ * decayed photon slots) in one file-scope device array of the library (about 17.8 MiB,
  * held by every process that loads the library on every device it uses) instead of the
  * context's buffers, and calls no cudaMalloc or cudaFree.  Limit: every given particle
  * set must have capacity <= 65536; larger sets are rejected with QED_ERR_INVALID_ARG (use

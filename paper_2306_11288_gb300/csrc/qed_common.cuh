@@ -300,6 +300,7 @@ struct DevState {
   unsigned long long n_surv;         // this step: photons surviving NBW
   unsigned long long n_nbw;          // this step: pairs created (ranked decays)
   unsigned long long n_ncs_tot;      // this step: ranked emissions
+  unsigned long long n_hlow;         // this step: decayed photon slots below n_surv
   unsigned long long cursor[2];      // this step: entries written to the NBW / NCS logs
   unsigned long long ev[8];          // this step: ncs_e, ncs_p, coarse (P > 0.1), range, drop, brems e-,
                                      // brems e+, Bethe-Heitler pairs

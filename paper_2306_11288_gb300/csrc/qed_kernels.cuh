@@ -2,9 +2,9 @@
 // qed_kernels.cuh -- the per-step kernels of the spin/polarization-resolved SF-QED hot path
 // (Wan et al., arXiv:2306.11288, Secs. II-IV) for sm_103a.
 //
-// One step = seven launches.  Caller's stream: k_photon, k_scan(photon tiles), k_nbw_ev,
-// k_fill, then (after joining the side stream) k_scan(lepton tiles), k_ncs_ev; the context's
-// side stream runs k_lepton concurrently with the photon chain.  The event kernels are
+// One step = five launches.  Caller's stream: k_photon, k_scan(photon tiles), then (after
+// joining the side stream) k_scan(lepton tiles), k_events; the context's side stream runs
+// k_lepton concurrently with the photon chain.  The scans and the event kernel are
 // programmatic dependents of the kernel before them.
 //   k_photon   : streaming pass over photons -- gather, Stokes frame rotation (Eq. rotation),
 //                VB phase (Eq. rotation2), NBW decision (Sec. III D); photons are updated in
@@ -14,11 +14,12 @@
 //                update and collapse is done here; emissions are logged.
 //   k_scan     : exclusive scan of the per-tile event counts (one block): the rank of an
 //                event is the prefix of its tile plus its rank inside the tile, which orders
-//                events by particle index exactly as a sequential pass would.
-//   k_nbw_ev   : one thread per logged decay: pair energy, spins, birth of e- and e+.
-//   k_fill     : decayed photon slots below the new count are refilled from the tail.
-//   k_ncs_ev   : one thread per logged emission: photon energy, recoil, spin collapse,
-//                photon Stokes, photon birth; its last block closes the step (counts, ids).
+//                events by particle index exactly as a sequential pass would; the photon
+//                scan also lists the decayed slots (holes) in index order.
+//   k_events   : one thread per task: a logged emission (photon energy, recoil, spin
+//                collapse, photon Stokes, photon birth), a logged decay (pair energy, spins,
+//                birth of e- and e+) or the refill of a decayed photon slot; its last block
+//                closes the step (counts, ids).
 // The streaming passes carry no cross-block waits; the rare events run at full warp width.
 //
 // GB300's FP64 pipe (and every FP32<->FP64 conversion, which runs on it) is ~70x slower
@@ -598,6 +599,10 @@ struct NbwRec {
   unsigned int stamp, ens;   // step stamp; ensemble of the photon
   double x, y, z;            // x^n (the photon itself has moved on in its slot)
   R chig, rmix, p1x, p1y, p1z;
+  // the photon as the decision left it (k, Stokes after this step's rotations, weight,
+  // id): the event reads none of the slot, which a refill or a birth may take meanwhile
+  R kx, ky, kz, x1, x2, x3, w;
+  unsigned long long id;
 };
 template <typename R>
 struct NcsRec {
@@ -931,6 +936,8 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
       rec.ens = (unsigned int)ens | (bh ? kEvMedium : 0u);   // bit 31: a Bethe-Heitler decay
       rec.x = x; rec.y = y; rec.z = z;
       rec.chig = chig; rec.rmix = rmix; rec.p1x = P1.x; rec.p1y = P1.y; rec.p1z = P1.z;
+      rec.kx = k.x; rec.ky = k.y; rec.kz = k.z; rec.x1 = xi.x; rec.x2 = xi.y; rec.x3 = xi.z;
+      rec.w = ld<R>(P.w, i); rec.id = id;
       evlog[slot] = rec;
     }
     if constexpr (kPf) {
@@ -1292,7 +1299,7 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
           // one event per lepton per step is coarse where W dt > 0.1 (rare: no ballot)
           if (Pe > R(0.1)) atomicAdd(&st->ev[2], 1ull);
           if (u.u0 < Pe) {
-            emit = true;   // completed by k_ncs_ev
+            emit = true;   // completed by k_events
           } else {
             // no emission: posterior mean spin, then collapse with P(+) = (1+|S|)/2
             const R den = f_rcp(R(1) - Pe);
@@ -1340,6 +1347,51 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
   }
 }
 
+// ---- photon slots after a step ----------------------------------------------------------
+// Decays leave holes h[0..D) (ascending).  With N photons at the step start and the new
+// count M = N - D, the k-th surviving photon at or above M fills the k-th hole below M
+// (both in index order), and the r-th birth takes slot M + r.  A birth into a slot below N
+// first moves the photon there (if it survived) into its hole, and the slots at or above M
+// that no birth takes are refill tasks of their own: so the refill, the births and the
+// pair events (which read their photons from the log) run in one kernel in any order.
+__device__ __forceinline__ unsigned long long upper_bound_u32(const unsigned int* h, unsigned long long n,
+                                                              unsigned long long v) {
+  unsigned long long lo = 0, hi = n;
+  while (lo < hi) {
+    const unsigned long long m = (lo + hi) >> 1;
+    if ((unsigned long long)h[m] <= v) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+
+// Empty slot j (M <= j < N) of the photon set P: a surviving photon there moves to its hole.
+// st carries D (n_nbw), M (n_surv) and the number of holes below M (n_hlow); h the holes.
+template <typename R>
+__device__ __noinline__ void ph_vacate(const SpeciesArgs& P, const DevState* st, const unsigned int* h,
+                                       unsigned long long j) {
+  // every load before the first store: the arrays may alias as far as the compiler knows,
+  // and a load after a store would wait for the one before it
+  const double x = P.x[j], y = P.y[j], z = P.z[j];
+  const R px = ld<R>(P.px, j), py = ld<R>(P.py, j), pz = ld<R>(P.pz, j);
+  const R s1 = ld<R>(P.s1, j), s2 = ld<R>(P.s2, j), s3 = ld<R>(P.s3, j);
+  const R th = ld<R>(P.theta, j), w = ld<R>(P.w, j);
+  const uint64_t id = P.id[j];
+  const unsigned long long D = st->n_nbw, M = st->n_surv, H = st->n_hlow;
+  unsigned long long lo = H, hi = D;   // the holes at or above M below j: h[H..lo)
+  while (lo < hi) {
+    const unsigned long long m = (lo + hi) >> 1;
+    if ((unsigned long long)h[m] < j) lo = m + 1; else hi = m;
+  }
+  if (lo < D && (unsigned long long)h[lo] == j) return;   // slot j decayed
+  const unsigned long long dst = h[(j - M) - (lo - H)];  // survivor rank among those at or above M
+  P.x[dst] = x; P.y[dst] = y; P.z[dst] = z;
+  stv<R>(P.px, dst, px); stv<R>(P.py, dst, py); stv<R>(P.pz, dst, pz);
+  stv<R>(P.s1, dst, s1); stv<R>(P.s2, dst, s2); stv<R>(P.s3, dst, s3);
+  stv<R>(P.theta, dst, th);
+  stv<R>(P.w, dst, w);
+  P.id[dst] = id;
+}
+
 // ======================================================================================
 // exclusive scan of the tile counts (which = 0: photon tiles, 1: lepton tiles), one block;
 // 32 consecutive counts per thread (vector loads) so that a pass covers 32768 tiles
@@ -1347,7 +1399,7 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 32;
 
-template <bool kB>
+template <typename R, bool kB>
 __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ StepArgs a, int which) {
   pdl_wait();
   pdl_trigger();
@@ -1440,15 +1492,47 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ S
       base[e] = tile0[e] < ntiles ? pre[tile0[e]] : (unsigned int)s_run;
     __syncthreads();
   }
+  if (which == 0) {
+    // the holes: the slot of every ranked decay at its rank (ascending slots per ensemble)
+    const DevState* gst = a.st;
+    const unsigned long long nrec = min(gst->cursor[0], a.rec_cap[0]);
+    const unsigned int epoch = gst->epoch;
+    const NbwRec<R>* evlog = reinterpret_cast<const NbwRec<R>*>(a.rec[0]);
+    for (unsigned long long kk = threadIdx.x; kk < nrec; kk += blockDim.x) {
+      const NbwRec<R>& rec = evlog[kk];
+      if (rec.stamp != epoch || cnt[rec.tile] == 0) continue;
+      a.holes[pre[rec.tile] + rec.r_in] = (unsigned int)rec.i;
+    }
+    __syncthreads();
+  }
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const EnsArgs& E = ens_of<kB>(a, e);
     const unsigned long long tot = kB ? (unsigned long long)(base[e + 1] - base[e]) : s_run;
     if (which == 0) {
       const unsigned long long nph = E.sp[2].present ? E.st->n_live[2] : 0ull;
+      const unsigned long long M = nph - tot;
       E.st->n_nbw = tot;
-      E.st->n_surv = nph - tot;
+      E.st->n_surv = M;
+      E.st->n_hlow = M == 0 ? 0ull : upper_bound_u32(a.holes + (kB ? base[e] : 0u), tot, M - 1);
     } else {
       E.st->n_ncs_tot = tot;
+    }
+  }
+  if constexpr (kB) {
+    // the refill tasks of each ensemble: its slots M + r, C <= r < D, that no birth takes
+    if (which == 1) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
+        unsigned int f = 0;
+        for (int e = 0; e < ne; ++e) {
+          a.map->fill_base[e] = f;
+          const DevState* st = ens_of<kB>(a, e).st;
+          const unsigned long long D = st->n_nbw, C = births ? st->n_ncs_tot : 0ull;
+          f += (unsigned int)(C < D ? D - C : 0ull);
+        }
+        a.map->fill_base[ne] = f;
+      }
     }
   }
 }
@@ -1457,21 +1541,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ S
 // NBW events: pair energy split (mixture over xi3' = +-1), SQAs D and D', joint spin
 // sampling from Eqs. G0-G3, birth of the pair at the photon's x^n (Sec. III D)
 // ======================================================================================
-// One decay (the body of k_nbw_ev), not inlined so that the single-ensemble and the
+// One decay (a task of k_events), not inlined so that the single-ensemble and the
 // batched kernels run the same compiled arithmetic (inlined into different kernels, the
 // compiler may fuse multiply-adds differently and results would differ in the last bit).
 template <typename R>
 __device__ __noinline__ void nbw_event(const NbwRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
                                        unsigned long long rank, DevState* gst) {
   DevState* st = E.st;
-  const SpeciesArgs& P = E.sp[2];
   const unsigned long long ne0 = st->n_live[0], np0 = st->n_live[1];
   const unsigned long long id0 = st->next_id;
-  const unsigned long long i = rec.i;
-  const V3<R> k = mk<R>(ld<R>(P.px, i), ld<R>(P.py, i), ld<R>(P.pz, i));
-  const V3<R> xi = mk<R>(ld<R>(P.s1, i), ld<R>(P.s2, i), ld<R>(P.s3, i));
-  const R wgt = ld<R>(P.w, i);
-  const uint64_t id = P.id[i];
+  const V3<R> k = mk<R>(rec.kx, rec.ky, rec.kz);
+  const V3<R> xi = mk<R>(rec.x1, rec.x2, rec.x3);
+  const R wgt = rec.w;
+  const uint64_t id = rec.id;
   const R om = norm(k);
   const V3<R> nn = (R(1) / om) * k;
   const V3<R> P1 = mk<R>(rec.p1x, rec.p1y, rec.p1z);
@@ -1565,11 +1647,9 @@ template <typename R>
 __device__ __noinline__ void bh_event(const StepArgs& a, const NbwRec<R>& rec, const EnsArgs& E, unsigned long long rank,
                                       DevState* gst) {
   DevState* st = E.st;
-  const SpeciesArgs& P = E.sp[2];
   const unsigned long long ne0 = st->n_live[0], np0 = st->n_live[1], id0 = st->next_id;
-  const unsigned long long i = rec.i;
-  const double kx = (double)ld<R>(P.px, i), ky = (double)ld<R>(P.py, i), kz = (double)ld<R>(P.pz, i);
-  const R wgt = ld<R>(P.w, i);
+  const double kx = (double)rec.kx, ky = (double)rec.ky, kz = (double)rec.kz;
+  const R wgt = rec.w;
   const double om = sqrt(kx * kx + ky * ky + kz * kz);
   const double nx = kx / om, ny = ky / om, nz = kz / om;
   const double xf = med_sample(a, 1, om, (double)rec.rmix);
@@ -1603,14 +1683,18 @@ __device__ __noinline__ void bh_event(const StepArgs& a, const NbwRec<R>& rec, c
 // at the lepton's x^{n+1}.
 template <typename R>
 __device__ __noinline__ void brems_event(const StepArgs& a, const NcsRec<R>& rec, const EnsArgs& E, unsigned int step,
-                                         unsigned long long rank, bool births, unsigned int flags, DevState* gst) {
+                                         unsigned long long rank, bool births, unsigned int flags, DevState* gst,
+                                         const unsigned int* holes) {
   DevState* st = E.st;
   const SpeciesArgs& G = E.sp[2];
   const SpeciesArgs& L = E.sp[rec.species & 1u];
   const unsigned long long nsurv = st->n_surv;
   const unsigned long long id0 = st->next_id + 2ull * st->n_nbw;
+  const unsigned long long nph0 = st->n_live[2];
   const unsigned long long i = rec.i;
   const double px = (double)ld<R>(L.px, i), py = (double)ld<R>(L.py, i), pz = (double)ld<R>(L.pz, i);
+  const double lx = L.x[i], ly = L.y[i], lz = L.z[i];   // read before the lepton's stores
+  const R lw = ld<R>(L.w, i);
   const double pmag = sqrt(px * px + py * py + pz * pz);
   if (!(pmag > 0.0)) return;
   const double g1 = sqrt(1.0 + px * px + py * py + pz * pz);
@@ -1630,97 +1714,14 @@ __device__ __noinline__ void brems_event(const StepArgs& a, const NcsRec<R>& rec
       atomicOr(&gst->status, QED_STATUS_CAPACITY);
       atomicAdd(&st->ev[4], 1ull);
     } else {
-      G.x[j] = L.x[i]; G.y[j] = L.y[i]; G.z[j] = L.z[i];
+      if (j < nph0) ph_vacate<R>(G, st, holes, j);
+      G.x[j] = lx; G.y[j] = ly; G.z[j] = lz;
       stv<R>(G.px, j, (R)(om * nx)); stv<R>(G.py, j, (R)(om * ny)); stv<R>(G.pz, j, (R)(om * nz));
       stv<R>(G.s1, j, R(0)); stv<R>(G.s2, j, R(0)); stv<R>(G.s3, j, R(0));
       stv<R>(G.theta, j, R(0));
-      stv<R>(G.w, j, ld<R>(L.w, i));
+      stv<R>(G.w, j, lw);
       G.id[j] = id0 + rank;
     }
-  }
-}
-
-template <typename R, bool kB>
-__global__ void __launch_bounds__(kTile) k_nbw_ev(const __grid_constant__ StepArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  DevState* gst = a.st;
-  const Tabs<R> tb = tabs_global<R>(a.tables);
-  const unsigned long long nrec = min(gst->cursor[0], a.rec_cap[0]);
-  const unsigned int epoch = gst->epoch;
-  const NbwRec<R>* evlog = reinterpret_cast<const NbwRec<R>*>(a.rec[0]);
-  for (unsigned long long kk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; kk < nrec;
-       kk += (unsigned long long)gridDim.x * blockDim.x) {
-    const NbwRec<R> rec = evlog[kk];
-    if (rec.stamp != epoch || a.tile_cnt[0][rec.tile] == 0) continue;
-    const unsigned int ens = rec.ens & ~kEvMedium;
-    const EnsArgs& E = ens_of<kB>(a, kB ? (int)ens : 0);
-    const EnsTime tm = time_of<kB>(E);
-    // global rank (index of the ranked hole) and rank inside the ensemble
-    const unsigned long long grank = (unsigned long long)a.tile_pre[0][rec.tile] + rec.r_in;
-    const unsigned long long rank = kB ? grank - a.map->ev_base[0][ens] : grank;
-    a.holes[grank] = (unsigned int)rec.i;
-    if (rec.ens & kEvMedium) bh_event<R>(a, rec, E, rank, gst);
-    else nbw_event<R>(rec, E, tb, tm.step, rank, gst);
-  }
-}
-
-// ======================================================================================
-// removal of decayed photons: the k-th decayed slot below the new count M = N - D receives
-// the k-th surviving photon at or above M (both in index order)
-// ======================================================================================
-__device__ __forceinline__ unsigned long long upper_bound_u32(const unsigned int* h, unsigned long long n,
-                                                              unsigned long long v) {
-  unsigned long long lo = 0, hi = n;
-  while (lo < hi) {
-    const unsigned long long m = (lo + hi) >> 1;
-    if ((unsigned long long)h[m] <= v) lo = m + 1; else hi = m;
-  }
-  return lo;
-}
-
-template <typename R, bool kB>
-__global__ void __launch_bounds__(kTile) k_fill(const __grid_constant__ StepArgs a) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ unsigned int s_base[kB ? kMaxEns + 1 : 1];
-  unsigned long long total;
-  if constexpr (kB) {
-    for (int e = threadIdx.x; e <= a.n_ens; e += blockDim.x) s_base[e] = a.map->ev_base[0][e];
-    __syncthreads();
-    total = s_base[a.n_ens];
-  } else {
-    total = a.e0.st->n_nbw;
-  }
-  // Per ensemble (holes h, D of them, N photons, new count M = N - D): H holes lie below
-  // M (they are refilled); the D - H holes at or above M are skipped over: with
-  // g(p) = h[H + p] - M - p survivors ahead of hole H + p (non-decreasing), the kk-th
-  // survivor at or above M is M + kk + #{p : g(p) <= kk}
-  for (unsigned long long gk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; gk < total;
-       gk += (unsigned long long)gridDim.x * blockDim.x) {
-    const int ens = kB ? find_ens(s_base, a.n_ens, (unsigned int)gk) : 0;
-    const EnsArgs& E = ens_of<kB>(a, ens);
-    const SpeciesArgs& P = E.sp[2];
-    if (!P.present) continue;
-    const unsigned long long b0 = kB ? s_base[ens] : 0ull;
-    const unsigned long long kk = gk - b0;
-    const unsigned int* h = a.holes + b0;
-    const unsigned long long D = E.st->n_nbw, N = E.st->n_live[2], M = N - D;
-    const unsigned long long H = M == 0 ? 0 : upper_bound_u32(h, D, M - 1);
-    if (kk >= H) continue;
-    const unsigned long long dst = h[kk];
-    unsigned long long lo = 0, hi = D - H;
-    while (lo < hi) {
-      const unsigned long long m = (lo + hi) >> 1;
-      if ((unsigned long long)h[H + m] - M - m <= kk) lo = m + 1; else hi = m;
-    }
-    const unsigned long long src = M + kk + lo;
-    P.x[dst] = P.x[src]; P.y[dst] = P.y[src]; P.z[dst] = P.z[src];
-    stv<R>(P.px, dst, ld<R>(P.px, src)); stv<R>(P.py, dst, ld<R>(P.py, src)); stv<R>(P.pz, dst, ld<R>(P.pz, src));
-    stv<R>(P.s1, dst, ld<R>(P.s1, src)); stv<R>(P.s2, dst, ld<R>(P.s2, src)); stv<R>(P.s3, dst, ld<R>(P.s3, src));
-    stv<R>(P.theta, dst, ld<R>(P.theta, src));
-    stv<R>(P.w, dst, ld<R>(P.w, src));
-    P.id[dst] = P.id[src];
   }
 }
 
@@ -1778,7 +1779,7 @@ __device__ __forceinline__ void close_step(const StepArgs& a, bool births) {
     }
     if (v->ev[3]) atomicOr(&gst->status, QED_STATUS_TABLE_RANGE);
     for (int q = 0; q < 8; ++q) v->ev[q] = 0;
-    v->n_nbw = 0; v->n_surv = 0; v->n_ncs_tot = 0;
+    v->n_nbw = 0; v->n_surv = 0; v->n_ncs_tot = 0; v->n_hlow = 0;
     if constexpr (kB) {
       // the ensemble's clock: the same operations as the host forms of a single step
       const double t = v->t + a.dt;
@@ -1798,20 +1799,22 @@ __device__ __forceinline__ void close_step(const StepArgs& a, bool births) {
   }
 }
 
-// One emission (the body of k_ncs_ev), not inlined for the same reason as nbw_event.
+// One emission (a task of k_events), not inlined for the same reason as nbw_event.
 template <typename R>
 __device__ __noinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
                                        unsigned long long rank, bool births, unsigned int flags, DevState* gst,
-                                       bool learned, float lnu_learned) {
+                                       bool learned, float lnu_learned, const unsigned int* holes) {
   DevState* st = E.st;
   const SpeciesArgs& G = E.sp[2];
-  const unsigned long long nsurv = st->n_surv;
+  const unsigned long long nsurv = st->n_surv, nph0 = st->n_live[2];
   const unsigned long long id0 = st->next_id + 2ull * st->n_nbw;
   const SpeciesArgs& L = E.sp[rec.species & 1u];
   const unsigned long long i = rec.i;
   const V3<R> pn = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
   const V3<R> S = mk<R>(ld<R>(L.s1, i), ld<R>(L.s2, i), ld<R>(L.s3, i));
   const uint64_t id = L.id[i];
+  const double lx = L.x[i], ly = L.y[i], lz = L.z[i];   // the photon's birth place and weight,
+  const R lw = ld<R>(L.w, i);                            // read before the lepton's stores
   const R chi = rec.chi;
   const V3<R> av = mk<R>(rec.ax, rec.ay, rec.az);
   const R g1 = sqrt(R(1) + dot(pn, pn));
@@ -1880,38 +1883,104 @@ __device__ __noinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E, c
       atomicOr(&gst->status, QED_STATUS_CAPACITY);
       atomicAdd(&st->ev[4], 1ull);
     } else {
+      if (j < nph0) ph_vacate<R>(G, st, holes, j);
       V3<R> e1, e2;
       frame(nn, e1, e2);
-      G.x[j] = L.x[i]; G.y[j] = L.y[i]; G.z[j] = L.z[i];
+      G.x[j] = lx; G.y[j] = ly; G.z[j] = lz;
       stv<R>(G.px, j, om * nn.x); stv<R>(G.py, j, om * nn.y); stv<R>(G.pz, j, om * nn.z);
       stv<R>(G.s1, j, xiph.x); stv<R>(G.s2, j, xiph.y); stv<R>(G.s3, j, xiph.z);
       stv<R>(G.theta, j, m_atan2(dot(av, e2), dot(av, e1)));
-      stv<R>(G.w, j, ld<R>(L.w, i));
+      stv<R>(G.w, j, lw);
       G.id[j] = id0 + rank;
     }
   }
 }
 
+// ---- the event kernel's tasks ----------------------------------------------------------
+// The ensemble's holes (its ranked decays' slots, ascending)
+template <bool kB>
+__device__ __forceinline__ const unsigned int* holes_of(const StepArgs& a, int ens) {
+  return a.holes + (kB ? a.map->ev_base[0][ens] : 0u);
+}
+
+// one logged decay: NBW (Sec. III D) or Bethe-Heitler (Sec. III E) pair creation
 template <typename R, bool kB>
-__global__ void __launch_bounds__(kTile) k_ncs_ev(const __grid_constant__ StepArgs a) {
+__device__ __forceinline__ void nbw_task(const StepArgs& a, const Tabs<R>& tb, const NbwRec<R>& rec,
+                                         unsigned int epoch, DevState* gst) {
+  if (rec.stamp != epoch || a.tile_cnt[0][rec.tile] == 0) return;
+  const unsigned int ens = rec.ens & ~kEvMedium;
+  const EnsArgs& E = ens_of<kB>(a, kB ? (int)ens : 0);
+  // global rank (index of the ranked hole) and rank inside the ensemble
+  const unsigned long long grank = (unsigned long long)a.tile_pre[0][rec.tile] + rec.r_in;
+  const unsigned long long rank = kB ? grank - a.map->ev_base[0][ens] : grank;
+  if (rec.ens & kEvMedium) bh_event<R>(a, rec, E, rank, gst);
+  else nbw_event<R>(rec, E, tb, time_of<kB>(E).step, rank, gst);
+}
+
+// refill task f: slot M + r of its ensemble, for the r (C <= r < D) that no birth takes
+template <typename R, bool kB>
+__device__ __forceinline__ void fill_task(const StepArgs& a, const unsigned int* s_fb, unsigned long long f) {
+  const int ens = kB ? find_ens(s_fb, a.n_ens, (unsigned int)f) : 0;
+  const EnsArgs& E = ens_of<kB>(a, ens);
+  const DevState* st = E.st;
+  const unsigned long long D = st->n_nbw;
+  const unsigned long long nf = kB ? (unsigned long long)(s_fb[ens + 1] - s_fb[ens]) : s_fb[0];
+  const unsigned long long r = (D - nf) + (f - (kB ? s_fb[ens] : 0u));
+  ph_vacate<R>(E.sp[2], st, holes_of<kB>(a, ens), st->n_surv + r);
+}
+
+// the number of refill tasks (single ensemble) or their per-ensemble bases (batched)
+template <bool kB>
+__device__ __forceinline__ unsigned long long fill_setup(const StepArgs& a, bool births, unsigned int* s_fb) {
+  if constexpr (kB) {
+    for (int e = threadIdx.x; e <= a.n_ens; e += blockDim.x) s_fb[e] = a.map->fill_base[e];
+    __syncthreads();
+    return s_fb[a.n_ens];
+  } else {
+    const DevState* st = a.e0.st;
+    const unsigned long long D = st->n_nbw, C = births ? st->n_ncs_tot : 0ull;
+    s_fb[0] = (unsigned int)(C < D ? D - C : 0ull);
+    return C < D ? D - C : 0ull;
+  }
+}
+
+// ======================================================================================
+// k_events: every logged emission, every logged decay and every refill task of the step,
+// one thread each (grid-stride); they touch disjoint data (see the photon-slot rules
+// above), so one launch runs them all.  Its last block closes the step.
+// ======================================================================================
+template <typename R, bool kB>
+__global__ void __launch_bounds__(kTile) k_events(const __grid_constant__ StepArgs a) {
   pdl_wait();
+  __shared__ unsigned int s_fb[kB ? kMaxEns + 1 : 1];
   DevState* gst = a.st;
   const Tabs<R> tb = tabs_global<R>(a.tables);
-  const unsigned long long nrec = min(gst->cursor[1], a.rec_cap[1]);
+  const unsigned long long n1 = min(gst->cursor[1], a.rec_cap[1]);
+  const unsigned long long n0 = min(gst->cursor[0], a.rec_cap[0]);
   const unsigned int epoch = gst->epoch;
-  const NcsRec<R>* evlog = reinterpret_cast<const NcsRec<R>*>(a.rec[1]);
   const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
-  for (unsigned long long kk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; kk < nrec;
+  const unsigned long long nfill = fill_setup<kB>(a, births, s_fb);
+  const NcsRec<R>* ncslog = reinterpret_cast<const NcsRec<R>*>(a.rec[1]);
+  const NbwRec<R>* nbwlog = reinterpret_cast<const NbwRec<R>*>(a.rec[0]);
+  const unsigned long long total = n1 + n0 + nfill;
+  for (unsigned long long kk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; kk < total;
        kk += (unsigned long long)gridDim.x * blockDim.x) {
-    const NcsRec<R> rec = evlog[kk];
-    if (rec.stamp != epoch || a.tile_cnt[1][rec.tile] == 0) continue;
-    const int ens = kB ? (int)((rec.species & ~kEvMedium) >> 1) : 0;
-    const EnsArgs& E = ens_of<kB>(a, ens);
-    const EnsTime tm = time_of<kB>(E);
-    const unsigned long long grank = (unsigned long long)a.tile_pre[1][rec.tile] + rec.r_in;
-    const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
-    if (rec.species & kEvMedium) brems_event<R>(a, rec, E, tm.step, rank, births, a.flags, gst);
-    else ncs_event<R>(rec, E, tb, tm.step, rank, births, a.flags, gst, false, 0.0f);
+    if (kk < n1) {
+      const NcsRec<R> rec = ncslog[kk];
+      if (rec.stamp != epoch || a.tile_cnt[1][rec.tile] == 0) continue;
+      const int ens = kB ? (int)((rec.species & ~kEvMedium) >> 1) : 0;
+      const EnsArgs& E = ens_of<kB>(a, ens);
+      const EnsTime tm = time_of<kB>(E);
+      const unsigned long long grank = (unsigned long long)a.tile_pre[1][rec.tile] + rec.r_in;
+      const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
+      const unsigned int* h = holes_of<kB>(a, ens);
+      if (rec.species & kEvMedium) brems_event<R>(a, rec, E, tm.step, rank, births, a.flags, gst, h);
+      else ncs_event<R>(rec, E, tb, tm.step, rank, births, a.flags, gst, false, 0.0f, h);
+    } else if (kk < n1 + n0) {
+      nbw_task<R, kB>(a, tb, nbwlog[kk - n1], epoch, gst);
+    } else {
+      fill_task<R, kB>(a, s_fb, kk - n1 - n0);
+    }
   }
   close_step<kB>(a, births);
 }
@@ -1920,12 +1989,14 @@ __global__ void __launch_bounds__(kTile) k_ncs_ev(const __grid_constant__ StepAr
 // ======================================================================================
 // NCS events with the learned energy sampler (mixed path): a block of 128 threads takes
 // 128 logged emissions at a time, evaluates the network for all of them on the tensor
-// cores (qed_mlp.cuh), then completes each event as k_ncs_ev does.
+// cores (qed_mlp.cuh), then completes each event as k_events does; the decays and the
+// refill tasks follow as in k_events.
 // ======================================================================================
 template <bool kB>
-__global__ void __launch_bounds__(kMlpRows) k_ncs_ev_mlp(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(kMlpRows) k_events_mlp(const __grid_constant__ StepArgs a) {
   pdl_wait();
   __shared__ MlpSmem sm;
+  __shared__ unsigned int s_fb[kB ? kMaxEns + 1 : 1];
   DevState* gst = a.st;
   const Tabs<float> tb = tabs_global<float>(a.tables);
   const unsigned long long nrec = min(gst->cursor[1], a.rec_cap[1]);
@@ -1976,11 +2047,22 @@ __global__ void __launch_bounds__(kMlpRows) k_ncs_ev_mlp(const __grid_constant__
       const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
       // outside the trained chi_e range the table sampler (the fallback) draws the energy
       const bool learned = rec.chi >= kMlpChiLo && rec.chi <= kMlpChiHi;
-      if (rec.species & kEvMedium) brems_event<float>(a, rec, E, tm.step, rank, births, a.flags, gst);
-      else ncs_event<float>(rec, E, tb, tm.step, rank, births, a.flags, gst, learned, mlp_base(lnchi, t) + 8.0f * y);
+      const unsigned int* h = holes_of<kB>(a, ens);
+      if (rec.species & kEvMedium) brems_event<float>(a, rec, E, tm.step, rank, births, a.flags, gst, h);
+      else ncs_event<float>(rec, E, tb, tm.step, rank, births, a.flags, gst, learned, mlp_base(lnchi, t) + 8.0f * y,
+                            h);
     }
   }
   mlp_teardown(sm);
+  }
+  // the decays and the refill tasks, as in k_events
+  const unsigned long long n0 = min(gst->cursor[0], a.rec_cap[0]);
+  const unsigned long long nfill = fill_setup<kB>(a, births, s_fb);
+  const NbwRec<float>* nbwlog = reinterpret_cast<const NbwRec<float>*>(a.rec[0]);
+  for (unsigned long long kk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; kk < n0 + nfill;
+       kk += (unsigned long long)gridDim.x * blockDim.x) {
+    if (kk < n0) nbw_task<float, kB>(a, tb, nbwlog[kk], epoch, gst);
+    else fill_task<float, kB>(a, s_fb, kk - n0);
   }
   close_step<kB>(a, births);
 }

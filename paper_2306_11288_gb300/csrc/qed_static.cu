@@ -30,9 +30,9 @@ constexpr size_t kSoCntLep = kSoPrePh + rnd(4 * kStTilesPh);
 constexpr size_t kSoPreLep = kSoCntLep + rnd(4 * kStTilesLep);
 constexpr size_t kSoHoles = kSoPreLep + rnd(4 * kStTilesLep);
 constexpr size_t kSoLogNbw = kSoHoles + rnd(4 * kStRecNbw);
-constexpr size_t kNbwRecMax = 96, kNcsRecMax = 64;   // bytes per record, bounds checked at run time
+constexpr size_t kNbwRecMax = 152, kNcsRecMax = 64;   // bytes per record, bounds checked at run time
 constexpr size_t kSoLogNcs = kSoLogNbw + rnd(kNbwRecMax * kStRecNbw);
-constexpr size_t kStaticBytes = kSoLogNcs + rnd(kNcsRecMax * kStRecNcs);   // about 14.3 MiB
+constexpr size_t kStaticBytes = kSoLogNcs + rnd(kNcsRecMax * kStRecNcs);   // about 17.8 MiB
 
 // One array per process and device, shared by every call and every context.
 static __device__ __align__(256) unsigned char g_step_scratch[kStaticBytes];

@@ -7,13 +7,10 @@ namespace qedk {
 size_t nbw_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NbwRec<double>) : sizeof(NbwRec<float>); }
 size_t ncs_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NcsRec<double>) : sizeof(NcsRec<float>); }
 
-// Photon chain on the caller's stream; the lepton pass on the context's side stream
-// (forked after all earlier work on the caller's stream, joined before the lepton scan):
-// the lepton pass reads only particles below the counts of the step start, the pair
-// births of k_nbw_ev go above them, so the two chains are independent until k_ncs_ev.
-// the lepton pass: with the radiative pusher flags its kRad instantiation
-// (the matter processes are their own instantiations, so that the others keep their
-// registers; they exclude the radiative pusher)
+// Photon pass and its scan on the caller's stream; the lepton pass on the context's side
+// stream (forked after all earlier work on the caller's stream, joined before the lepton
+// scan): the two passes touch disjoint particles, and everything that needs both (births,
+// refills, pair events) is in k_events.
 template <typename R>
 static void launch_lepton(const StepArgs& a, int grid, cudaStream_t s) {
   const bool rad = a.flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT), dep = a.flags & QED_F_DEPOSIT;
@@ -42,9 +39,7 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
   if (a.flags & QED_F_BH) k_photon<R, false, true, true><<<nb[0], kTile, 0, s>>>(a);
   else k_photon<R, false, true><<<nb[0], kTile, 0, s>>>(a);
   if (ss.tev) cudaEventRecord(ss.tev[1], s);
-  launch_k(k_scan<false>, 1, kScanThreads, s, pdl, a, 0);
-  launch_k(k_nbw_ev<R, false>, nb[2], kTile, s, pdl, a);
-  launch_k(k_fill<R, false>, nb[2], kTile, s, pdl, a);
+  launch_k(k_scan<R, false>, 1, kScanThreads, s, pdl, a, 0);
   if (fork) {
     cudaStreamWaitEvent(s, ss.join, 0);
   } else {
@@ -52,12 +47,12 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     launch_lepton<R>(a, nb[1], s);
     if (ss.tev) cudaEventRecord(ss.tev[5], s);
   }
-  k_scan<false><<<1, kScanThreads, 0, s>>>(a, 1);
+  k_scan<R, false><<<1, kScanThreads, 0, s>>>(a, 1);
   if constexpr (sizeof(R) == 4) {
-    if (a.flags & QED_F_MLP) launch_k(k_ncs_ev_mlp<false>, nb[2] * 2, kMlpRows, s, pdl, a);
-    else launch_k(k_ncs_ev<R, false>, nb[2], kTile, s, pdl, a);
+    if (a.flags & QED_F_MLP) launch_k(k_events_mlp<false>, nb[2] * 2, kMlpRows, s, pdl, a);
+    else launch_k(k_events<R, false>, nb[2], kTile, s, pdl, a);
   } else {
-    launch_k(k_ncs_ev<R, false>, nb[2], kTile, s, pdl, a);
+    launch_k(k_events<R, false>, nb[2], kTile, s, pdl, a);
   }
   if (ss.tev) cudaEventRecord(ss.tev[3], s);
   const cudaError_t e = cudaGetLastError();
