@@ -48,6 +48,9 @@ typedef enum {
 #define QED_STATUS_LOG_FULL 8u     /* a tile's events were not logged (event log full).  The
                                       logs hold one event per particle of capacity, the most
                                       a step can produce, so this bit marks a library fault */
+#define QED_STATUS_SHARD 16u       /* qed_step_end: the gathered counts at this rank's place
+                                      differ from the ones qed_step_begin reported (ids of
+                                      the ranks would collide)                               */
 
 typedef enum { QED_ELECTRON = 0, QED_POSITRON = 1, QED_PHOTON = 2 } qed_species;
 
@@ -261,6 +264,30 @@ qed_status qed_get_next_id(qed_ctx *ctx, uint64_t *next_id, void *stream);
 qed_status qed_step(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed_particles *ph,
                     const qed_fields *f, double t, double dt, uint64_t seed, uint32_t step,
                     uint32_t flags, qed_step_stats *dev_stats, void *stream);
+
+/* A step of one part of a population that several ranks (one process per GPU) step
+ * together, each its own particles (Sec. IV: particles are independent given the fields).
+ * The only exchange is the births' ids, so that they stay unique and gapless across the
+ * ranks: a step numbers its births as one sequential pass over all ranks' particles in rank
+ * order would (every rank's pairs, then every e- emission, then every e+ emission; within a
+ * rank, qed_step's order).  Every rank keeps the same id counter.
+ *   qed_step_begin: the step up to its event kernel (both streaming passes and the scans;
+ *     same arguments and validation as qed_step); writes this rank's three birth counts
+ *     (pairs, e- emissions, e+ emissions; uint64) to dev_counts (device memory) on stream.
+ *   Then the caller gathers every rank's dev_counts into dev_all (world x 3, rank-major;
+ *     an all-gather of 24 bytes per rank, e.g. ncclAllGather on the same stream).
+ *   qed_step_end: the births with ids offset by the ranks before this one, and the rest of
+ *     the step; the counter advances by all ranks' births.  Sets QED_STATUS_SHARD if
+ *     dev_all at this rank's place is not what qed_step_begin wrote.
+ * With world = 1 the two calls equal one qed_step.  Between them the context, the particle
+ * sets and dev_counts must stay as they are; no other step on the context.
+ * Errors: as qed_step; QED_ERR_INVALID_ARG (qed_step_end without qed_step_begin, NULL
+ * dev_counts / dev_all, rank outside [0, world), a second qed_step_begin before the end,
+ * per-kernel timing on). */
+qed_status qed_step_begin(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed_particles *ph,
+                          const qed_fields *f, double t, double dt, uint64_t seed, uint32_t step,
+                          uint32_t flags, qed_step_stats *dev_stats, uint64_t *dev_counts, void *stream);
+qed_status qed_step_end(qed_ctx *ctx, const uint64_t *dev_all, int rank, int world, void *stream);
 
 /* Matter for QED_F_BREMS and QED_F_BH (paper Sec. III E, high-energy bremsstrahlung and
  * the Bethe-Heitler pair creation that "follows a similar process"): atoms of charge Z at

@@ -104,6 +104,12 @@ def lib():
             L.or_step.argtypes = [C.c_void_p, C.POINTER(Particles), C.POINTER(Particles),
                                   C.POINTER(Particles), C.POINTER(Fields), d, d, u64,
                                   C.c_uint32, C.c_uint32, C.POINTER(Stats)]
+            L.or_step_decide.argtypes = [C.c_void_p, C.POINTER(Particles), C.POINTER(Particles),
+                                         C.POINTER(Particles), C.POINTER(Fields), d, d, u64,
+                                         C.c_uint32, C.c_uint32, C.POINTER(Stats), C.POINTER(u64)]
+            L.or_step_commit.argtypes = [C.c_void_p, C.POINTER(Particles), C.POINTER(Particles),
+                                         C.POINTER(Particles), C.POINTER(u64), C.POINTER(Stats)]
+            L.or_shard_bases.argtypes = [u64, C.POINTER(u64), C.c_int, C.c_int, C.POINTER(u64)]
             L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
             L.or_uniforms.argtypes = [u64, u64, C.c_uint32, C.c_uint32, pd]
             L.or_besselk_scaled.argtypes = [d, pd]
@@ -209,6 +215,21 @@ def make_fields(kind=FIELD_NONE, circular=0, a0=0.0, phi0=0.0, length=1.0, w0=1.
     return f
 
 
+def _stats_dict(st) -> dict:
+    return {"n_ncs_e": st.n_ncs[0], "n_ncs_p": st.n_ncs[1], "n_nbw": st.n_nbw,
+            "n_range": st.n_range, "n_drop": st.n_drop, "n_near": st.n_near, "n_coarse": st.n_coarse,
+            "n_brems_e": st.n_brems[0], "n_brems_p": st.n_brems[1], "n_bh": st.n_bh}
+
+
+def shard_bases(next_id: int, all_counts, rank: int) -> np.ndarray:
+    """or_shard_bases: the 4 id bases of rank ``rank`` from every rank's 3 counts."""
+    a = np.ascontiguousarray(np.asarray(all_counts, dtype=np.uint64).reshape(-1, 3))
+    out = np.zeros(4, dtype=np.uint64)
+    lib().or_shard_bases(int(next_id), a.ctypes.data_as(C.POINTER(C.c_uint64)), int(rank), int(a.shape[0]),
+                         out.ctypes.data_as(C.POINTER(C.c_uint64)))
+    return out
+
+
 class Oracle:
     """Owns one oracle context (tables + id counter)."""
 
@@ -236,9 +257,31 @@ class Oracle:
         self.L.or_step(self.ctx, e.struct(), pos.struct(), ph.struct(), C.byref(fields),
                        float(t), float(dt), int(seed), int(step), int(flags), C.byref(st))
         e.sync(); pos.sync(); ph.sync()
-        return {"n_ncs_e": st.n_ncs[0], "n_ncs_p": st.n_ncs[1], "n_nbw": st.n_nbw,
-                "n_range": st.n_range, "n_drop": st.n_drop, "n_near": st.n_near, "n_coarse": st.n_coarse,
-                "n_brems_e": st.n_brems[0], "n_brems_p": st.n_brems[1], "n_bh": st.n_bh}
+        return _stats_dict(st)
+
+    def step_decide(self, e, pos, ph, fields, t, dt, seed, step, flags):
+        """Every decision of one step; returns (counts, stats): counts = (pairs, e- emissions,
+        e+ emissions), held until step_commit."""
+        st = Stats()
+        cnt = np.zeros(3, dtype=np.uint64)
+        self.L.or_step_decide(self.ctx, e.struct(), pos.struct(), ph.struct(), C.byref(fields),
+                              float(t), float(dt), int(seed), int(step), int(flags), C.byref(st),
+                              cnt.ctypes.data_as(C.POINTER(C.c_uint64)))
+        e.sync(); pos.sync(); ph.sync()
+        return cnt, _stats_dict(st)
+
+    def step_commit(self, e, pos, ph, bases=None):
+        """The births of the decided step, numbered from ``bases`` (4 ids, or_step_commit)."""
+        st = Stats()
+        b = None
+        if bases is not None:
+            b = np.ascontiguousarray(bases, dtype=np.uint64)
+        r = self.L.or_step_commit(self.ctx, e.struct(), pos.struct(), ph.struct(),
+                                  b.ctypes.data_as(C.POINTER(C.c_uint64)) if b is not None else None, C.byref(st))
+        if r != 0:
+            raise RuntimeError("or_step_commit without a decided step")
+        e.sync(); pos.sync(); ph.sync()
+        return _stats_dict(st)
 
     def set_threads(self, n: int) -> int:
         """Threads of the particle loops of a step (OpenMP); returns the count in effect."""
@@ -417,6 +460,22 @@ class Sim:
             self.t += self.dt
             self.step_no += 1
         return tot
+
+    def decide(self, flags):
+        """One step's decisions (Oracle.step_decide); the clock advances at commit."""
+        return self.o.step_decide(self.e, self.pos, self.ph, self.fields, self.t, self.dt, self.seed,
+                                  self.step_no, flags)
+
+    def commit(self, bases=None):
+        s = self.o.step_commit(self.e, self.pos, self.ph, bases)
+        self.t += self.dt
+        self.step_no += 1
+        return s
+
+    def load(self, st: dict):
+        """Replace the particle arrays (e.g. reordered) and the id counter."""
+        self.e.load(st["e"]); self.pos.load(st["pos"]); self.ph.load(st["ph"])
+        self.o.set_next_id(int(st["next_id"]))
 
     def state(self):
         return {"e": self.e.view(), "pos": self.pos.view(), "ph": self.ph.view(),

@@ -30,6 +30,9 @@
  *                           equation of a beam along -z, is flat and Gaussian at its
  *                           focus, carries the same transverse power at every z, and
  *                           keeps |E_perp| constant when circular
+ *   sharded ids ........... or_shard_bases against its closed form for three ranks (the
+ *                           id blocks tile the range); decide + commit = or_step; two
+ *                           ranks = one process stepping the population in rank order
  */
 #include "qed_oracle.h"
 
@@ -92,6 +95,11 @@ struct or_ctx {
   int threads;                                  /* particle-loop threads of or_step (OpenMP) */
   uint64_t nlog, logcap;
   uint64_t *log_id; uint32_t *log_step, *log_kind; double *log_margin;
+  /* a step decided by or_step_decide and not yet committed: the decayed photons' slots
+     (index order), the pairs they create, the photons the leptons emit (e- then e+) */
+  int pending;
+  void *p_be, *p_bp, *p_bg;
+  uint64_t *p_dec, p_nnbw, p_nncs, p_nncs_e;
 };
 
 /* ======================================================================= *
@@ -649,6 +657,7 @@ or_ctx *or_ctx_create(void) {
 void or_ctx_destroy(or_ctx *c) {
   if (!c) return;
   free(c->log_id); free(c->log_step); free(c->log_kind); free(c->log_margin);
+  free(c->p_be); free(c->p_bp); free(c->p_bg); free(c->p_dec);   /* an uncommitted step */
   free(c);
 }
 void or_set_next_id(or_ctx *c, uint64_t id) { c->next_id = id; c->nlog = 0; }
@@ -1646,12 +1655,23 @@ static int or_lepton(or_ctx *c, or_particles *L, uint64_t i, double q, const or_
  *  at the next step.  Ids: NBW pairs first (photon order, e- then e+),     *
  *  then NCS photons (e- order, then e+ order).  Decayed photons leave the  *
  *  array: their slots below the new count are refilled from the tail.      *
+ *  or_step_decide takes every decision of a step and holds the births;     *
+ *  or_step_commit applies them with the ids given (or the sequential ones) *
  * ======================================================================= */
-int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, const or_fields *f, double t, double dt,
-            uint64_t seed, uint32_t step, uint32_t flags, or_stats *st) {
+static void or_drop_pending(or_ctx *c) {
+  if (!c->pending) return;
+  free(c->p_be); free(c->p_bp); free(c->p_bg); free(c->p_dec);
+  c->p_be = c->p_bp = c->p_bg = NULL;
+  c->p_dec = NULL;
+  c->pending = 0;
+}
+
+int or_step_decide(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, const or_fields *f, double t,
+                   double dt, uint64_t seed, uint32_t step, uint32_t flags, or_stats *st, uint64_t counts[3]) {
+  or_drop_pending(c);
   uint64_t nph = ph ? ph->n : 0, ne = e ? e->n : 0, np = pos ? pos->n : 0;
   /* every particle's outcome goes to its own slot (index i), so the particle loops may run
-     in any order or in parallel; births are then appended in index order below */
+     in any order or in parallel; the births are then listed in index order below */
   or_lep_birth *be = (or_lep_birth *)malloc(sizeof(or_lep_birth) * (nph + 1));
   or_lep_birth *bp = (or_lep_birth *)malloc(sizeof(or_lep_birth) * (nph + 1));
   or_ph_birth *bg = (or_ph_birth *)malloc(sizeof(or_ph_birth) * (ne + np + 1));
@@ -1696,7 +1716,7 @@ int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, con
   free(ts);
   /* decays and emissions in index order: pair births (photon order), NCS photons (e- then
      e+ order) */
-  uint64_t nnbw = 0, nncs = 0;
+  uint64_t nnbw = 0, nncs = 0, nncs_e = 0;
   uint64_t *dec = (uint64_t *)malloc(sizeof(uint64_t) * (nph + 1));
   for (uint64_t i = 0; i < nph; ++i)
     if (dflag[i]) {
@@ -1704,11 +1724,40 @@ int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, con
       dec[nnbw++] = i;
     }
   for (uint64_t i = 0; i < ne + np; ++i)
-    if (eflag[i]) bg[nncs++] = bg[i];
+    if (eflag[i]) {
+      bg[nncs++] = bg[i];
+      if (i < ne) nncs_e++;
+    }
   free(dflag); free(eflag);
+  c->pending = 1;
+  c->p_be = be; c->p_bp = bp; c->p_bg = bg; c->p_dec = dec;
+  c->p_nnbw = nnbw; c->p_nncs = nncs; c->p_nncs_e = nncs_e;
+  if (counts) { counts[0] = nnbw; counts[1] = nncs_e; counts[2] = nncs - nncs_e; }
+  return 0;
+}
+
+int or_step_commit(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, const uint64_t *bases,
+                   or_stats *st) {
+  if (!c->pending) return -1;
+  or_lep_birth *be = (or_lep_birth *)c->p_be, *bp = (or_lep_birth *)c->p_bp;
+  or_ph_birth *bg = (or_ph_birth *)c->p_bg;
+  uint64_t *dec = c->p_dec;
+  const uint64_t nnbw = c->p_nnbw, nncs = c->p_nncs, nncs_e = c->p_nncs_e;
+  /* the ids: pairs from b[0] (2 a pair), e- emissions from b[1], e+ emissions from b[2];
+     the counter continues at b[3].  Alone, they follow one another from next_id. */
+  uint64_t b[4];
+  if (bases) {
+    for (int k = 0; k < 4; ++k) b[k] = bases[k];
+  } else {
+    b[0] = c->next_id;
+    b[1] = b[0] + 2 * nnbw;
+    b[2] = b[1] + nncs_e;
+    b[3] = b[2] + (nncs - nncs_e);
+  }
   /* removal of decayed photons: with M = n - (decays), the k-th decayed slot below M
      receives the k-th surviving photon at or above M (both in index order) */
   if (ph) {
+    uint64_t nph = ph->n;
     uint64_t M = nph - nnbw, H = 0;
     while (H < nnbw && dec[H] < M) H++;
     uint64_t q = H, j = M;
@@ -1723,15 +1772,13 @@ int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, con
     }
     ph->n = M;
   }
-  free(dec);
   /* append */
-  uint64_t id = c->next_id;
   for (uint64_t k = 0; k < nnbw; ++k) {
     or_lep_birth *src[2] = {&be[k], &bp[k]};
     or_particles *dst[2] = {e, pos};
     for (int s = 0; s < 2; ++s) {
       or_particles *L = dst[s];
-      uint64_t myid = id + 2 * k + s;
+      uint64_t myid = b[0] + 2 * k + s;
       if (!L || L->n >= L->cap) { if (st) st->n_drop++; continue; }
       uint64_t j = L->n++;
       L->x[j] = src[s]->x[0]; L->y[j] = src[s]->x[1]; L->z[j] = src[s]->x[2];
@@ -1740,17 +1787,40 @@ int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, con
       L->w[j] = src[s]->w; L->id[j] = myid;
     }
   }
-  id += 2 * nnbw;
   for (uint64_t k = 0; k < nncs; ++k) {
     if (!ph || ph->n >= ph->cap) { if (st) st->n_drop++; continue; }
     uint64_t j = ph->n++;
     ph->x[j] = bg[k].x[0]; ph->y[j] = bg[k].x[1]; ph->z[j] = bg[k].x[2];
     ph->px[j] = bg[k].k[0]; ph->py[j] = bg[k].k[1]; ph->pz[j] = bg[k].k[2];
     ph->s1[j] = bg[k].xi[0]; ph->s2[j] = bg[k].xi[1]; ph->s3[j] = bg[k].xi[2];
-    ph->theta[j] = bg[k].th; ph->w[j] = bg[k].w; ph->id[j] = id + k;
+    ph->theta[j] = bg[k].th; ph->w[j] = bg[k].w;
+    ph->id[j] = k < nncs_e ? b[1] + k : b[2] + (k - nncs_e);
   }
-  id += nncs;
-  c->next_id = id;
-  free(be); free(bp); free(bg);
+  c->next_id = b[3];
+  or_drop_pending(c);
   return 0;
+}
+
+int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph, const or_fields *f, double t, double dt,
+            uint64_t seed, uint32_t step, uint32_t flags, or_stats *st) {
+  or_step_decide(c, e, pos, ph, f, t, dt, seed, step, flags, st, NULL);
+  return or_step_commit(c, e, pos, ph, NULL, st);
+}
+
+/* Ids of one rank's births when R ranks step disjoint parts of one population: the step's
+   births are numbered as one sequential pass over the ranks' particles in rank order would
+   number them (all pairs, then every e- emission, then every e+ emission), so that the ids
+   are unique and gapless across the ranks.  all: R x 3 counts (pairs, e- emissions, e+
+   emissions), rank-major; out: the bases of or_step_commit. */
+void or_shard_bases(uint64_t next_id, const uint64_t *all, int rank, int world, uint64_t out[4]) {
+  uint64_t before[3] = {0, 0, 0}, tot[3] = {0, 0, 0};
+  for (int q = 0; q < world; ++q)
+    for (int k = 0; k < 3; ++k) {
+      tot[k] += all[3 * q + k];
+      if (q < rank) before[k] += all[3 * q + k];
+    }
+  out[0] = next_id + 2 * before[0];
+  out[1] = next_id + 2 * tot[0] + before[1];
+  out[2] = next_id + 2 * tot[0] + tot[1] + before[2];
+  out[3] = next_id + 2 * tot[0] + tot[1] + tot[2];
 }

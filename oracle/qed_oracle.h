@@ -134,6 +134,20 @@ uint64_t or_near_log(or_ctx *c, uint64_t *ids, uint32_t *steps, uint32_t *kinds,
 int or_step(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph,
             const or_fields *f, double t, double dt, uint64_t seed, uint32_t step,
             uint32_t flags, or_stats *st);
+/* or_step in two parts: every decision of the step (the particles are updated in place,
+ * the births held); counts = (pairs, e- emissions, e+ emissions) when non-NULL.  Then the
+ * births with the ids bases[0] + 2k + s (pair k, s = 0 e-, 1 e+), bases[1] + k (the k-th
+ * e- emission), bases[2] + k (e+), and the counter at bases[3]; NULL bases number them from
+ * the counter in that order (or_step).  Commit returns -1 without a decided step. */
+int or_step_decide(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph,
+                   const or_fields *f, double t, double dt, uint64_t seed, uint32_t step,
+                   uint32_t flags, or_stats *st, uint64_t counts[3]);
+int or_step_commit(or_ctx *c, or_particles *e, or_particles *pos, or_particles *ph,
+                   const uint64_t *bases, or_stats *st);
+/* the bases of rank `rank` of `world` ranks stepping disjoint parts of one population:
+ * its births are numbered as one pass over all ranks' particles in rank order would number
+ * them; all = world x 3 counts of or_step_decide, rank-major */
+void or_shard_bases(uint64_t next_id, const uint64_t *all, int rank, int world, uint64_t out[4]);
 
 /* Yee leapfrog halves (Sec. II B): B -= dt curl E;  E += dt (curl B - J) */
 void or_fdtd_b(const or_grid *g, double dt);

@@ -27,11 +27,13 @@ QED_F_DEPOSIT = 1024
 QED_F_BREMS, QED_F_BH = 2048, 4096
 QED_FDTD_B, QED_FDTD_E = 0, 1
 QED_STATUS_CAPACITY, QED_STATUS_TIMEOUT, QED_STATUS_TABLE_RANGE, QED_STATUS_LOG_FULL = 1, 2, 4, 8
+QED_STATUS_SHARD = 16
 FIELD_KIND = {"none": 0, "uniform": 1, "plane": 2, "gauss": 3, "grid2d": 4}
 
 ABI_FUNCTIONS = ("qed_init_tables", "qed_destroy", "particles_create", "particles_count",
                  "particles_set_count", "particles_destroy", "qed_set_next_id", "qed_get_next_id",
-                 "qed_step", "qed_step_host", "qed_step_static", "qed_read_status", "qed_copy_table",
+                 "qed_step", "qed_step_host", "qed_step_static", "qed_step_begin", "qed_step_end",
+                 "qed_read_status", "qed_copy_table",
                  "qed_set_timing", "qed_get_timing", "qed_diag", "qed_ctx_share", "qed_batch_create",
                  "qed_batch_step", "qed_batch_run", "qed_batch_clock", "qed_batch_get_config",
                  "qed_batch_set_config", "qed_batch_tune", "qed_batch_destroy", "qed_mlp_train",
@@ -116,6 +118,8 @@ def lib():
                                     C.POINTER(qed_soa), C.POINTER(u64), C.POINTER(qed_fields), d, d, u64,
                                     u32, u32, vp]
         L.qed_step_static.argtypes = [vp, vp, vp, vp, C.POINTER(qed_fields), d, d, u64, u32, u32, vp, vp]
+        L.qed_step_begin.argtypes = [vp, vp, vp, vp, C.POINTER(qed_fields), d, d, u64, u32, u32, vp, vp, vp]
+        L.qed_step_end.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         L.qed_read_status.argtypes = [vp, C.POINTER(u32), C.c_int, vp]
         L.qed_copy_table.argtypes = [vp, C.c_int, C.POINTER(C.c_double), u64, C.POINTER(u64), vp]
         L.qed_philox_blocks.argtypes = [vp, u64, vp, u64, vp]
@@ -303,6 +307,20 @@ def qed_get_next_id(ctx, stream=None) -> int:
 def qed_step(ctx, e, pos, ph, fields: qed_fields, t, dt, seed, step, flags, dev_stats=None, stream=None):
     _check(lib().qed_step(ctx, e, pos, ph, C.byref(fields), float(t), float(dt), int(seed), int(step),
                           int(flags), dev_stats, _stream(stream)), "qed_step")
+
+
+def qed_step_begin(ctx, e, pos, ph, fields: qed_fields, t, dt, seed, step, flags, dev_counts, dev_stats=None,
+                   stream=None):
+    """First half of a sharded step: writes this rank's (pairs, e- emissions, e+ emissions)
+    to dev_counts (device pointer to 3 uint64)."""
+    _check(lib().qed_step_begin(ctx, e, pos, ph, C.byref(fields), float(t), float(dt), int(seed), int(step),
+                                int(flags), dev_stats, dev_counts, _stream(stream)), "qed_step_begin")
+
+
+def qed_step_end(ctx, dev_all, rank, world, stream=None):
+    """Second half: births numbered after the ranks before ``rank`` (dev_all: device pointer
+    to world x 3 uint64, every rank's counts, rank-major)."""
+    _check(lib().qed_step_end(ctx, dev_all, int(rank), int(world), _stream(stream)), "qed_step_end")
 
 
 def qed_step_static(ctx, e, pos, ph, fields: qed_fields, t, dt, seed, step, flags, dev_stats=None, stream=None):
@@ -552,6 +570,25 @@ class Simulation:
             self.t += self.dt
             self.step_no += 1
 
+    def step_begin(self, flags, stream=None):
+        """qed_step_begin of the next step; returns this rank's counts (3, int64, device)."""
+        torch = self.torch
+        self._counts = torch.zeros(3, dtype=torch.int64, device="cuda")
+        qed_step_begin(self.ctx, self.e.handle, self.pos.handle, self.ph.handle, self.fields, self.t, self.dt,
+                       self.seed, self.step_no, flags, self._counts.data_ptr(), self.stats.data_ptr(), stream)
+        return self._counts
+
+    def step_end(self, all_counts, rank, world, stream=None):
+        """qed_step_end with every rank's counts (world x 3 int64 tensor, rank-major)."""
+        torch = self.torch
+        allc = all_counts.to(device="cuda", dtype=torch.int64).contiguous()
+        if allc.numel() != 3 * world:
+            raise ValueError("all_counts must hold world x 3 counts")
+        self._all = allc   # kept alive until the step has run
+        qed_step_end(self.ctx, allc.data_ptr(), rank, world, stream)
+        self.t += self.dt
+        self.step_no += 1
+
     def state(self) -> dict:
         self.torch.cuda.synchronize()
         return {"e": self.e.to_dict(), "pos": self.pos.to_dict(), "ph": self.ph.to_dict(),
@@ -657,3 +694,44 @@ class PicSimulation(Simulation):
     def field_arrays(self) -> dict:
         self.torch.cuda.synchronize()
         return {k: v.cpu().numpy().astype(np.float64) for k, v in self.yee.items()}
+
+
+# ---------------------------------------------------------------------------------
+# Several ranks (one process per GPU) stepping one population, each its own part.  The
+# step's only exchange is the births' id numbering (one all-gather of 3 counts per rank);
+# diagnostics are summed over the ranks at the end (one all-reduce).
+# ---------------------------------------------------------------------------------
+def shard_exchange(counts, group=None):
+    """Every rank's (pairs, e- emissions, e+ emissions) of this step: an all-gather of
+    ``counts`` (3 int64).  With NCCL the tensors stay on the device; with gloo they go
+    through host memory.  Returns a (world, 3) tensor on ``counts``' device."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    host = dist.get_backend(group) == "gloo"
+    src = counts.detach().to("cpu") if host else counts
+    out = [torch.empty_like(src) for _ in range(world)]
+    dist.all_gather(out, src, group=group)
+    return torch.stack(out).to(counts.device)
+
+
+def sharded_step(sim, flags, group=None, stream=None):
+    """One step of ``sim`` (a Simulation holding this rank's part) with ids numbered across
+    the ranks of ``group`` (qed_step_begin, shard_exchange, qed_step_end)."""
+    import torch.distributed as dist
+    c = sim.step_begin(flags, stream)
+    allc = shard_exchange(c, group)
+    sim.step_end(allc, dist.get_rank(group), dist.get_world_size(group), stream)
+
+
+def allreduce_hist(h, group=None):
+    """Sum of a histogram (any tensor) over the ranks of ``group``, in place; with gloo
+    through host memory.  Returns ``h``."""
+    import torch.distributed as dist
+    if dist.get_backend(group) == "gloo" and h.device.type != "cpu":
+        t = h.detach().cpu()
+        dist.all_reduce(t, group=group)
+        h.copy_(t)
+    else:
+        dist.all_reduce(h, group=group)
+    return h

@@ -422,6 +422,7 @@ qed_status check_fields(const qed_fields* f, const char* who) {
 static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
                                 const qed_fields* f, double dt, uint32_t flags, qed_precision* prec) {
   if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_step: invalid context");
+  if (c->pending) FAIL(QED_ERR_INVALID_ARG, "qed_step: a sharded step is between qed_step_begin and qed_step_end");
   if (!f) FAIL(QED_ERR_INVALID_ARG, "qed_step: fields is NULL");
   if (!(dt > 0.0) || !std::isfinite(dt)) FAIL(QED_ERR_INVALID_ARG, "qed_step: dt must be positive and finite");
   {
@@ -456,14 +457,10 @@ static qed_status validate_step(qed_ctx* c, qed_particles* e, qed_particles* pos
   return QED_OK;
 }
 
-extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
-                               const qed_fields* f, double t, double dt, uint64_t seed, uint32_t step,
-                               uint32_t flags, qed_step_stats* dev_stats, void* stream) {
-  const qedk::NvtxRange nvtx_range("qed_step");
-  qed_precision prec;
-  qed_status r = validate_step(c, e, pos, ph, f, dt, flags, &prec);
-  if (r != QED_OK) return r;
-  StepArgs a;
+// the launch arguments of one step on the context's scratch
+static void step_args(StepArgs& a, qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
+                      const qed_fields* f, double t, double dt, uint64_t seed, uint32_t step, uint32_t flags,
+                      qed_step_stats* dev_stats, qed_precision prec) {
   memset(&a, 0, sizeof(a));
   fill_ensemble(a.e0, e, pos, ph, f, t, seed, step, c->st, dev_stats);
   a.dt = dt;
@@ -480,6 +477,55 @@ extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos,
   }
   a.holes = c->holes;
   set_medium_args(a, c);
+}
+
+extern "C" qed_status qed_step_begin(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
+                                     const qed_fields* f, double t, double dt, uint64_t seed, uint32_t step,
+                                     uint32_t flags, qed_step_stats* dev_stats, uint64_t* dev_counts, void* stream) {
+  const qedk::NvtxRange nvtx_range("qed_step_begin");
+  qed_precision prec;
+  qed_status r = validate_step(c, e, pos, ph, f, dt, flags, &prec);
+  if (r != QED_OK) return r;
+  if (!dev_counts) FAIL(QED_ERR_INVALID_ARG, "qed_step_begin: dev_counts is NULL");
+  if (c->timing) FAIL(QED_ERR_INVALID_ARG, "qed_step_begin: per-kernel timing is on");
+  StepArgs& a = c->pend;
+  step_args(a, c, e, pos, ph, f, t, dt, seed, step, flags, dev_stats, prec);
+  a.shard_counts = reinterpret_cast<unsigned long long*>(dev_counts);
+  const int pi = prec == QED_PREC_F64 ? 0 : 1;
+  StreamSet ss{c->side, c->fork, c->join, nullptr};
+  r = launch_step(a, prec, c->nblk[pi], S(stream), ss, kStepBegin);
+  if (r != QED_OK) return r;
+  c->pend_prec = prec;
+  c->pending = 1;
+  return QED_OK;
+}
+
+extern "C" qed_status qed_step_end(qed_ctx* c, const uint64_t* dev_all, int rank, int world, void* stream) {
+  const qedk::NvtxRange nvtx_range("qed_step_end");
+  if (!c || !c->alive) FAIL(QED_ERR_NOT_INITIALIZED, "qed_step_end: invalid context");
+  if (!c->pending) FAIL(QED_ERR_INVALID_ARG, "qed_step_end: no step begun (qed_step_begin)");
+  if (!dev_all) FAIL(QED_ERR_INVALID_ARG, "qed_step_end: dev_all is NULL");
+  if (world < 1 || rank < 0 || rank >= world)
+    FAIL(QED_ERR_INVALID_ARG, "qed_step_end: rank %d outside [0, %d)", rank, world);
+  StepArgs& a = c->pend;
+  a.shard_all = reinterpret_cast<const unsigned long long*>(dev_all);
+  a.shard_rank = rank;
+  a.shard_world = world;
+  const int pi = c->pend_prec == QED_PREC_F64 ? 0 : 1;
+  StreamSet ss{c->side, c->fork, c->join, nullptr};
+  c->pending = 0;
+  return launch_step(a, c->pend_prec, c->nblk[pi], S(stream), ss, kStepEnd);
+}
+
+extern "C" qed_status qed_step(qed_ctx* c, qed_particles* e, qed_particles* pos, qed_particles* ph,
+                               const qed_fields* f, double t, double dt, uint64_t seed, uint32_t step,
+                               uint32_t flags, qed_step_stats* dev_stats, void* stream) {
+  const qedk::NvtxRange nvtx_range("qed_step");
+  qed_precision prec;
+  qed_status r = validate_step(c, e, pos, ph, f, dt, flags, &prec);
+  if (r != QED_OK) return r;
+  StepArgs a;
+  step_args(a, c, e, pos, ph, f, t, dt, seed, step, flags, dev_stats, prec);
   const int pi = prec == QED_PREC_F64 ? 0 : 1;
   // per-kernel timing runs the passes one after the other, so that each duration is the
   // kernel's own (no overlap of the lepton pass with the photon chain)

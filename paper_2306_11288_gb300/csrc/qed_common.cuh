@@ -301,6 +301,11 @@ struct DevState {
   unsigned long long n_nbw;          // this step: pairs created (ranked decays)
   unsigned long long n_ncs_tot;      // this step: ranked emissions
   unsigned long long n_hlow;         // this step: decayed photon slots below n_surv
+  unsigned long long n_ncs_e;        // this step: ranked emissions of e- (they rank first)
+  // this step, sharded (qed_step_end): added to the ids of pairs, of e- and of e+
+  // emissions, and to the id counter, so that the births of all ranks are numbered as one
+  // pass over the ranks in order; zero otherwise
+  unsigned long long id_add[4];
   unsigned long long cursor[2];      // this step: entries written to the NBW / NCS logs
   unsigned long long ev[8];          // this step: ncs_e, ncs_p, coarse (P > 0.1), range, drop, brems e-,
                                      // brems e+, Bethe-Heitler pairs

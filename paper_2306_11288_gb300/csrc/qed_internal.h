@@ -92,6 +92,11 @@ struct StepArgs {
   const float* med_tot;
   double med_nar2, med_lo, med_hi, med_kmin;
   int med_axis;
+  // sharded steps (qed_step_begin / qed_step_end): this rank's birth counts out, every
+  // rank's counts in (world x 3, rank-major)
+  unsigned long long* shard_counts;
+  const unsigned long long* shard_all;
+  int shard_rank, shard_world;
 };
 
 // side stream and events of one step.  side == nullptr runs everything on the caller's
@@ -105,7 +110,11 @@ struct StreamSet {
 
 // launches one step of one ensemble (a.e0); prec selects the instantiation; nblk = grid
 // sizes (photon, lepton, events)
-qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, const StreamSet& ss);
+// which part of a step launch_step runs: all of it, or the two halves of a sharded step
+// (up to the scans and the rank's birth counts / the id offsets and the event kernel)
+enum StepPart { kStepWhole = 0, kStepBegin = 1, kStepEnd = 2 };
+qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, const StreamSet& ss,
+                       StepPart part = kStepWhole);
 // fills one ensemble's arguments (sets may be NULL; t, step: the ensemble's clock)
 void fill_ensemble(EnsArgs& E, const qed_particles* e, const qed_particles* pos, const qed_particles* ph,
                    const qed_fields* f, double t, uint64_t seed, uint32_t step, DevState* st,
@@ -166,6 +175,9 @@ struct qed_ctx {
   size_t diag_bytes;
   void* sort_buf;                     // qed_sort_cells scratch (keys, indices, one array)
   size_t sort_bytes;
+  qedk::StepArgs pend;                // a sharded step between qed_step_begin and qed_step_end
+  qed_precision pend_prec;
+  int pending;
   void* med_buf;                      // medium tables (qed_set_medium)
   qed_medium med;
   int has_medium;

@@ -1516,6 +1516,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ S
       E.st->n_hlow = M == 0 ? 0ull : upper_bound_u32(a.holes + (kB ? base[e] : 0u), tot, M - 1);
     } else {
       E.st->n_ncs_tot = tot;
+      if constexpr (!kB) {   // the e- tiles come first: their events are the first ranks
+        const unsigned long long n0 = E.sp[0].present ? E.st->n_live[0] : 0ull;
+        const unsigned long long te = (n0 + kTile - 1) / kTile;
+        E.st->n_ncs_e = te < ntiles ? (unsigned long long)pre[te] : tot;
+      }
     }
   }
   if constexpr (kB) {
@@ -1549,7 +1554,7 @@ __device__ __noinline__ void nbw_event(const NbwRec<R>& rec, const EnsArgs& E, c
                                        unsigned long long rank, DevState* gst) {
   DevState* st = E.st;
   const unsigned long long ne0 = st->n_live[0], np0 = st->n_live[1];
-  const unsigned long long id0 = st->next_id;
+  const unsigned long long id0 = st->next_id + st->id_add[0];
   const V3<R> k = mk<R>(rec.kx, rec.ky, rec.kz);
   const V3<R> xi = mk<R>(rec.x1, rec.x2, rec.x3);
   const R wgt = rec.w;
@@ -1647,7 +1652,7 @@ template <typename R>
 __device__ __noinline__ void bh_event(const StepArgs& a, const NbwRec<R>& rec, const EnsArgs& E, unsigned long long rank,
                                       DevState* gst) {
   DevState* st = E.st;
-  const unsigned long long ne0 = st->n_live[0], np0 = st->n_live[1], id0 = st->next_id;
+  const unsigned long long ne0 = st->n_live[0], np0 = st->n_live[1], id0 = st->next_id + st->id_add[0];
   const double kx = (double)rec.kx, ky = (double)rec.ky, kz = (double)rec.kz;
   const R wgt = rec.w;
   const double om = sqrt(kx * kx + ky * ky + kz * kz);
@@ -1689,7 +1694,7 @@ __device__ __noinline__ void brems_event(const StepArgs& a, const NcsRec<R>& rec
   const SpeciesArgs& G = E.sp[2];
   const SpeciesArgs& L = E.sp[rec.species & 1u];
   const unsigned long long nsurv = st->n_surv;
-  const unsigned long long id0 = st->next_id + 2ull * st->n_nbw;
+  const unsigned long long id0 = st->next_id + 2ull * st->n_nbw + st->id_add[1u + (rec.species & 1u)];
   const unsigned long long nph0 = st->n_live[2];
   const unsigned long long i = rec.i;
   const double px = (double)ld<R>(L.px, i), py = (double)ld<R>(L.py, i), pz = (double)ld<R>(L.pz, i);
@@ -1762,7 +1767,7 @@ __device__ __forceinline__ void close_step(const StepArgs& a, bool births) {
       const unsigned long long nn = surv + ncs;
       v->n_live[2] = nn > E.sp[2].cap ? E.sp[2].cap : nn;
     }
-    v->next_id = v->next_id + 2ull * nbw + ncs;
+    v->next_id = v->next_id + 2ull * nbw + ncs + v->id_add[3];
     atomicAdd(&gst->processed, processed);
     if (E.user_stats) {
       E.user_stats->n_processed += processed;
@@ -1779,7 +1784,8 @@ __device__ __forceinline__ void close_step(const StepArgs& a, bool births) {
     }
     if (v->ev[3]) atomicOr(&gst->status, QED_STATUS_TABLE_RANGE);
     for (int q = 0; q < 8; ++q) v->ev[q] = 0;
-    v->n_nbw = 0; v->n_surv = 0; v->n_ncs_tot = 0; v->n_hlow = 0;
+    v->n_nbw = 0; v->n_surv = 0; v->n_ncs_tot = 0; v->n_hlow = 0; v->n_ncs_e = 0;
+    for (int q = 0; q < 4; ++q) v->id_add[q] = 0;
     if constexpr (kB) {
       // the ensemble's clock: the same operations as the host forms of a single step
       const double t = v->t + a.dt;
@@ -1807,7 +1813,7 @@ __device__ __noinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E, c
   DevState* st = E.st;
   const SpeciesArgs& G = E.sp[2];
   const unsigned long long nsurv = st->n_surv, nph0 = st->n_live[2];
-  const unsigned long long id0 = st->next_id + 2ull * st->n_nbw;
+  const unsigned long long id0 = st->next_id + 2ull * st->n_nbw + st->id_add[1u + (rec.species & 1u)];
   const SpeciesArgs& L = E.sp[rec.species & 1u];
   const unsigned long long i = rec.i;
   const V3<R> pn = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
@@ -1894,6 +1900,47 @@ __device__ __noinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E, c
       G.id[j] = id0 + rank;
     }
   }
+}
+
+// ---- sharded steps: one rank's birth counts; the id offsets from every rank's -------------
+// counts = (pairs, e- emissions, e+ emissions); without births (QED_F_NO_RECOIL,
+// QED_F_DROP_PHOTONS) the emissions take no ids and count zero
+static __global__ void k_shard_counts(const __grid_constant__ StepArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const DevState* st = a.e0.st;
+  const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
+  a.shard_counts[0] = st->n_nbw;
+  a.shard_counts[1] = births ? st->n_ncs_e : 0ull;
+  a.shard_counts[2] = births ? st->n_ncs_tot - st->n_ncs_e : 0ull;
+}
+
+// The step's births on all ranks numbered as one sequential pass over the ranks' particles
+// in rank order would number them: all pairs, then every e- emission, then every e+
+// emission.  With P, E, Q the counts of the ranks before this one and TP, TE, TQ the totals,
+// a pair k gets next + 2 (P + k) + s, an e- emission k next + 2 TP + E + k, an e+ emission k
+// next + 2 TP + TE + Q + k, and the counter moves to next + 2 TP + TE + TQ: the offsets
+// against this rank's own numbering go to id_add.  A rank whose gathered counts are not its
+// own sets QED_STATUS_SHARD (the ids would collide).
+static __global__ void k_shard_ids(const __grid_constant__ StepArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  DevState* st = a.e0.st;
+  const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
+  const unsigned long long own[3] = {st->n_nbw, births ? st->n_ncs_e : 0ull,
+                                     births ? st->n_ncs_tot - st->n_ncs_e : 0ull};
+  unsigned long long before[3] = {0ull, 0ull, 0ull}, tot[3] = {0ull, 0ull, 0ull};
+  for (int q = 0; q < a.shard_world; ++q)
+    for (int k = 0; k < 3; ++k) {
+      const unsigned long long v = a.shard_all[3 * q + k];
+      tot[k] += v;
+      if (q < a.shard_rank) before[k] += v;
+    }
+  for (int k = 0; k < 3; ++k)
+    if (a.shard_all[3 * a.shard_rank + k] != own[k]) atomicOr(&a.st->status, QED_STATUS_SHARD);
+  const unsigned long long dp = 2ull * (tot[0] - own[0]);   // unsigned: offsets wrap mod 2^64
+  st->id_add[0] = 2ull * before[0];
+  st->id_add[1] = dp + before[1];
+  st->id_add[2] = dp + tot[1] + before[2] - own[1];
+  st->id_add[3] = dp + (tot[1] + tot[2]) - (own[1] + own[2]);
 }
 
 // ---- the event kernel's tasks ----------------------------------------------------------

@@ -79,6 +79,10 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
     set_error("qed_step_static: invalid context");
     return QED_ERR_NOT_INITIALIZED;
   }
+  if (c->pending) {
+    set_error("qed_step_static: a sharded step is between qed_step_begin and qed_step_end");
+    return QED_ERR_INVALID_ARG;
+  }
   if (!f) {
     set_error("qed_step_static: fields is NULL");
     return QED_ERR_INVALID_ARG;

@@ -23,10 +23,36 @@ static void launch_lepton(const StepArgs& a, int grid, cudaStream_t s) {
   else k_lepton<R, false, true><<<grid, kTile, 0, s>>>(a);
 }
 
+static qed_status launch_status() {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("step launch failed: %s", cudaGetErrorString(e));
+    return QED_ERR_CUDA;
+  }
+  return QED_OK;
+}
+
+// the event kernel, which closes the step
 template <typename R>
-static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, const StreamSet& ss) {
+static qed_status launch_events(const StepArgs& a, const int* nb, cudaStream_t s, bool pdl, const StreamSet& ss) {
+  if constexpr (sizeof(R) == 4) {
+    if (a.flags & QED_F_MLP) launch_k(k_events_mlp<false>, nb[2] * 2, kMlpRows, s, pdl, a);
+    else launch_k(k_events<R, false>, nb[2], kTile, s, pdl, a);
+  } else {
+    launch_k(k_events<R, false>, nb[2], kTile, s, pdl, a);
+  }
+  if (ss.tev) cudaEventRecord(ss.tev[3], s);
+  return launch_status();
+}
+
+template <typename R>
+static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, const StreamSet& ss, StepPart part) {
   const bool fork = ss.side != nullptr;
   const bool pdl = ss.tev == nullptr;   // timing events between kernels would break the pairs
+  if (part == kStepEnd) {
+    k_shard_ids<<<1, 32, 0, s>>>(a);
+    return launch_events<R>(a, nb, s, pdl, ss);
+  }
   if (ss.tev) cudaEventRecord(ss.tev[0], s);
   if (fork) {
     cudaEventRecord(ss.fork, s);
@@ -48,23 +74,16 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     if (ss.tev) cudaEventRecord(ss.tev[5], s);
   }
   k_scan<R, false><<<1, kScanThreads, 0, s>>>(a, 1);
-  if constexpr (sizeof(R) == 4) {
-    if (a.flags & QED_F_MLP) launch_k(k_events_mlp<false>, nb[2] * 2, kMlpRows, s, pdl, a);
-    else launch_k(k_events<R, false>, nb[2], kTile, s, pdl, a);
-  } else {
-    launch_k(k_events<R, false>, nb[2], kTile, s, pdl, a);
+  if (part == kStepBegin) {
+    k_shard_counts<<<1, 32, 0, s>>>(a);
+    return launch_status();
   }
-  if (ss.tev) cudaEventRecord(ss.tev[3], s);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    set_error("step launch failed: %s", cudaGetErrorString(e));
-    return QED_ERR_CUDA;
-  }
-  return QED_OK;
+  return launch_events<R>(a, nb, s, pdl, ss);
 }
 
-qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, const StreamSet& ss) {
-  return prec == QED_PREC_F64 ? launch_t<double>(a, nblk, s, ss) : launch_t<float>(a, nblk, s, ss);
+qed_status launch_step(const StepArgs& a, qed_precision prec, const int* nblk, cudaStream_t s, const StreamSet& ss,
+                       StepPart part) {
+  return prec == QED_PREC_F64 ? launch_t<double>(a, nblk, s, ss, part) : launch_t<float>(a, nblk, s, ss, part);
 }
 
 qed_status step_grid_sizes(qed_precision prec, int* nblk) {

@@ -225,3 +225,41 @@ def slab(n=1_000_000, seed=5, gamma0=2000.0, spread=0.0, name="Au", thickness_mm
     return {"e": e, "pos": empty(), "ph": empty(True), "field": {"kind": "none"},
             "dt": dt_um * 1e-4 / LENGTH_UNIT_CM, "t0": 0.0, "seed": seed, "next_id": n,
             "medium": medium(name, thickness_mm, k_min), "name": f"slab_{name}_{thickness_mm:g}mm_g{gamma0:g}_n{n}"}
+
+
+# ---------------------------------------------------------------------------------
+# Sharding: a small mixed population (e-, e+, polarised photons) in a strong crossed field
+# where pairs and emissions happen every step, and its split over ranks
+# ---------------------------------------------------------------------------------
+def crossed(ne=400, npos=200, nph=600, E0=200.0, seed=1, dt=0.3):
+    """e- and e+ at gamma ~ 4000 along +z with random spins, photons of ~1.5 GeV with random
+    partial polarisation, in the uniform crossed field E = E0 x, B = -E0 y."""
+    rng = np.random.default_rng(seed)
+
+    def lep(n, first):
+        s = _sphere(rng, n)
+        p = rng.normal(size=(n, 3)) * 30 + np.array([0, 0, 4000.0])
+        return {"x": rng.normal(size=n), "y": rng.normal(size=n), "z": rng.uniform(0, 50, n),
+                "px": p[:, 0], "py": p[:, 1], "pz": p[:, 2], "s1": s[:, 0], "s2": s[:, 1], "s3": s[:, 2],
+                "w": rng.uniform(0.5, 2, n), "id": _ids(n, first)}
+    e, pos = lep(ne, 0), lep(npos, ne)
+    k = rng.normal(size=(nph, 3)) * 50 + np.array([0, 0, 3000.0])
+    xi = _sphere(rng, nph) * rng.uniform(0, 1, (nph, 1))
+    first = ne + npos
+    ph = {"x": rng.normal(size=nph), "y": rng.normal(size=nph), "z": rng.uniform(0, 50, nph), "px": k[:, 0],
+          "py": k[:, 1], "pz": k[:, 2], "s1": xi[:, 0], "s2": xi[:, 1], "s3": xi[:, 2],
+          "theta": rng.uniform(-3, 3, nph), "w": np.ones(nph), "id": _ids(nph, first)}
+    return {"e": e, "pos": pos, "ph": ph, "field": {"kind": "uniform", "E": (E0, 0, 0), "B": (0, -E0, 0)},
+            "dt": dt, "seed": seed + 4, "next_id": first + nph, "name": f"crossed_E{E0:g}_{ne}_{npos}_{nph}"}
+
+
+def shard(wl, rank, world):
+    """Rank `rank` of `world` takes a contiguous part of every species (the ranks' parts in
+    rank order are the whole population in its order); fields, clock and id counter are
+    every rank's."""
+    out = dict(wl)
+    for sp in ("e", "pos", "ph"):
+        n = len(wl[sp]["id"])
+        lo, hi = n * rank // world, n * (rank + 1) // world
+        out[sp] = {k: v[lo:hi] for k, v in wl[sp].items()}
+    return out
