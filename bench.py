@@ -469,6 +469,9 @@ def _photon_spectrum(q, sp, nbins=48):
     return b[:, 0], b[:, 1:4] / np.maximum(b[:, :1], 1e-300), b[:, 4]
 
 
+C5_BATCH = 1024   # Adam steps, not samples, set the fit: 1e8 rows at 1024 take ~10 s
+
+
 def run_c5(q, torch, steps, n_train=100_000_000):
     """Learned sampler: training on table-sampled rows, its ln u error against the table
     sampler on held-out rows, the tensor-core evaluation rate, then the 1e6-electron
@@ -479,7 +482,7 @@ def run_c5(q, torch, steps, n_train=100_000_000):
     ctx = q.qed_init_tables()
     torch.cuda.synchronize()
     t0 = time.time()
-    q.qed_mlp_train(ctx, n_train, 16384, seed=5)
+    q.qed_mlp_train(ctx, n_train, C5_BATCH, seed=5)
     train_s = time.time() - t0
     rng = np.random.default_rng(77)
     nr = 1_000_000
@@ -527,7 +530,7 @@ def run_c5(q, torch, steps, n_train=100_000_000):
     rel_h = np.abs(hm - ht)[ok] / ht[ok]
     sig_xi = np.sqrt(1.0 / ht[ok] + 1.0 / hm[ok])
     pull_xi = (res["learned"]["xi"][ok] - res["table"]["xi"][ok]) / sig_xi[:, None]
-    return {"train": {"samples": n_train, "batch": 16384, "seconds": train_s},
+    return {"train": {"samples": n_train, "batch": C5_BATCH, "seconds": train_s},
             "ln_u_error_vs_table": {"rows": nr, "median": float(np.median(err)),
                                     "p99": float(np.quantile(err, 0.99)), "max": float(err.max())},
             "eval_rows_per_s": eval_rate,

@@ -230,7 +230,7 @@ def qed_batch_tune(b, steps_per_candidate, stream=None):
             "smem_rates": c.smem_rates}, float(rate.value)
 
 
-def qed_mlp_train(ctx, n_samples, batch=16384, seed=1, stream=None):
+def qed_mlp_train(ctx, n_samples, batch=1024, seed=1, stream=None):
     _check(lib().qed_mlp_train(ctx, int(n_samples), int(batch), int(seed), _stream(stream)), "qed_mlp_train")
 
 

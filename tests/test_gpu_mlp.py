@@ -2,11 +2,12 @@
 
 * The training target (the table sampler's mixture inverse on the FP32 tables) against the
   oracle's mixture inverse on its own tables.
-* Tensor-core evaluation (tcgen05, BF16 hidden layer, FP32 accumulation in tensor memory)
-  against the numpy network with the same BF16 rounding, for given parameters.
+* Tensor-core evaluation (tcgen05, FP16 hidden layer, FP32 accumulation in tensor memory)
+  against the numpy network with the same FP16 rounding, for given parameters.
 * A short training run learns the target (median and tail errors in ln u), and a step with
-  QED_F_MLP reproduces the table path's photon spectrum and polarisation within the error
-  the sampler's own ln u error allows (independent draws: statistical bounds)."""
+  QED_F_MLP (its own training run) reproduces the photon spectrum and polarisation of the
+  table path and of the FP64 oracle within 3 sigma per bin (fixed seeds: the outcome is
+  reproducible)."""
 import math
 
 import numpy as np
@@ -60,13 +61,16 @@ def test_tensor_core_eval_matches_numpy_network(ctx):
     assert q.qed_read_status(ctx) == 0
 
 
+TRAIN = (20_000_000, 1024)   # ~20k Adam steps, a few seconds
+
+
 def test_training_learns_the_table_sampler(ctx):
-    q.qed_mlp_train(ctx, 20_000_000, 16384, seed=3)
+    q.qed_mlp_train(ctx, *TRAIN, seed=3)
     rows = _rows(20000, 11)
     got = q.mlp_apply(ctx, rows, "eval")
     tgt = q.mlp_apply(ctx, rows, "target")
     d = np.abs(got - tgt)
-    assert np.median(d) < 0.05 and np.quantile(d, 0.99) < 0.5, (np.median(d), np.quantile(d, 0.99))
+    assert np.median(d) < 0.004 and np.quantile(d, 0.99) < 0.03, (np.median(d), np.quantile(d, 0.99))
 
 
 def _spectrum(ph, bins):
@@ -77,7 +81,7 @@ def _spectrum(ph, bins):
 
 
 def test_step_with_learned_sampler(ctx, orc):
-    # needs the parameters of the previous test (module order)
+    q.qed_mlp_train(ctx, *TRAIN, seed=4)
     n = 8000
     out = {}
     for name, extra in (("table", 0), ("mlp", q.QED_F_MLP)):
@@ -92,11 +96,13 @@ def test_step_with_learned_sampler(ctx, orc):
     bins = np.geomspace(1.0, 2000.0, 13)
     ht, h3t = _spectrum(pt, bins)
     hm, h3m = _spectrum(pm, bins)
+    # weighted counts (weights 1 in config 1): Poisson errors of independent runs, which the
+    # same-seed pair (correlated) can only undercut
     sig = np.sqrt(ht + hm + 1e-9)
-    assert np.all(np.abs(ht - hm) <= 4.0 * sig + 0.03 * ht + 2), (ht, hm)
+    assert np.all(np.abs(ht - hm) <= 3.0 * sig), (ht, hm)
     m = (ht > 300) & (hm > 300)
     xt, xm = h3t[m] / ht[m], h3m[m] / hm[m]
-    assert np.all(np.abs(xt - xm) <= 4.0 * np.sqrt(1.0 / ht[m] + 1.0 / hm[m]) + 0.02)
+    assert np.all(np.abs(xt - xm) <= 3.0 * np.sqrt(1.0 / ht[m] + 1.0 / hm[m]))
     # against the FP64 oracle (independent seed): the same bounds
     import oracle
     wl = workloads.c1(n=n, seed=22)
@@ -104,6 +110,6 @@ def test_step_with_learned_sampler(ctx, orc):
     osim.run(450, q.QED_F_NCS | q.QED_F_SPIN)
     ho, h3o = _spectrum(osim.state()["ph"], bins)
     sig = np.sqrt(ho + hm + 1e-9)
-    assert np.all(np.abs(ho - hm) <= 4.0 * sig + 0.03 * ho + 2), (ho, hm)
+    assert np.all(np.abs(ho - hm) <= 3.0 * sig), (ho, hm)
     m = (ho > 300) & (hm > 300)
-    assert np.all(np.abs(h3o[m] / ho[m] - h3m[m] / hm[m]) <= 4.0 * np.sqrt(1.0 / ho[m] + 1.0 / hm[m]) + 0.02)
+    assert np.all(np.abs(h3o[m] / ho[m] - h3m[m] / hm[m]) <= 3.0 * np.sqrt(1.0 / ho[m] + 1.0 / hm[m]))
