@@ -336,11 +336,12 @@ qed_status qed_fdtd_advance(const qed_grid2d *g, int which, double dt, void *str
 /* Cell sort of one particle set on a 2D grid (async; no host synchronisation): the live
  * particles are reordered by 32x32-cell tile of `grid` (a QED_FIELD_GRID2D descriptor; only
  * its geometry is used) and, inside a tile, by cell (row-major); particles outside a
- * bounded grid go last; a periodic grid wraps positions.  Stable: particles of one cell keep
+ * bounded grid go last; a periodic grid wraps positions.  The cell of x is
+ * floor((x - x0) * (1/dx)), each operation rounded in double (likewise y).  Stable: particles of one cell keep
  * their order, so the result is deterministic.  Every array of the set is permuted (the
  * live part).  A PIC code sorts periodically: the gather and the deposition of a warp then
  * touch a few cache lines (Sec. II D, E: field and current interpolation on the grid).
- * Scratch (24 B per element of capacity plus 512 KB) is allocated on the context on first
+ * Scratch (48 B per element of capacity plus 512 KB) is allocated on the context on first
  * use and kept.  Errors: QED_ERR_INVALID_ARG (not a grid, set of another context, capacity
  * >= 2^32, grid too large for 32-bit keys), QED_ERR_NOT_INITIALIZED, QED_ERR_CUDA. */
 qed_status qed_sort_cells(qed_ctx *ctx, qed_particles *set, const qed_fields *grid, void *stream);

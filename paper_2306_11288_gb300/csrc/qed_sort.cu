@@ -22,27 +22,41 @@ namespace qedk {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortBlocks = 512;
+constexpr int kSortItems = 8;    // sub-tiles of 256 keys per scatter iteration
+constexpr int kGroup = 4;        // arrays gathered by one launch
 
 __device__ __forceinline__ unsigned long long sort_chunk(unsigned long long n) {
   const unsigned long long c = (n + kSortBlocks - 1) / kSortBlocks;
   return (c + kSortThreads - 1) / kSortThreads * kSortThreads;
 }
 
+// cell of a coordinate: floor((x - x0) * (1/dx)), both operations rounded in double, the
+// floor taken by the conversion itself (three FP64 operations, no division)
+__device__ __forceinline__ long long cell_index(double x, double x0, double inv) {
+  return __double2ll_rd((x - x0) * inv);
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_sort_keys(const unsigned long long* n_live, qed_fields f,
-                                                            const double* x, const double* y, unsigned int* key,
-                                                            unsigned int* idx, unsigned int key_out) {
+                                                            double inv_dx, double inv_dy, const double* x,
+                                                            const double* y, unsigned int* key, unsigned int* idx,
+                                                            unsigned int key_out) {
   const unsigned long long n = *n_live;
   const int tx = (f.nx + 31) >> 5;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    const double X = (x[i] - f.x0) / f.dx, Y = (y[i] - f.y0) / f.dy;
-    long long ci = (long long)floor(X), cj = (long long)floor(Y);
+    long long ci = cell_index(x[i], f.x0, inv_dx), cj = cell_index(y[i], f.y0, inv_dy);
     unsigned int k = key_out;
     if (f.periodic) {
-      ci %= f.nx; ci += ci < 0 ? f.nx : 0;
-      cj %= f.ny; cj += cj < 0 ? f.ny : 0;
+      // wrap: one period either way without a division, the general case with one
+      if (ci < 0 && ci >= -(long long)f.nx) ci += f.nx;
+      else if (ci >= f.nx && ci < 2ll * f.nx) ci -= f.nx;
+      else if (ci < 0 || ci >= f.nx) { ci %= f.nx; ci += ci < 0 ? f.nx : 0; }
+      if (cj < 0 && cj >= -(long long)f.ny) cj += f.ny;
+      else if (cj >= f.ny && cj < 2ll * f.ny) cj -= f.ny;
+      else if (cj < 0 || cj >= f.ny) { cj %= f.ny; cj += cj < 0 ? f.ny : 0; }
     }
-    if (ci >= 0 && ci < f.nx && cj >= 0 && cj < f.ny)   // NaN positions fail these tests too
+    // a NaN position converts to the most negative integer: outside
+    if (ci >= 0 && ci < f.nx && cj >= 0 && cj < f.ny)
       k = (unsigned int)((((cj >> 5) * tx + (ci >> 5)) << 10) + ((cj & 31) << 5) + (ci & 31));
     key[i] = k;
     idx[i] = (unsigned int)i;
@@ -61,97 +75,207 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const unsigned long 
   counts[threadIdx.x * kSortBlocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of 256 * kSortBlocks counts in place (one block of 1024 threads, each a
-// contiguous run of kPer counts: sum, block scan of the sums, then the run rewritten)
+// exclusive scan of the 256 * kSortBlocks counts in place, one block of 1024 threads, in
+// chunks of 8192: each thread takes 8 consecutive counts (two 16-byte loads, so a warp
+// reads 1 KB in one piece), a block scan of the thread sums, the running total carried
 __global__ void __launch_bounds__(1024) k_sort_scan(unsigned int* counts) {
-  constexpr int kN = 256 * kSortBlocks, kPer = kN / 1024;
+  constexpr int kN = 256 * kSortBlocks, kPer = 8, kChunk = 1024 * kPer;
+  static_assert(kN % kChunk == 0, "whole chunks");
   __shared__ unsigned int s_w[32];
-  unsigned int* c = counts + threadIdx.x * kPer;
-  unsigned int t = 0;
-  for (int j = 0; j < kPer; ++j) t += c[j];
+  __shared__ unsigned int s_run;
   const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned int incl = t;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned int u = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= (unsigned)o) incl += u;
-  }
-  if (lane == 31) s_w[warp] = incl;
+  if (threadIdx.x == 0) s_run = 0;
   __syncthreads();
-  if (warp == 0) {
-    unsigned int w = s_w[lane];
+  for (int base = 0; base < kN; base += kChunk) {
+    uint4* p = reinterpret_cast<uint4*>(counts + base + threadIdx.x * kPer);
+    const uint4 a = p[0], b = p[1];
+    unsigned int v[kPer] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    unsigned int t = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) t += v[j];
+    unsigned int incl = t;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned int u = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= (unsigned)o) w += u;
+      const unsigned int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += u;
     }
-    s_w[lane] = w;
-  }
-  __syncthreads();
-  unsigned int run = (warp ? s_w[warp - 1] : 0u) + incl - t;
-  for (int j = 0; j < kPer; ++j) {
-    const unsigned int v = c[j];
-    c[j] = run;
-    run += v;
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned int w = s_w[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int u = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= (unsigned)o) w += u;
+      }
+      s_w[lane] = w;
+    }
+    __syncthreads();
+    unsigned int run = s_run + (warp ? s_w[warp - 1] : 0u) + incl - t;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const unsigned int e = run;
+      run += v[j];
+      v[j] = e;
+    }
+    p[0] = make_uint4(v[0], v[1], v[2], v[3]);
+    p[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    __syncthreads();
+    if (threadIdx.x == 0) s_run += s_w[31];
+    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const unsigned long long* n_live, const unsigned int* kin,
-                                                               const unsigned int* iin, unsigned int* kout,
-                                                               unsigned int* iout, int shift,
-                                                               const unsigned int* offsets) {
-  __shared__ unsigned int s_off[256];
-  __shared__ unsigned int s_cnt[kSortThreads / 32][256];
-  const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  s_off[threadIdx.x] = offsets[threadIdx.x * kSortBlocks + blockIdx.x];
+// Stable scatter of one digit.  Every block walks its chunk in order, kIter keys per
+// iteration (the next iteration's keys in flight meanwhile); warp w owns the iteration's
+// keys w*256 .. w*256+255, kSortItems per lane (item j of lane l is key w*256 + 32 j + l):
+//  1. each warp ranks its keys in order: equal digits of one item are ranked with
+//     __match_any_sync and counted into the warp's own row of digit counters (warp-level
+//     sync only);
+//  2. one pass over (digit, warp) turns the counters into the staging position of every
+//     (digit, warp) run: digit starts (a scan over the digits), then the warps in order;
+//  3. the keys are staged in shared memory in digit order and written out in that order:
+//     a digit's keys go to consecutive global positions, so a warp writes runs.
+__global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const unsigned long long* n_live, const unsigned int* kin,
+                                                                  const unsigned int* iin, unsigned int* kout,
+                                                                  unsigned int* iout, int shift,
+                                                                  const unsigned int* offsets) {
+  constexpr int kWarps = kSortThreads / 32, kIter = kSortThreads * kSortItems;
+  __shared__ unsigned int s_off[256];                  // next global position of each digit
+  __shared__ int s_delta[256];                         // global position - staged position
+  __shared__ unsigned int s_wc[kWarps][256];           // per-warp digit counts, then run starts
+  __shared__ unsigned int s_w[kWarps];
+  __shared__ unsigned int s_k[kIter], s_i[kIter];
+  const unsigned int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
+  s_off[t] = offsets[t * kSortBlocks + blockIdx.x];
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) s_wc[w][t] = 0;
+  __syncthreads();
   const unsigned long long n = *n_live, c = sort_chunk(n);
   const unsigned long long b0 = blockIdx.x * c, b1 = b0 + c < n ? b0 + c : n;
-  for (unsigned long long base = b0; base < b1; base += kSortThreads) {
+  const unsigned int wbase = warp * (32u * kSortItems);
+  unsigned int nk[kSortItems], ni[kSortItems];
+  auto load = [&](unsigned long long base) {
 #pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) s_cnt[w][threadIdx.x] = 0;
-    __syncthreads();
-    const unsigned long long i = base + threadIdx.x;
-    const bool valid = i < b1;
-    unsigned int k = 0, ix = 0, d = 256u + lane;   // invalid lanes match only themselves
-    if (valid) {
-      k = kin[i];
-      ix = iin[i];
-      d = (k >> shift) & 255u;
+    for (int j = 0; j < kSortItems; ++j) {
+      const unsigned long long i = base + wbase + 32u * j + lane;
+      if (i < b1) {
+        nk[j] = kin[i];
+        ni[j] = iin[i];
+      }
     }
-    const unsigned int m = __match_any_sync(0xffffffffu, d);
-    const unsigned int rank = __popc(m & ((1u << lane) - 1u));
-    if (valid && rank == 0) s_cnt[warp][d] = __popc(m);
-    __syncthreads();
-    if (valid) {
-      unsigned int pos = s_off[d] + rank;
-      for (unsigned int w = 0; w < warp; ++w) pos += s_cnt[w][d];
-      kout[pos] = k;
-      iout[pos] = ix;
-    }
-    __syncthreads();
-    unsigned int add = 0;
+  };
+  if (b0 < b1) load(b0);
+  for (unsigned long long base = b0; base < b1; base += kIter) {
+    unsigned int k[kSortItems], ix[kSortItems], r[kSortItems];
 #pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) add += s_cnt[w][threadIdx.x];
-    s_off[threadIdx.x] += add;
+    for (int j = 0; j < kSortItems; ++j) {
+      k[j] = nk[j];
+      ix[j] = ni[j];
+    }
+    if (base + kIter < b1) load(base + kIter);
+    const unsigned int m_it = (unsigned int)(b1 - base < (unsigned long long)kIter ? b1 - base : kIter);
+    // 1. ranks inside the warp's run of each digit
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const bool valid = wbase + 32u * j + lane < m_it;
+      const unsigned int d = valid ? (k[j] >> shift) & 255u : 256u + lane;   // invalid lanes match only themselves
+      const unsigned int m = __match_any_sync(0xffffffffu, d);
+      const unsigned int below = __popc(m & ((1u << lane) - 1u));
+      if (valid) r[j] = s_wc[warp][d] + below;
+      __syncwarp();
+      if (valid && below == 0) s_wc[warp][d] += __popc(m);
+      __syncwarp();
+    }
+    __syncthreads();
+    // 2. staging starts: digit t's count over the warps, scanned over the digits
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) cnt += s_wc[w][t];
+    unsigned int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (unsigned)o) incl += u;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    unsigned int start = incl - cnt;
+    for (unsigned int w = 0; w < warp; ++w) start += s_w[w];
+    s_delta[t] = (int)s_off[t] - (int)start;
+    s_off[t] += cnt;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {   // the runs of digit t, warp by warp
+      const unsigned int v = s_wc[w][t];
+      s_wc[w][t] = start;
+      start += v;
+    }
+    __syncthreads();
+    // 3. staged in digit order, then out
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      if (wbase + 32u * j + lane < m_it) {
+        const unsigned int q = s_wc[warp][(k[j] >> shift) & 255u] + r[j];
+        s_k[q] = k[j];
+        s_i[q] = ix[j];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const unsigned int q = (unsigned int)(j * kSortThreads) + t;
+      if (q < m_it) {
+        const unsigned int kk = s_k[q];
+        const unsigned int g = (unsigned int)((int)q + s_delta[(kk >> shift) & 255u]);
+        kout[g] = kk;
+        iout[g] = s_i[q];
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s_wc[w][t] = 0;
     __syncthreads();
   }
 }
 
+// up to kGroup arrays of one element size per launch: gathered through the sorted indices
+// into the scratch (array j at tmp + j * cap), then copied back over the live elements
 template <typename T>
-__global__ void __launch_bounds__(kSortThreads) k_sort_copy(const unsigned long long* n_live, const T* src, T* dst) {
+struct SortGroup {
+  T* a[kGroup];
+  int na;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kSortThreads) k_sort_gather(const unsigned long long* n_live, SortGroup<T> g,
+                                                              T* tmp, unsigned long long cap, const unsigned int* idx) {
   const unsigned long long n = *n_live;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * blockDim.x)
-    dst[i] = src[i];
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned int s = idx[i];
+    T v[kGroup];
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j)
+      if (j < g.na) v[j] = g.a[j][s];
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j)
+      if (j < g.na) tmp[(unsigned long long)j * cap + i] = v[j];
+  }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSortThreads) k_sort_gather(const unsigned long long* n_live, const T* src, T* dst,
-                                                              const unsigned int* idx) {
+__global__ void __launch_bounds__(kSortThreads) k_sort_copy(const unsigned long long* n_live, const T* tmp,
+                                                            unsigned long long cap, SortGroup<T> g) {
   const unsigned long long n = *n_live;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * blockDim.x)
-    dst[i] = src[idx[i]];
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    T v[kGroup];
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j)
+      if (j < g.na) v[j] = tmp[(unsigned long long)j * cap + i];
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j)
+      if (j < g.na) g.a[j][i] = v[j];
+  }
 }
 
 }  // namespace qedk
@@ -185,9 +309,9 @@ extern "C" qed_status qed_sort_cells(qed_ctx* c, qed_particles* set, const qed_f
   int bits = 1;
   while (bits < 32 && (1ull << bits) <= key_out) ++bits;
   const int passes = (bits + 7) / 8;
-  // scratch: two (key, index) buffers, the largest element of the set, the digit counts
+  // scratch: two (key, index) buffers, kGroup arrays of the largest element, the digit counts
   const size_t cap = set->cap ? set->cap : 1;
-  const size_t need = 16 * cap + 8 * cap + sizeof(unsigned int) * 256 * kSortBlocks;
+  const size_t need = 16 * cap + 8 * kGroup * cap + sizeof(unsigned int) * 256 * kSortBlocks;
   if (c->sort_bytes < need) {
     SCK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
     if (c->sort_buf) cudaFree(c->sort_buf);
@@ -200,14 +324,15 @@ extern "C" qed_status qed_sort_cells(qed_ctx* c, qed_particles* set, const qed_f
   unsigned int* key[2] = {reinterpret_cast<unsigned int*>(b), reinterpret_cast<unsigned int*>(b + 4 * cap)};
   unsigned int* idx[2] = {reinterpret_cast<unsigned int*>(b + 8 * cap), reinterpret_cast<unsigned int*>(b + 12 * cap)};
   void* tmp = b + 16 * cap;
-  unsigned int* counts = reinterpret_cast<unsigned int*>(b + 24 * cap);
+  unsigned int* counts = reinterpret_cast<unsigned int*>(b + (16 + 8 * kGroup) * cap);
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const unsigned long long* n_live = &c->st->n_live[set->species];
   int dev = 0, sms = 0;
   SCK(cudaGetDevice(&dev));
   SCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid_n = sms * 8;
-  k_sort_keys<<<grid_n, kSortThreads, 0, s>>>(n_live, *grid, static_cast<const double*>(set->soa.x),
+  k_sort_keys<<<grid_n, kSortThreads, 0, s>>>(n_live, *grid, 1.0 / grid->dx, 1.0 / grid->dy,
+                                               static_cast<const double*>(set->soa.x),
                                                static_cast<const double*>(set->soa.y), key[0], idx[0], key_out);
   int cur = 0;
   for (int p = 0; p < passes; ++p) {
@@ -223,23 +348,34 @@ extern "C" qed_status qed_sort_cells(qed_ctx* c, qed_particles* set, const qed_f
                    set->soa.s2, set->soa.s3, set->soa.w, set->soa.id, set->soa.theta};
   const size_t esz[12] = {8, 8, 8, r, r, r, r, r, r, r, 8, r};
   const int na = set->species == QED_PHOTON ? 12 : 11;
-  for (int k = 0; k < na; ++k) {
-    if (!arr[k]) continue;
-    if (esz[k] == 8) {
-      k_sort_gather<unsigned long long><<<grid_n, kSortThreads, 0, s>>>(
-          n_live, static_cast<const unsigned long long*>(arr[k]), static_cast<unsigned long long*>(tmp), order);
-    } else {
-      k_sort_gather<unsigned int><<<grid_n, kSortThreads, 0, s>>>(n_live, static_cast<const unsigned int*>(arr[k]),
-                                                                 static_cast<unsigned int*>(tmp), order);
-    }
-    // the live part back into the caller's array (the count is on the device: a kernel
-    // copies exactly the live elements)
-    if (esz[k] == 8) {
-      k_sort_copy<unsigned long long><<<grid_n, kSortThreads, 0, s>>>(
-          n_live, static_cast<const unsigned long long*>(tmp), static_cast<unsigned long long*>(arr[k]));
-    } else {
-      k_sort_copy<unsigned int><<<grid_n, kSortThreads, 0, s>>>(n_live, static_cast<const unsigned int*>(tmp),
-                                                               static_cast<unsigned int*>(arr[k]));
+  // groups of up to kGroup arrays of one element size: one gather and one copy each
+  for (size_t size : {(size_t)8, (size_t)4}) {
+    SortGroup<unsigned long long> g8{};
+    SortGroup<unsigned int> g4{};
+    int cnt = 0;
+    for (int k = 0; k <= na; ++k) {
+      const bool take = k < na && arr[k] && esz[k] == size;
+      if (take) {
+        if (size == 8) g8.a[cnt] = static_cast<unsigned long long*>(arr[k]);
+        else g4.a[cnt] = static_cast<unsigned int*>(arr[k]);
+        ++cnt;
+      }
+      if (cnt == kGroup || (k == na && cnt > 0)) {
+        if (size == 8) {
+          g8.na = cnt;
+          k_sort_gather<unsigned long long><<<grid_n, kSortThreads, 0, s>>>(
+              n_live, g8, static_cast<unsigned long long*>(tmp), cap, order);
+          k_sort_copy<unsigned long long><<<grid_n, kSortThreads, 0, s>>>(
+              n_live, static_cast<const unsigned long long*>(tmp), cap, g8);
+        } else {
+          g4.na = cnt;
+          k_sort_gather<unsigned int><<<grid_n, kSortThreads, 0, s>>>(n_live, g4, static_cast<unsigned int*>(tmp),
+                                                                     cap, order);
+          k_sort_copy<unsigned int><<<grid_n, kSortThreads, 0, s>>>(n_live, static_cast<const unsigned int*>(tmp),
+                                                                   cap, g4);
+        }
+        cnt = 0;
+      }
     }
   }
   const cudaError_t e = cudaGetLastError();

@@ -34,8 +34,9 @@ def _grid(nx, ny, periodic):
 
 
 def _key(x, y, g, nx, ny):
-    ci = np.floor((x - g["x0"]) / g["dx"]).astype(np.int64)
-    cj = np.floor((y - g["y0"]) / g["dy"]).astype(np.int64)
+    # the documented cell: floor((x - x0) * (1/dx)), each operation rounded in double
+    ci = np.floor((x - g["x0"]) * (1.0 / g["dx"])).astype(np.int64)
+    cj = np.floor((y - g["y0"]) * (1.0 / g["dy"])).astype(np.int64)
     if g["periodic"]:
         ci %= nx
         cj %= ny
@@ -47,8 +48,12 @@ def _key(x, y, g, nx, ny):
 
 
 def _set(n, rng, photon, g, nx, ny):
-    lo, hi = -0.1, 1.1   # a few percent outside the box
-    d = {"x": g["x0"] + rng.uniform(lo, hi, n) * nx * g["dx"], "y": g["y0"] + rng.uniform(lo, hi, n) * ny * g["dy"],
+    def frac():   # mostly in the box or just outside; a fifth one or more periods away
+        u = rng.uniform(-0.1, 1.1, n)
+        far = rng.uniform(size=n) < 0.2
+        u[far] = rng.uniform(-2.6, 3.1, int(far.sum()))
+        return u
+    d = {"x": g["x0"] + frac() * nx * g["dx"], "y": g["y0"] + frac() * ny * g["dy"],
          "z": rng.normal(size=n), "px": rng.normal(size=n), "py": rng.normal(size=n), "pz": rng.normal(size=n),
          "s1": rng.normal(size=n), "s2": rng.normal(size=n), "s3": rng.normal(size=n), "w": rng.uniform(0.5, 2, n),
          "id": rng.permutation(n).astype(np.uint64) + 1000}
