@@ -366,10 +366,10 @@ qed_status qed_step_host(qed_ctx *ctx, qed_particles *e, qed_particles *pos, qed
  * held by every process that loads the library on every device it uses) instead of the
  * context's buffers, and calls no cudaMalloc or cudaFree.  Limit: every given particle
  * set must have capacity <= 65536; larger sets are rejected with QED_ERR_INVALID_ARG (use
- * qed_step).  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) with that device current and keeps it for the process; make that
- * first call before any stream capture on the device, and do not use the call after a
- * cudaDeviceReset (the kept address would be stale).  Every call, on every context of the
+ * qed_step).  A call outside stream capture looks the array's address up
+ * (cudaGetSymbolAddress) with the device current and keeps it; a call inside a capture
+ * uses the kept address, so make the first call on a device (and the first after a
+ * cudaDeviceReset) outside any capture -- otherwise QED_ERR_INVALID_ARG.  Every call, on every context of the
  * process, shares the array and leaves its contents behind; a step reads only entries it
  * has written, so nothing needs clearing.  Calls whose work overlaps on the GPU (other
  * streams, other threads, other contexts) race on the array: order them on one stream.

@@ -38,11 +38,13 @@ constexpr size_t kStaticBytes = kSoLogNcs + rnd(kNcsRecMax * kStRecNcs);   // ab
 static __device__ __align__(256) unsigned char g_step_scratch[kStaticBytes];
 
 // Host code cannot use g_step_scratch's name as a device address: the address is looked
-// up once per device (with that device current) and cached.
+// up with the device current.  Every call that is not being captured looks it up again (a
+// device reset or another context may have moved it) and caches it per device; a call
+// inside a stream capture uses the cache, which a first call outside capture has filled.
 static std::mutex g_addr_mu;
 static void* g_addr[256];
 
-static qed_status scratch_address(void** out) {
+static qed_status scratch_address(cudaStream_t stream, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -53,8 +55,14 @@ static qed_status scratch_address(void** out) {
     set_error("qed_step_static: device ordinal %d out of range", dev);
     return QED_ERR_CUDA;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) {
+    set_error("qed_step_static: cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    return QED_ERR_CUDA;
+  }
   std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_step_scratch);
     if (e != cudaSuccess || !p) {
@@ -62,6 +70,9 @@ static qed_status scratch_address(void** out) {
       return QED_ERR_CUDA;
     }
     g_addr[dev] = p;
+  } else if (!g_addr[dev]) {
+    set_error("qed_step_static: the first call on a device must be made outside stream capture");
+    return QED_ERR_INVALID_ARG;
   }
   *out = g_addr[dev];
   return QED_OK;
@@ -138,7 +149,7 @@ extern "C" qed_status qed_step_static(qed_ctx* c, qed_particles* e, qed_particle
     return QED_ERR_INVALID_ARG;
   }
   void* base = nullptr;
-  qed_status r = scratch_address(&base);
+  qed_status r = scratch_address(reinterpret_cast<cudaStream_t>(stream), &base);
   if (r != QED_OK) return r;
   unsigned char* b = static_cast<unsigned char*>(base);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -88,3 +88,74 @@ def test_static_scratch_step_rejects_large_sets():
         q.qed_step_static(big.ctx, big.e.handle, big.pos.handle, big.ph.handle, big.fields, big.t, big.dt,
                           big.seed, big.step_no, ALL)
     big.close()
+
+
+def _static_step(s):
+    q.qed_step_static(s.ctx, s.e.handle, s.pos.handle, s.ph.handle, s.fields, s.t, s.dt, s.seed, s.step_no, ALL,
+                      s.stats.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    s.t += s.dt
+    s.step_no += 1
+
+
+def _plain_step(s):
+    q.qed_step(s.ctx, s.e.handle, s.pos.handle, s.ph.handle, s.fields, s.t, s.dt, s.seed, s.step_no, ALL,
+               s.stats.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    s.t += s.dt
+    s.step_no += 1
+
+
+def test_static_scratch_at_its_capacity_limit():
+    """Every species at the 65,536 limit, most tiles live: the whole tile-count region and the
+    logs' full extent are in use; the static step equals qed_step and nothing is dropped."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    q.build()
+    # about a quarter of the leptons emit per step at this field: 30k photons become ~61k
+    wl = workloads.crossed(ne=30000, npos=30000, nph=30000, E0=60.0, seed=6)
+    caps = dict(cap_e=65536, cap_p=65536, cap_ph=65536)
+    ref = q.Simulation(wl, prec=q.QED_PREC_F64, **caps)
+    sta = q.Simulation(wl, prec=q.QED_PREC_F64, **caps)
+    for _ in range(2):
+        _plain_step(ref)
+        _static_step(sta)
+    torch.cuda.synchronize()
+    assert sta.ph.count() > 55000 and sta.e.count() > 30000
+    _same(sta.state(), ref.state(), 1e-10)
+    for s in (ref, sta):
+        assert not s.status() & q.QED_STATUS_CAPACITY
+        assert s.counters()["n_nbw"] > 0
+    ref.close()
+    sta.close()
+
+
+def test_static_scratch_step_in_a_captured_graph():
+    """A warm-up call outside capture, then two qed_step_static calls captured into a CUDA
+    graph on a side stream and replayed: the particles equal two plain qed_step calls."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    q.build()
+    caps = dict(cap_e=8192, cap_p=8192, cap_ph=32768)
+    ref = q.Simulation(_workload(), prec=q.QED_PREC_F64, **caps)
+    sta = q.Simulation(_workload(), prec=q.QED_PREC_F64, **caps)
+    ref.run(30, ALL)
+    sta.run(30, ALL)
+    _plain_step(ref)
+    _static_step(sta)                      # the first call: outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    t0, s0 = sta.t, sta.step_no
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            _static_step(sta)
+            _static_step(sta)
+    sta.t, sta.step_no = t0, s0            # capture ran nothing: replay does the two steps
+    g.replay()
+    torch.cuda.synchronize()
+    _plain_step(ref)
+    _plain_step(ref)
+    torch.cuda.synchronize()
+    _same(sta.state(), ref.state(), 1e-10)
+    assert sta.status() == 0
+    ref.close()
+    sta.close()
