@@ -62,10 +62,10 @@ BYTES = {
 }
 
 # DRAM bytes per unit (dram__bytes_read.sum + dram__bytes_write.sum of one launch divided
-# by the particles it processed) from the ncu capture summarised in
-# profiles/k_photon_k_lepton_c2_1e6_traffic.md; scaled to a launch by its particle count.
-# Must be re-captured whenever either streaming kernel changes.
-TRAFFIC_PER_UNIT = {"k_photon": 87.06, "k_lepton": 62.44}
+# by the particles it processed) from the ncu traffic capture of the streaming passes kept
+# under profiles/; scaled to a launch by its particle count.  Must be re-captured whenever
+# either streaming kernel changes.
+TRAFFIC_PER_UNIT = {"k_photon": 85.77, "k_lepton": 63.95}
 
 
 class ClockSampler:
