@@ -947,7 +947,7 @@ def main():
         "pic": pic,
         "matter": matter,
         "c5": c5,
-        "gpu_launches": 5 * args.steps,   # headline loop; per step: photon, lepton, 2 scans, events
+        "gpu_launches": 4 * args.steps,   # headline loop; per step: photon, lepton, scans, events
         "clocks": clk.summary(),
         "counts_after": {"e": info["final_counts"][0], "pos": info["final_counts"][1],
                          "ph": info["final_counts"][2]},

@@ -79,9 +79,8 @@ static void launch_batch_t(const StepArgs& a, const int* nb, cudaStream_t s, cud
   else k_lepton<R, true, kSm><<<nb[1], kTile, 0, side>>>(a);
   cudaEventRecord(join, side);
   k_photon<R, true, kSm><<<nb[0], kTile, 0, s>>>(a);
-  launch_k(k_scan<R, true>, 1, kScanThreads, s, pdl, a, 0);
   cudaStreamWaitEvent(s, join, 0);
-  k_scan<R, true><<<1, kScanThreads, 0, s>>>(a, 1);
+  k_scan<R, true><<<2, kScanThreads, 0, s>>>(a, -1);   // both scans, after both passes
   if constexpr (sizeof(R) == 4) {
     if (a.flags & QED_F_MLP) launch_k(k_events_mlp<true>, nb[2] * 2, kMlpRows, s, pdl, a);
     else launch_k(k_events<R, true>, nb[2], kTile, s, pdl, a);

@@ -66,7 +66,6 @@ struct BatchMap {
   unsigned int lep_tile0[kMaxEns + 1];    // first lepton tile (its e- tiles, then its e+ tiles)
   unsigned int lep_e_tiles[kMaxEns];      // e- tiles of each ensemble
   unsigned int ev_base[2][kMaxEns + 1];   // first rank of each ensemble's decays / emissions
-  unsigned int fill_base[kMaxEns + 1];    // first refill task of each ensemble (slots no birth takes)
 };
 
 // per-launch parameters of the step kernels (one struct, passed by value)

@@ -2,10 +2,10 @@
 // qed_kernels.cuh -- the per-step kernels of the spin/polarization-resolved SF-QED hot path
 // (Wan et al., arXiv:2306.11288, Secs. II-IV) for sm_103a.
 //
-// One step = five launches.  Caller's stream: k_photon, k_scan(photon tiles), then (after
-// joining the side stream) k_scan(lepton tiles), k_events; the context's side stream runs
-// k_lepton concurrently with the photon chain.  The scans and the event kernel are
-// programmatic dependents of the kernel before them.
+// One step = four launches.  Caller's stream: k_photon, then (after joining the side
+// stream) k_scan (two blocks: photon tiles, lepton tiles) and k_events; the context's side
+// stream runs k_lepton concurrently with the photon pass.  The event kernel is a
+// programmatic dependent of the scans.
 //   k_photon   : streaming pass over photons -- gather, Stokes frame rotation (Eq. rotation),
 //                VB phase (Eq. rotation2), NBW decision (Sec. III D); photons are updated in
 //                place and every decay is logged (tile, rank inside the tile) in an event log.
@@ -1354,16 +1354,6 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
 // first moves the photon there (if it survived) into its hole, and the slots at or above M
 // that no birth takes are refill tasks of their own: so the refill, the births and the
 // pair events (which read their photons from the log) run in one kernel in any order.
-__device__ __forceinline__ unsigned long long upper_bound_u32(const unsigned int* h, unsigned long long n,
-                                                              unsigned long long v) {
-  unsigned long long lo = 0, hi = n;
-  while (lo < hi) {
-    const unsigned long long m = (lo + hi) >> 1;
-    if ((unsigned long long)h[m] <= v) lo = m + 1; else hi = m;
-  }
-  return lo;
-}
-
 // Empty slot j (M <= j < N) of the photon set P: a surviving photon there moves to its hole.
 // st carries D (n_nbw), M (n_surv) and the number of holes below M (n_hlow); h the holes.
 template <typename R>
@@ -1399,10 +1389,13 @@ __device__ __noinline__ void ph_vacate(const SpeciesArgs& P, const DevState* st,
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 32;
 
+// which < 0: both scans in one launch of two blocks (block 0 the photon tiles, block 1 the
+// lepton tiles; they share nothing)
 template <typename R, bool kB>
 __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ StepArgs a, int which) {
   pdl_wait();
   pdl_trigger();
+  if (which < 0) which = (int)blockIdx.x;
   __shared__ unsigned int s_w[kScanThreads / 32];
   __shared__ unsigned long long s_run;
   unsigned long long ntiles;
@@ -1492,8 +1485,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ S
       base[e] = tile0[e] < ntiles ? pre[tile0[e]] : (unsigned int)s_run;
     __syncthreads();
   }
+  __shared__ unsigned long long s_m[kB ? kMaxEns : 1];    // new photon count M of each ensemble
+  __shared__ unsigned int s_hl[kB ? kMaxEns : 1];         // its holes below M
   if (which == 0) {
-    // the holes: the slot of every ranked decay at its rank (ascending slots per ensemble)
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const EnsArgs& E = ens_of<kB>(a, e);
+      const unsigned long long tot = kB ? (unsigned long long)(base[e + 1] - base[e]) : s_run;
+      s_m[e] = (E.sp[2].present ? E.st->n_live[2] : 0ull) - tot;
+      s_hl[e] = 0u;
+    }
+    __syncthreads();
+    // the holes: the slot of every ranked decay at its rank (ascending slots per ensemble),
+    // and how many lie below the ensemble's new count
     const DevState* gst = a.st;
     const unsigned long long nrec = min(gst->cursor[0], a.rec_cap[0]);
     const unsigned int epoch = gst->epoch;
@@ -1502,6 +1505,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ S
       const NbwRec<R>& rec = evlog[kk];
       if (rec.stamp != epoch || cnt[rec.tile] == 0) continue;
       a.holes[pre[rec.tile] + rec.r_in] = (unsigned int)rec.i;
+      const int ens = kB ? (int)(rec.ens & ~kEvMedium) : 0;
+      if (rec.i < s_m[ens]) atomicAdd(&s_hl[ens], 1u);
     }
     __syncthreads();
   }
@@ -1509,34 +1514,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ S
     const EnsArgs& E = ens_of<kB>(a, e);
     const unsigned long long tot = kB ? (unsigned long long)(base[e + 1] - base[e]) : s_run;
     if (which == 0) {
-      const unsigned long long nph = E.sp[2].present ? E.st->n_live[2] : 0ull;
-      const unsigned long long M = nph - tot;
       E.st->n_nbw = tot;
-      E.st->n_surv = M;
-      E.st->n_hlow = M == 0 ? 0ull : upper_bound_u32(a.holes + (kB ? base[e] : 0u), tot, M - 1);
+      E.st->n_surv = s_m[e];
+      E.st->n_hlow = s_hl[e];
     } else {
       E.st->n_ncs_tot = tot;
       if constexpr (!kB) {   // the e- tiles come first: their events are the first ranks
         const unsigned long long n0 = E.sp[0].present ? E.st->n_live[0] : 0ull;
         const unsigned long long te = (n0 + kTile - 1) / kTile;
         E.st->n_ncs_e = te < ntiles ? (unsigned long long)pre[te] : tot;
-      }
-    }
-  }
-  if constexpr (kB) {
-    // the refill tasks of each ensemble: its slots M + r, C <= r < D, that no birth takes
-    if (which == 1) {
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
-        unsigned int f = 0;
-        for (int e = 0; e < ne; ++e) {
-          a.map->fill_base[e] = f;
-          const DevState* st = ens_of<kB>(a, e).st;
-          const unsigned long long D = st->n_nbw, C = births ? st->n_ncs_tot : 0ull;
-          f += (unsigned int)(C < D ? D - C : 0ull);
-        }
-        a.map->fill_base[ne] = f;
       }
     }
   }
@@ -1976,11 +1962,21 @@ __device__ __forceinline__ void fill_task(const StepArgs& a, const unsigned int*
   ph_vacate<R>(E.sp[2], st, holes_of<kB>(a, ens), st->n_surv + r);
 }
 
-// the number of refill tasks (single ensemble) or their per-ensemble bases (batched)
+// the number of refill tasks (single ensemble) or their per-ensemble bases (batched: the
+// refill tasks of ensemble e are its slots M + r, C <= r < D, that no birth takes)
 template <bool kB>
 __device__ __forceinline__ unsigned long long fill_setup(const StepArgs& a, bool births, unsigned int* s_fb) {
   if constexpr (kB) {
-    for (int e = threadIdx.x; e <= a.n_ens; e += blockDim.x) s_fb[e] = a.map->fill_base[e];
+    if (threadIdx.x == 0) {
+      unsigned int f = 0;
+      for (int e = 0; e < a.n_ens; ++e) {
+        s_fb[e] = f;
+        const DevState* st = ens_of<kB>(a, e).st;
+        const unsigned long long D = st->n_nbw, C = births ? st->n_ncs_tot : 0ull;
+        f += (unsigned int)(C < D ? D - C : 0ull);
+      }
+      s_fb[a.n_ens] = f;
+    }
     __syncthreads();
     return s_fb[a.n_ens];
   } else {

@@ -65,7 +65,6 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
   if (a.flags & QED_F_BH) k_photon<R, false, true, true><<<nb[0], kTile, 0, s>>>(a);
   else k_photon<R, false, true><<<nb[0], kTile, 0, s>>>(a);
   if (ss.tev) cudaEventRecord(ss.tev[1], s);
-  launch_k(k_scan<R, false>, 1, kScanThreads, s, pdl, a, 0);
   if (fork) {
     cudaStreamWaitEvent(s, ss.join, 0);
   } else {
@@ -73,7 +72,7 @@ static qed_status launch_t(const StepArgs& a, const int* nb, cudaStream_t s, con
     launch_lepton<R>(a, nb[1], s);
     if (ss.tev) cudaEventRecord(ss.tev[5], s);
   }
-  k_scan<R, false><<<1, kScanThreads, 0, s>>>(a, 1);
+  k_scan<R, false><<<2, kScanThreads, 0, s>>>(a, -1);   // both scans, after both passes
   if (part == kStepBegin) {
     k_shard_counts<<<1, 32, 0, s>>>(a);
     return launch_status();
