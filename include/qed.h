@@ -516,10 +516,12 @@ qed_status qed_batch_set_config(qed_batch *b, const qed_batch_config *cfg);
 
 /* Autotuner: runs steps_per_candidate real steps of the batch under each candidate launch
  * shape (streaming blocks per SM x event blocks per SM x rate-table placement), times
- * them with CUDA events, and keeps the one with the most particle-steps per second (the
- * population changes from one candidate to the next).  The steps advance the simulation;
- * the results do not depend on the launch shape.  Syncs.  *rate (optional) receives the
- * best particle-steps per second.  Errors: QED_ERR_INVALID_ARG, QED_ERR_CUDA. */
+ * them with CUDA events, and keeps the one with the most particle-steps per second.  The
+ * population grows while the candidates run, so every candidate is timed twice, in a
+ * forward and in a backward sweep, and ranked by the mean of its two rates.  The steps
+ * (2 x (steps_per_candidate + 1) per candidate) advance the simulation; the results do not
+ * depend on the launch shape.  Syncs.  *rate (optional) receives the chosen shape's mean
+ * particle-steps per second.  Errors: QED_ERR_INVALID_ARG, QED_ERR_CUDA. */
 qed_status qed_batch_tune(qed_batch *b, uint32_t steps_per_candidate, void *stream, qed_batch_config *chosen,
                           double *rate);
 

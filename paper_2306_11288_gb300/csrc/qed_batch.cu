@@ -414,35 +414,46 @@ extern "C" qed_status qed_batch_tune(qed_batch* b, uint32_t steps_per_candidate,
   if (!b || steps_per_candidate < 1) BFAIL(QED_ERR_INVALID_ARG, "qed_batch_tune: bad arguments");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int sblocks[4] = {1, 2, 3, 4}, eblocks[4] = {1, 2, 4, 8};
-  qed_batch_config best = b->cfg;
-  double best_rate = -1.0;
+  // the candidates (a larger stream count than the occupancy allows repeats a smaller one)
+  qed_batch_config cand[32];
+  int nc = 0;
   for (int sm = 1; sm >= 0; --sm) {
     const int occ_max = std::max(b->occ[sm][0], b->occ[sm][1]);
     for (int si = 0; si < 4; ++si) {
-      if (sblocks[si] > std::max(occ_max, 1)) continue;   // same grid as a smaller count
-      for (int ei = 0; ei < 4; ++ei) {
-        qed_batch_config c{sblocks[si], eblocks[ei], sm};
-        qed_status r = qed_batch_set_config(b, &c);
-        if (r == QED_OK) r = batch_launch(b, s, true);   // settle
-        unsigned long long p0 = 0, p1 = 0;
-        if (r == QED_OK) r = batch_processed(b, s, &p0);
-        if (r != QED_OK) return r;
-        BCK(cudaEventRecord(b->t0, s));
-        for (uint32_t k = 0; k < steps_per_candidate && r == QED_OK; ++k) r = batch_launch(b, s, true);
-        if (r != QED_OK) return r;
-        BCK(cudaEventRecord(b->t1, s));
-        BCK(cudaEventSynchronize(b->t1));
-        float ms = 0;
-        BCK(cudaEventElapsedTime(&ms, b->t0, b->t1));
-        r = batch_processed(b, s, &p1);
-        if (r != QED_OK) return r;
-        // the population changes from candidate to candidate: compare particle-steps per second
-        const double rt = ms > 0 ? (double)(p1 - p0) / (ms * 1e-3) : 0.0;
-        if (rt > best_rate) {
-          best_rate = rt;
-          best = c;
-        }
-      }
+      if (sblocks[si] > std::max(occ_max, 1)) continue;
+      for (int ei = 0; ei < 4; ++ei) cand[nc++] = qed_batch_config{sblocks[si], eblocks[ei], sm};
+    }
+  }
+  // The population grows while the candidates run, and a larger population steps at a higher
+  // rate: each candidate is timed twice, once in a forward and once in a backward sweep, and
+  // ranked by the mean of its two rates, so that the drift cancels to first order.
+  double sum[32] = {0};
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int k = 0; k < nc; ++k) {
+      const int j = pass == 0 ? k : nc - 1 - k;
+      qed_status r = qed_batch_set_config(b, &cand[j]);
+      if (r == QED_OK) r = batch_launch(b, s, true);   // settle
+      unsigned long long p0 = 0, p1 = 0;
+      if (r == QED_OK) r = batch_processed(b, s, &p0);
+      if (r != QED_OK) return r;
+      BCK(cudaEventRecord(b->t0, s));
+      for (uint32_t q = 0; q < steps_per_candidate && r == QED_OK; ++q) r = batch_launch(b, s, true);
+      if (r != QED_OK) return r;
+      BCK(cudaEventRecord(b->t1, s));
+      BCK(cudaEventSynchronize(b->t1));
+      float ms = 0;
+      BCK(cudaEventElapsedTime(&ms, b->t0, b->t1));
+      r = batch_processed(b, s, &p1);
+      if (r != QED_OK) return r;
+      sum[j] += ms > 0 ? (double)(p1 - p0) / (ms * 1e-3) : 0.0;   // particle-steps per second
+    }
+  }
+  qed_batch_config best = b->cfg;
+  double best_rate = -1.0;
+  for (int j = 0; j < nc; ++j) {
+    if (0.5 * sum[j] > best_rate) {
+      best_rate = 0.5 * sum[j];
+      best = cand[j];
     }
   }
   const qed_status r = qed_batch_set_config(b, &best);
