@@ -12,7 +12,7 @@
 // (forward with the FP16 rounding of the hidden layer that inference applies, backward
 // with straight-through rounding) and leaves one partial gradient per block; k_mlp_adam
 // adds the partials in block order (deterministic) and applies Adam with a cosine learning
-// rate.  k_mlp_pack writes the BF16 hidden-layer weights in the tensor-core layout.
+// rate.  k_mlp_pack writes the FP16 hidden-layer weights in the tensor-core layout.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -59,10 +59,9 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
   return 0.5f * (1.0f + th) + 0.5f * x * (1.0f - th * th) * c * (1.0f + 3.0f * 0.044715f * x * x);
 }
 
-// float -> FP16 bits, round to nearest even, and back.  FP16 rather than BF16 for the
-// hidden layer: its 10 mantissa bits keep the rounding of the activations 8x below BF16's,
-// which sets the sampler's accuracy floor; GELU outputs and the weights are far inside the
-// FP16 range.
+// float -> FP16 bits, round to nearest even, and back.  FP16 for the hidden layer: its 10
+// mantissa bits keep the rounding of the activations 8x below BF16's, well under the
+// trained network's error; GELU outputs and the weights are far inside the FP16 range.
 __device__ __forceinline__ unsigned short f16_rn(float f) { return __half_as_ushort(__float2half_rn(f)); }
 __device__ __forceinline__ float f16_to_f(unsigned short h) { return __half2float(__ushort_as_half(h)); }
 
