@@ -563,11 +563,30 @@ __device__ __forceinline__ Tabs<R> tabs_global(const void* tables) {
 template <typename R, bool kPh> struct SmemTab {
   static constexpr size_t n = sizeof(R) == 8 ? kSmemRateLen : (kPh ? kCoefPhLen : kCoefLepLen);
 };
-// Copies them to s (16-byte aligned) and points the table accessors there.
+// Copies them to s (16-byte aligned) and points the table accessors there.  16-byte
+// read-only loads, every one of a thread's loads issued before its first store (the table
+// pointer is generic, so a store could alias a later load and serialise the copy).
+// Block size kTile.
 template <typename R, bool kPh>
 __device__ __forceinline__ void stage_rates(Tabs<R>& tb, R* s) {
-  const size_t o = sizeof(R) == 8 ? kOffRA : (kPh ? kOffCoefVB : kOffCoefN);
-  for (int i = threadIdx.x; i < (int)SmemTab<R, kPh>::n; i += blockDim.x) s[i] = tb.g[o + i];
+  constexpr size_t o = sizeof(R) == 8 ? kOffRA : (kPh ? kOffCoefVB : kOffCoefN);
+  constexpr size_t kEl = 16 / sizeof(R);                       // elements per 16 bytes
+  constexpr size_t n = SmemTab<R, kPh>::n;
+  static_assert(o % kEl == 0 && n % kEl == 0, "16-byte table segments");
+  constexpr int nv = (int)(n / kEl), kPer = (nv + kTile - 1) / kTile;
+  const uint4* src = reinterpret_cast<const uint4*>(tb.g + o);
+  uint4* dst = reinterpret_cast<uint4*>(s);
+  uint4 v[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int q = (int)threadIdx.x + j * kTile;
+    if (q < nv) v[j] = __ldg(src + q);
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int q = (int)threadIdx.x + j * kTile;
+    if (q < nv) dst[q] = v[j];
+  }
   if constexpr (sizeof(R) == 8) {
     tb.s = s;
   } else if constexpr (kPh) {
