@@ -1986,15 +1986,21 @@ __device__ __forceinline__ void fill_task(const StepArgs& a, const unsigned int*
 template <bool kB>
 __device__ __forceinline__ unsigned long long fill_setup(const StepArgs& a, bool births, unsigned int* s_fb) {
   if constexpr (kB) {
+    // every ensemble's count by its own thread (the loads in parallel), then the prefix in
+    // shared memory
+    for (int e = threadIdx.x; e < a.n_ens; e += blockDim.x) {
+      const DevState* st = ens_of<kB>(a, e).st;
+      const unsigned long long D = st->n_nbw, C = births ? st->n_ncs_tot : 0ull;
+      s_fb[e + 1] = (unsigned int)(C < D ? D - C : 0ull);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       unsigned int f = 0;
-      for (int e = 0; e < a.n_ens; ++e) {
+      s_fb[0] = 0u;
+      for (int e = 1; e <= a.n_ens; ++e) {
+        f += s_fb[e];
         s_fb[e] = f;
-        const DevState* st = ens_of<kB>(a, e).st;
-        const unsigned long long D = st->n_nbw, C = births ? st->n_ncs_tot : 0ull;
-        f += (unsigned int)(C < D ? D - C : 0ull);
       }
-      s_fb[a.n_ens] = f;
     }
     __syncthreads();
     return s_fb[a.n_ens];
