@@ -515,8 +515,9 @@ qed_status qed_batch_get_config(const qed_batch *b, qed_batch_config *cfg);
 qed_status qed_batch_set_config(qed_batch *b, const qed_batch_config *cfg);
 
 /* Autotuner: runs steps_per_candidate real steps of the batch under each candidate launch
- * shape (streaming blocks per SM x event blocks per SM x rate-table placement), times
- * them with CUDA events, and keeps the one with the most particle-steps per second.  The
+ * shape (streaming blocks per SM x event blocks per SM x rate-table placement) as
+ * qed_batch_run runs them (a captured graph, replayed), times them with CUDA events, and
+ * keeps the one with the most particle-steps per second.  The
  * population grows while the candidates run, so every candidate is timed twice, in a
  * forward and in a backward sweep, and ranked by the mean of its two rates.  The steps
  * (2 x (steps_per_candidate + 1) per candidate) advance the simulation; the results do not

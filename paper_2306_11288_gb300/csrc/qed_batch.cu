@@ -426,18 +426,20 @@ extern "C" qed_status qed_batch_tune(qed_batch* b, uint32_t steps_per_candidate,
   }
   // The population grows while the candidates run, and a larger population steps at a higher
   // rate: each candidate is timed twice, once in a forward and once in a backward sweep, and
-  // ranked by the mean of its two rates, so that the drift cancels to first order.
+  // ranked by the mean of its two rates, so that the drift cancels to first order.  A
+  // candidate runs as qed_batch_run runs it, replaying its captured graph (the graph may
+  // order the two streaming passes otherwise than direct launches do).
   double sum[32] = {0};
   for (int pass = 0; pass < 2; ++pass) {
     for (int k = 0; k < nc; ++k) {
       const int j = pass == 0 ? k : nc - 1 - k;
       qed_status r = qed_batch_set_config(b, &cand[j]);
-      if (r == QED_OK) r = batch_launch(b, s, true);   // settle
+      if (r == QED_OK) r = qed_batch_run(b, 1, stream);   // capture and settle
       unsigned long long p0 = 0, p1 = 0;
       if (r == QED_OK) r = batch_processed(b, s, &p0);
       if (r != QED_OK) return r;
       BCK(cudaEventRecord(b->t0, s));
-      for (uint32_t q = 0; q < steps_per_candidate && r == QED_OK; ++q) r = batch_launch(b, s, true);
+      r = qed_batch_run(b, steps_per_candidate, stream);
       if (r != QED_OK) return r;
       BCK(cudaEventRecord(b->t1, s));
       BCK(cudaEventSynchronize(b->t1));
