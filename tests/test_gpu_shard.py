@@ -103,3 +103,36 @@ def test_foreign_counts_and_misuse(ctx):
     assert sim.status() == 0
     sim.close()
     q.qed_destroy(sim.ctx)
+
+
+def test_three_shards_one_empty_mixed_equal_one_context(ctx):
+    """Mixed path, three ranks, the middle one holding no particle at all: the shards' union
+    equals one context stepping the whole population in the ranks' order (GPU against
+    GPU, the same arithmetic: bit for bit), and the counter is every rank's."""
+    wl = workloads.crossed(seed=7, ne=300, npos=150, nph=400)
+    empty = {sp: {k: v[:0] for k, v in wl[sp].items()} for sp in shard_cases.SPECIES}
+    parts = [workloads.shard(wl, 0, 2), dict(wl, **empty), workloads.shard(wl, 1, 2)]
+    shards = [q.Simulation(p, prec=q.QED_PREC_MIXED, ctx=q.qed_ctx_share(ctx), **CAPS) for p in parts]
+    ref = q.Simulation(wl, prec=q.QED_PREC_MIXED, ctx=q.qed_ctx_share(ctx), **CAPS)
+    for _ in range(6):
+        order = [_ids(s) for s in shards]
+        st = shard_cases.rank_order(ref.state(), {sp: [o[sp] for o in order] for sp in shard_cases.SPECIES})
+        for sp in shard_cases.SPECIES:
+            getattr(ref, sp).load(st[sp])
+        ref.run(1, FLAGS)
+        counts = [s.step_begin(FLAGS) for s in shards]
+        allc = torch.stack(counts)
+        for r, s in enumerate(shards):
+            s.step_end(allc, r, 3)
+    torch.cuda.synchronize()
+    states = [s.state() for s in shards]
+    assert len({st["next_id"] for st in states}) == 1
+    want = ref.state()
+    shard_cases.assert_same(shard_cases.union(states), want, 0.0)
+    assert states[1]["e"]["id"].size == 0 and states[1]["ph"]["id"].size == 0
+    c = [s.counters() for s in shards]
+    assert sum(x["n_nbw"] for x in c) == ref.counters()["n_nbw"] > 0
+    for s in shards + [ref]:
+        assert s.status() == 0
+        s.close()
+        q.qed_destroy(s.ctx)
