@@ -12,10 +12,10 @@
 //   k_lepton   : streaming pass over e- then e+ -- gather, Boris (Eqs. boris1-6), T-BMT
 //                (Eqs. bmt-boris1-4), x update, chi_e, NCS decision; the no-emission spin
 //                update and collapse is done here; emissions are logged.
-//   k_scan     : exclusive scan of the per-tile event counts (one block): the rank of an
-//                event is the prefix of its tile plus its rank inside the tile, which orders
-//                events by particle index exactly as a sequential pass would; the photon
-//                scan also lists the decayed slots (holes) in index order.
+//   k_scan     : exclusive scans of the per-tile event counts (one block per scan): the
+//                rank of an event is the prefix of its tile plus its rank inside the tile,
+//                which orders events by particle index exactly as a sequential pass would;
+//                the photon scan also lists the decayed slots (holes) in index order.
 //   k_events   : one thread per task: a logged emission (photon energy, recoil, spin
 //                collapse, photon Stokes, photon birth), a logged decay (pair energy, spins,
 //                birth of e- and e+) or the refill of a decayed photon slot; its last block

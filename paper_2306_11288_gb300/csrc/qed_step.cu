@@ -7,10 +7,10 @@ namespace qedk {
 size_t nbw_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NbwRec<double>) : sizeof(NbwRec<float>); }
 size_t ncs_rec_bytes(qed_precision p) { return p == QED_PREC_F64 ? sizeof(NcsRec<double>) : sizeof(NcsRec<float>); }
 
-// Photon pass and its scan on the caller's stream; the lepton pass on the context's side
-// stream (forked after all earlier work on the caller's stream, joined before the lepton
-// scan): the two passes touch disjoint particles, and everything that needs both (births,
-// refills, pair events) is in k_events.
+// Photon pass on the caller's stream; the lepton pass on the context's side stream (forked
+// after all earlier work on the caller's stream, joined before the scans): the two passes
+// touch disjoint particles, and everything that needs both (births, refills, pair events)
+// is in k_events.
 template <typename R>
 static void launch_lepton(const StepArgs& a, int grid, cudaStream_t s) {
   const bool rad = a.flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT), dep = a.flags & QED_F_DEPOSIT;
