@@ -532,7 +532,7 @@ qed_status qed_batch_destroy(qed_batch *b);
  * A 3 -> 64 -> 64 -> 1 GELU network maps (ln chi_e, s = S.zeta, one uniform r) to ln u,
  * u = omega/(gamma - omega), in place of the two-component inverse-CDF table lookup (the
  * spin mixture of Eq. Wspin2, inverted as one monotone map of r).  Its 64 x 64 layer runs on
- * the tensor cores in FP16 with FP32 accumulation; the rest in FP32.  The paper has no
+ * the tensor cores in BF16 with FP32 accumulation; the rest in FP32.  The paper has no
  * counterpart: this is an alternative sampler, judged against the table sampler.
  * Parameters live on the context that owns the tables (a shared context uses its owner's).
  * Parameter vector (4481 floats): w1[64][3], b1[64], w2[64][64], b2[64], w3[64], b3. */

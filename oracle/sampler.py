@@ -8,7 +8,7 @@ smoke check and the benchmark's CPU legs use this package).
   F+-(y) the level at which the oracle's own component inverse CDF reaches y.  F is
   inverted by bisection.  Built on the oracle's tables only.
 * ``forward``: the network the library evaluates (3 -> 64 -> 64 -> 1, GELU with the tanh
-  form), in numpy, with the library's FP16 rounding of the hidden activations and weights
+  form), in numpy, with the library's BF16 rounding of the hidden activations and weights
   of the 64 x 64 layer (round to nearest even), and its input features / output transform.
 """
 from __future__ import annotations
@@ -66,9 +66,11 @@ def two_uniform_sample(orc, chi: float, s: float, um0: float, um1: float) -> flo
     return orc.ncs_invcdf(comp, chi, float(logit_clamped(um1)))
 
 
-def f16_round(x: np.ndarray) -> np.ndarray:
-    """float32 -> nearest IEEE half (ties to even, numpy's conversion), returned as float32."""
-    return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float32)
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """float32 -> nearest BF16 (ties to even), returned as float32."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
 
 
 def gelu(x):
@@ -103,7 +105,7 @@ def forward(p: np.ndarray, lnchi, s, r) -> np.ndarray:
     lnchi = np.asarray(lnchi, dtype=np.float64)
     t = logit_clamped(np.asarray(r, dtype=np.float64))
     x = features(lnchi, np.asarray(s, dtype=np.float64), t).astype(np.float32)
-    h1 = f16_round(gelu(x.astype(np.float64) @ w1.T.astype(np.float64) + b1).astype(np.float32))
-    z2 = h1.astype(np.float64) @ f16_round(w2).T.astype(np.float64) + b2
+    h1 = bf16_round(gelu(x.astype(np.float64) @ w1.T.astype(np.float64) + b1).astype(np.float32))
+    z2 = h1.astype(np.float64) @ bf16_round(w2).T.astype(np.float64) + b2
     y = gelu(z2) @ w3.astype(np.float64) + b3
     return base(lnchi, t) + 8.0 * y

@@ -9,10 +9,10 @@
 // are found by bisection on the tables (FP32).
 //
 // Training: plain FP32 kernels written here.  k_mlp_grad evaluates tiles of 64 samples
-// (forward with the FP16 rounding of the hidden layer that inference applies, backward
+// (forward with the BF16 rounding of the hidden layer that inference applies, backward
 // with straight-through rounding) and leaves one partial gradient per block; k_mlp_adam
 // adds the partials in block order (deterministic) and applies Adam with a cosine learning
-// rate.  k_mlp_pack writes the FP16 hidden-layer weights in the tensor-core layout.
+// rate.  k_mlp_pack writes the BF16 hidden-layer weights in the tensor-core layout.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -100,7 +100,7 @@ struct TrainSmem {
   float b3;
   float x[kTrainTile][3], tgt[kTrainTile], dy[kTrainTile];
   float g1[kTrainTile][kMlpH + 1];   // gelu'(z1)
-  float h1q[kTrainTile][kMlpH + 1];  // FP16-rounded gelu(z1)
+  float h1q[kTrainTile][kMlpH + 1];  // BF16-rounded gelu(z1)
   float g2[kTrainTile][kMlpH + 1];   // gelu'(z2), then dZ2
   float h2[kTrainTile][kMlpH + 1];   // gelu(z2)
 };
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_grad(const MlpParams* P, 
   }
   for (int i = tid; i < kMlpH * kMlpH; i += blockDim.x) {
     const float w = P->w2[i / kMlpH][i % kMlpH];
-    S.w2q[i / kMlpH][i % kMlpH] = f16_to_f(f16_rn(w));
+    S.w2q[i / kMlpH][i % kMlpH] = bf16_to_f(bf16_rn(w));
   }
   if (tid == 0) S.b3 = P->b3;
   __syncthreads();
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_grad(const MlpParams* P, 
       const int m = e / kMlpH, j = e % kMlpH;
       const float z = fmaf(S.w1[j][0], S.x[m][0], fmaf(S.w1[j][1], S.x[m][1], fmaf(S.w1[j][2], S.x[m][2], S.b1[j])));
       S.g1[m][j] = gelu_grad_f(z);
-      S.h1q[m][j] = f16_to_f(f16_rn(gelu_f(z)));
+      S.h1q[m][j] = bf16_to_f(bf16_rn(gelu_f(z)));
     }
     __syncthreads();
     // layer 2
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_mlp_grad(const MlpParams* P, 
       S.g2[m][j] *= S.dy[m] * S.w3[j];
     }
     __syncthreads();
-    // W2 gradient (straight through the FP16 rounding): dZ2^T h1q; b2 gradient
+    // W2 gradient (straight through the BF16 rounding): dZ2^T h1q; b2 gradient
 #pragma unroll
     for (int k = 0; k < kMlpH * kMlpH / kTrainThreads; ++k) {
       const int e = tid + k * kTrainThreads;
@@ -254,7 +254,7 @@ __global__ void k_mlp_adam(MlpParams* P, float* m, float* v, const float* grad, 
 __global__ void k_mlp_pack(MlpParams* P) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kMlpH * kMlpH; e += gridDim.x * blockDim.x) {
     const int n = e / kMlpH, k = e % kMlpH;
-    P->w2p[a_offset((unsigned)n, (unsigned)k) / 2] = f16_rn(P->w2[n][k]);
+    P->w2p[a_offset((unsigned)n, (unsigned)k) / 2] = bf16_rn(P->w2[n][k]);
   }
 }
 

@@ -5,16 +5,14 @@
 //
 // Inference on the tensor cores: a CTA of 128 threads evaluates 128 rows.  Layer 1 (K = 3)
 // and the output layer run in FP32 on the CUDA cores; the 64 x 64 hidden layer (94 % of
-// the FLOPs) is one tcgen05.mma chain: A = the FP16 hidden activations of the 128 rows and
-// B = the FP16 weights, both in shared memory in the canonical no-swizzle K-major layout,
+// the FLOPs) is one tcgen05.mma chain: A = the BF16 hidden activations of the 128 rows and
+// B = the BF16 weights, both in shared memory in the canonical no-swizzle K-major layout,
 // the FP32 accumulator in tensor memory (64 columns), issued by one thread, completion on
 // an mbarrier, read back with tcgen05.ld.
 #pragma once
 #include <cuda_runtime.h>
 
 #include <cstdint>
-
-#include <cuda_fp16.h>
 
 namespace qedk {
 
@@ -23,13 +21,13 @@ constexpr int kMlpParams = kMlpH * 3 + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1
 constexpr int kMlpRows = 128;                   // rows per CTA (= threads = TMEM lanes)
 
 // FP32 parameters (the training master copy and the inference copy of layers 1 and 3) and
-// the packed FP16 hidden-layer weights
+// the packed BF16 hidden-layer weights
 struct MlpParams {
   float w1[kMlpH][3], b1[kMlpH];
   float w2[kMlpH][kMlpH], b2[kMlpH];
   float w3[kMlpH], b3;
   float pad[3];
-  unsigned short w2p[kMlpH * kMlpH];           // FP16, canonical core-matrix layout (see a_offset)
+  unsigned short w2p[kMlpH * kMlpH];           // BF16, canonical core-matrix layout (see a_offset)
 };
 
 // input features and output transform (shared by training and inference)
@@ -59,13 +57,14 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
   return 0.5f * (1.0f + th) + 0.5f * x * (1.0f - th * th) * c * (1.0f + 3.0f * 0.044715f * x * x);
 }
 
-// float -> FP16 bits, round to nearest even, and back.  FP16 for the hidden layer: its 10
-// mantissa bits keep the rounding of the activations 8x below BF16's, well under the
-// trained network's error; GELU outputs and the weights are far inside the FP16 range.
-__device__ __forceinline__ unsigned short f16_rn(float f) { return __half_as_ushort(__float2half_rn(f)); }
-__device__ __forceinline__ float f16_to_f(unsigned short h) { return __half2float(__ushort_as_half(h)); }
+// float -> BF16, round to nearest even (finite inputs)
+__device__ __forceinline__ unsigned short bf16_rn(float f) {
+  const unsigned int b = __float_as_uint(f);
+  return (unsigned short)((b + 0x7FFFu + ((b >> 16) & 1u)) >> 16);
+}
+__device__ __forceinline__ float bf16_to_f(unsigned short h) { return __uint_as_float((unsigned int)h << 16); }
 
-// byte offset of element (row, k) of a [rows x 64] FP16 operand in the canonical
+// byte offset of element (row, k) of a [rows x 64] BF16 operand in the canonical
 // no-swizzle K-major layout: 8 x 8 core matrices of 128 contiguous bytes (8 rows of 16 B),
 // K-adjacent core matrices 128 B apart (LBO), row-adjacent ones 1024 B apart (SBO)
 __host__ __device__ __forceinline__ unsigned int a_offset(unsigned int row, unsigned int k) {
@@ -73,8 +72,8 @@ __host__ __device__ __forceinline__ unsigned int a_offset(unsigned int row, unsi
 }
 
 struct MlpSmem {
-  alignas(1024) unsigned char a[kMlpRows * kMlpH * 2];   // hidden activations, FP16 (16 KB)
-  alignas(1024) unsigned char w2[kMlpH * kMlpH * 2];     // hidden weights, FP16 (8 KB)
+  alignas(1024) unsigned char a[kMlpRows * kMlpH * 2];   // hidden activations, BF16 (16 KB)
+  alignas(1024) unsigned char w2[kMlpH * kMlpH * 2];     // hidden weights, BF16 (8 KB)
   float w1[kMlpH][3], b1[kMlpH], b2[kMlpH], w3[kMlpH];
   float b3;
   unsigned int taddr;
@@ -92,10 +91,9 @@ __device__ __forceinline__ unsigned long long smem_desc(unsigned int saddr, unsi
   d |= 1ull << 46;
   return d;
 }
-// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B FP16 (bits 7-9, 10-12 =
-// 0; both operands of one MMA share the type), both K-major, N >> 3 at bits 17-22, M >> 4 at
-// bits 24-28
-constexpr unsigned int kMlpIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((unsigned)(kMlpH >> 3) << 17) |
+// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 =
+// 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr unsigned int kMlpIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kMlpH >> 3) << 17) |
                                    ((unsigned)(kMlpRows >> 4) << 24);
 
 __device__ __forceinline__ void mlp_mbar_init(unsigned long long* bar) {
@@ -162,7 +160,7 @@ __device__ __forceinline__ void mlp_teardown(MlpSmem& sm) {
 // chain did not complete within the wait limit.
 __device__ __forceinline__ float mlp_rows(MlpSmem& sm, const float x[3], unsigned int& phase, bool* ok) {
   const unsigned int tid = threadIdx.x;
-  // layer 1 in FP32, GELU, FP16 into row tid of A
+  // layer 1 in FP32, GELU, BF16 into row tid of A
 #pragma unroll
   for (int j8 = 0; j8 < kMlpH / 8; ++j8) {
     unsigned int w[4];
@@ -173,7 +171,7 @@ __device__ __forceinline__ float mlp_rows(MlpSmem& sm, const float x[3], unsigne
       for (int q = 0; q < 2; ++q) {
         const int j = j8 * 8 + h * 2 + q;
         const float z = fmaf(sm.w1[j][0], x[0], fmaf(sm.w1[j][1], x[1], fmaf(sm.w1[j][2], x[2], sm.b1[j])));
-        v[q] = f16_rn(gelu_f(z));
+        v[q] = bf16_rn(gelu_f(z));
       }
       w[h] = (unsigned int)v[0] | ((unsigned int)v[1] << 16);
     }

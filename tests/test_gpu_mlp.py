@@ -2,8 +2,8 @@
 
 * The training target (the table sampler's mixture inverse on the FP32 tables) against the
   oracle's mixture inverse on its own tables.
-* Tensor-core evaluation (tcgen05, FP16 hidden layer, FP32 accumulation in tensor memory)
-  against the numpy network with the same FP16 rounding, for given parameters.
+* Tensor-core evaluation (tcgen05, BF16 hidden layer, FP32 accumulation in tensor memory)
+  against the numpy network with the same BF16 rounding, for given parameters.
 * A short training run learns the target (median and tail errors in ln u), and a step with
   QED_F_MLP (its own training run) reproduces the photon spectrum and polarisation of the
   table path and of the FP64 oracle within 3 sigma per bin (fixed seeds: the outcome is

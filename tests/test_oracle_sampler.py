@@ -6,9 +6,8 @@
   pure components s = +-1.
 * The mixture inverse is monotone in r and, at s = +1 (only the "+" component), equals the
   component's own inverse CDF.
-* FP16 rounding is IEEE round-to-nearest-even (hand-checked values at the half-ulp ties,
-  the largest finite value and the underflow to zero), and the numpy network with zero
-  hidden weights reduces to its closed form."""
+* BF16 rounding is round-to-nearest-even on the float32 bit pattern (hand-checked values),
+  and the numpy network with zero hidden weights reduces to its closed form."""
 import math
 
 import numpy as np
@@ -36,12 +35,11 @@ def test_mixture_inverse_monotone_and_pure_component(orc):
         assert abs(SM.mixture_inverse(orc, 2.0, 1.0, r) - orc.ncs_invcdf(0, 2.0, t)) < 1e-9
 
 
-def test_f16_round_to_nearest_even():
-    # 10 mantissa bits: the spacing above 1 is 2^-10, a tie is 2^-11
-    x = np.array([1.0, 1.0 + 2 ** -11, 1.0 + 3 * 2 ** -11, 1.0 + 2 ** -12, 1.0 + 2 ** -11 + 2 ** -15, -2.5,
-                  65504.0, 1e-8], dtype=np.float32)
-    want = np.array([1.0, 1.0, 1.0 + 2 ** -9, 1.0, 1.0 + 2 ** -10, -2.5, 65504.0, 0.0], dtype=np.float32)
-    assert np.array_equal(SM.f16_round(x), want)
+def test_bf16_round_to_nearest_even():
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -9, 1.0 + 2 ** -8 + 2 ** -12, -2.5],
+                 dtype=np.float32)
+    want = np.array([1.0, 1.0, 1.0 + 2 ** -6, 1.0, 1.0 + 2 ** -7, -2.5], dtype=np.float32)
+    assert np.array_equal(SM.bf16_round(x), want)
 
 
 def test_forward_closed_form_with_zero_hidden_weights():
