@@ -563,29 +563,44 @@ __device__ __forceinline__ Tabs<R> tabs_global(const void* tables) {
 template <typename R, bool kPh> struct SmemTab {
   static constexpr size_t n = sizeof(R) == 8 ? kSmemRateLen : (kPh ? kCoefPhLen : kCoefLepLen);
 };
-// Copies them to s (16-byte aligned) and points the table accessors there.  16-byte
-// read-only loads, every one of a thread's loads issued before its first store (the table
-// pointer is generic, so a store could alias a later load and serialise the copy).
-// Block size kTile.
+// global -> shared 1-D bulk copy (TMA) of `bytes` (16-byte aligned ends, a multiple of 16),
+// completing on the mbarrier bar
+__device__ __forceinline__ void tma_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned int bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Copies them to s (16-byte aligned) by TMA -- one bulk copy issued by one thread, completed
+// on an mbarrier that every thread waits on (bounded) -- and points the table accessors
+// there.  Block size kTile; the caller synchronises the block afterwards.  A wait that
+// gives up (never expected) sets QED_STATUS_TIMEOUT, waits once more for the copy in
+// flight, and copies the tables with plain loads.
 template <typename R, bool kPh>
-__device__ __forceinline__ void stage_rates(Tabs<R>& tb, R* s) {
+__device__ __forceinline__ void stage_rates(Tabs<R>& tb, R* s, unsigned int* status) {
   constexpr size_t o = sizeof(R) == 8 ? kOffRA : (kPh ? kOffCoefVB : kOffCoefN);
   constexpr size_t kEl = 16 / sizeof(R);                       // elements per 16 bytes
   constexpr size_t n = SmemTab<R, kPh>::n;
   static_assert(o % kEl == 0 && n % kEl == 0, "16-byte table segments");
-  constexpr int nv = (int)(n / kEl), kPer = (nv + kTile - 1) / kTile;
-  const uint4* src = reinterpret_cast<const uint4*>(tb.g + o);
-  uint4* dst = reinterpret_cast<uint4*>(s);
-  uint4 v[kPer];
-#pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const int q = (int)threadIdx.x + j * kTile;
-    if (q < nv) v[j] = __ldg(src + q);
+  constexpr unsigned int kBytes = (unsigned int)(n * sizeof(R));
+  __shared__ __align__(8) unsigned long long s_bar;
+  if (threadIdx.x == 0) {
+    mlp_mbar_init(&s_bar);
+    tma_expect_tx(&s_bar, kBytes);
+    tma_load_1d(s, tb.g + o, kBytes, &s_bar);
   }
-#pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const int q = (int)threadIdx.x + j * kTile;
-    if (q < nv) dst[q] = v[j];
+  __syncthreads();   // the barrier's initialisation before anyone waits on it
+  if (!mlp_mbar_wait(&s_bar, 0u)) {
+    if (threadIdx.x == 0) atomicOr(status, QED_STATUS_TIMEOUT);
+    mlp_mbar_wait(&s_bar, 0u);
+    const uint4* src = reinterpret_cast<const uint4*>(tb.g + o);
+    uint4* dst = reinterpret_cast<uint4*>(s);
+    for (int q = (int)threadIdx.x; q < (int)(n / kEl); q += kTile) dst[q] = src[q];
   }
   if constexpr (sizeof(R) == 8) {
     tb.s = s;
@@ -829,7 +844,7 @@ __global__ void __launch_bounds__(kTile, kB ? Occ<R>::v : OccPh<R>::v) k_photon(
     ntiles = (unsigned int)((n_one + kTile - 1) / kTile);
   }
   Tabs<R> tb = tabs_global<R>(a.tables);
-  if constexpr (kSm) stage_rates<R, true>(tb, s_rates);
+  if constexpr (kSm) stage_rates<R, true>(tb, s_rates, &a.st->status);
   __syncthreads();
   const unsigned int epoch = gst->epoch;
   const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.fdt;
@@ -1186,7 +1201,7 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
     ntiles = t0s + (unsigned int)((n1s + kTile - 1) / kTile);
   }
   Tabs<R> tb = tabs_global<R>(a.tables);
-  if constexpr (kSm) stage_rates<R, false>(tb, s_rates);
+  if constexpr (kSm) stage_rates<R, false>(tb, s_rates, &a.st->status);
   __syncthreads();
   const unsigned int epoch = gst->epoch;
   const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.fdt;
