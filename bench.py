@@ -65,7 +65,7 @@ BYTES = {
 # by the particles it processed) from the ncu traffic capture of the streaming passes kept
 # under profiles/; scaled to a launch by its particle count.  Must be re-captured whenever
 # either streaming kernel changes.
-TRAFFIC_PER_UNIT = {"k_photon": 85.72, "k_lepton": 63.99}
+TRAFFIC_PER_UNIT = {"k_photon": 85.74, "k_lepton": 63.92}
 
 
 class ClockSampler:
