@@ -1566,15 +1566,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const __grid_constant__ S
 // NBW events: pair energy split (mixture over xi3' = +-1), SQAs D and D', joint spin
 // sampling from Eqs. G0-G3, birth of the pair at the photon's x^n (Sec. III D)
 // ======================================================================================
-// One decay (a task of k_events), not inlined so that the single-ensemble and the
-// batched kernels run the same compiled arithmetic (inlined into different kernels, the
-// compiler may fuse multiply-adds differently and results would differ in the last bit).
+// A decay's pair as the decay leaves it: everything of its birth but the slots and ids.
 template <typename R>
-__device__ __noinline__ void nbw_event(const NbwRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
-                                       unsigned long long rank, DevState* gst) {
-  DevState* st = E.st;
-  const unsigned long long ne0 = st->n_live[0], np0 = st->n_live[1];
-  const unsigned long long id0 = st->next_id + st->id_add[0];
+struct NbwPair {
+  double x, y, z;    // the photon's x^n
+  V3<R> p[2], s[2];  // momenta and spins, e- then e+
+  R w;               // the photon's weight
+};
+
+// One decay (a task of k_events) up to its pair's slots.  It reads only its log entry and
+// the tables, so it may run before the scan that ranks the events has finished.  Not inlined,
+// so that the single-ensemble and the batched kernels run the same compiled arithmetic
+// (inlined into different kernels, the compiler may fuse multiply-adds differently and
+// results would differ in the last bit).
+template <typename R>
+__device__ __noinline__ void nbw_pair(const NbwRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
+                                      NbwPair<R>* out) {
   const V3<R> k = mk<R>(rec.kx, rec.ky, rec.kz);
   const V3<R> xi = mk<R>(rec.x1, rec.x2, rec.x3);
   const R wgt = rec.w;
@@ -1644,9 +1651,22 @@ __device__ __noinline__ void nbw_event(const NbwRec<R>& rec, const EnsArgs& E, c
   }
   const R sp = (o < 2) ? R(1) : R(-1), sm = (o % 2 == 0) ? R(1) : R(-1);
   const R pp = sqrt(ep * ep - R(1)), pm = sqrt(em * em - R(1));
-  const unsigned long long base[2] = {ne0, np0};
-  const R pmag[2] = {pm, pp};
-  const V3<R> spin[2] = {sm * Sm, sp * Sp};
+  out->x = rec.x; out->y = rec.y; out->z = rec.z;
+  out->p[0] = mk<R>(pm * nn.x, pm * nn.y, pm * nn.z);
+  out->p[1] = mk<R>(pp * nn.x, pp * nn.y, pp * nn.z);
+  out->s[0] = sm * Sm;
+  out->s[1] = sp * Sp;
+  out->w = wgt;
+}
+
+// The pair of the decay of rank `rank` takes slot n_live + rank of each lepton set, with
+// ids next_id + 2 rank (e-) and + 1 (e+).  Needs the scan's rank only.
+template <typename R>
+__device__ __forceinline__ void nbw_birth(const NbwPair<R>& q, const EnsArgs& E, unsigned long long rank,
+                                          DevState* gst) {
+  DevState* st = E.st;
+  const unsigned long long base[2] = {st->n_live[0], st->n_live[1]};
+  const unsigned long long id0 = st->next_id + st->id_add[0];
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const SpeciesArgs& L = E.sp[s];
@@ -1656,12 +1676,21 @@ __device__ __noinline__ void nbw_event(const NbwRec<R>& rec, const EnsArgs& E, c
       atomicAdd(&st->ev[4], 1ull);
       continue;
     }
-    L.x[j] = rec.x; L.y[j] = rec.y; L.z[j] = rec.z;
-    stv<R>(L.px, j, pmag[s] * nn.x); stv<R>(L.py, j, pmag[s] * nn.y); stv<R>(L.pz, j, pmag[s] * nn.z);
-    stv<R>(L.s1, j, spin[s].x); stv<R>(L.s2, j, spin[s].y); stv<R>(L.s3, j, spin[s].z);
-    stv<R>(L.w, j, wgt);
+    L.x[j] = q.x; L.y[j] = q.y; L.z[j] = q.z;
+    stv<R>(L.px, j, q.p[s].x); stv<R>(L.py, j, q.p[s].y); stv<R>(L.pz, j, q.p[s].z);
+    stv<R>(L.s1, j, q.s[s].x); stv<R>(L.s2, j, q.s[s].y); stv<R>(L.s3, j, q.s[s].z);
+    stv<R>(L.w, j, q.w);
     L.id[j] = id0 + 2ull * rank + (unsigned long long)s;
   }
+}
+
+// a whole decay, once the scan has finished
+template <typename R>
+__device__ __forceinline__ void nbw_event(const NbwRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
+                                          unsigned long long rank, DevState* gst) {
+  NbwPair<R> q;
+  nbw_pair<R>(rec, E, tb, step, &q);
+  nbw_birth<R>(q, E, rank, gst);
 }
 
 // ---- matter events (Sec. III E) ------------------------------------------------------
@@ -1825,15 +1854,22 @@ __device__ __forceinline__ void close_step(const StepArgs& a, bool births) {
   }
 }
 
-// One emission (a task of k_events), not inlined for the same reason as nbw_event.
+// An emitted photon as its emission leaves it: everything of its birth but the slot and id.
 template <typename R>
-__device__ __noinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
-                                       unsigned long long rank, bool births, unsigned int flags, DevState* gst,
-                                       bool learned, float lnu_learned, const unsigned int* holes) {
-  DevState* st = E.st;
-  const SpeciesArgs& G = E.sp[2];
-  const unsigned long long nsurv = st->n_surv, nph0 = st->n_live[2];
-  const unsigned long long id0 = st->next_id + 2ull * st->n_nbw + st->id_add[1u + (rec.species & 1u)];
+struct NcsBirth {
+  double x, y, z;   // the lepton's x^{n+1}
+  V3<R> k, xi;      // omega n and the pure Stokes state
+  R theta, w;       // basis angle of the Stokes frame, weight
+};
+
+// One emission (a task of k_events) up to its photon's slot: energy, recoil, spin collapse
+// and the photon's state (written to *out when births are on).  It reads only the lepton,
+// its log entry and the tables, and writes only the lepton, so it may run before the scan
+// that ranks the events has finished.  Not inlined for the same reason as nbw_pair.
+template <typename R>
+__device__ __noinline__ void ncs_emit(const NcsRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
+                                      bool births, unsigned int flags, bool learned, float lnu_learned,
+                                      NcsBirth<R>* out) {
   const SpeciesArgs& L = E.sp[rec.species & 1u];
   const unsigned long long i = rec.i;
   const V3<R> pn = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
@@ -1904,22 +1940,49 @@ __device__ __noinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E, c
     stv<R>(L.px, i, pf * nn.x); stv<R>(L.py, i, pf * nn.y); stv<R>(L.pz, i, pf * nn.z);
   }
   if (births) {
-    const unsigned long long j = nsurv + rank;
-    if (!G.present || j >= G.cap) {
-      atomicOr(&gst->status, QED_STATUS_CAPACITY);
-      atomicAdd(&st->ev[4], 1ull);
-    } else {
-      if (j < nph0) ph_vacate<R>(G, st, holes, j);
-      V3<R> e1, e2;
-      frame(nn, e1, e2);
-      G.x[j] = lx; G.y[j] = ly; G.z[j] = lz;
-      stv<R>(G.px, j, om * nn.x); stv<R>(G.py, j, om * nn.y); stv<R>(G.pz, j, om * nn.z);
-      stv<R>(G.s1, j, xiph.x); stv<R>(G.s2, j, xiph.y); stv<R>(G.s3, j, xiph.z);
-      stv<R>(G.theta, j, m_atan2(dot(av, e2), dot(av, e1)));
-      stv<R>(G.w, j, lw);
-      G.id[j] = id0 + rank;
-    }
+    V3<R> e1, e2;
+    frame(nn, e1, e2);
+    out->x = lx; out->y = ly; out->z = lz;
+    out->k = mk<R>(om * nn.x, om * nn.y, om * nn.z);
+    out->xi = xiph;
+    out->theta = m_atan2(dot(av, e2), dot(av, e1));
+    out->w = lw;
   }
+}
+
+// The photon of the emission of rank `rank` (species: its lepton's log tag) takes slot
+// n_surv + rank, after the survivor there has moved to its hole; its id is the next free one
+// after the step's pairs.  Needs the scan's counts and holes.
+template <typename R>
+__device__ __forceinline__ void ncs_birth(const NcsBirth<R>& b, const EnsArgs& E, unsigned int species,
+                                          unsigned long long rank, DevState* gst, const unsigned int* holes) {
+  DevState* st = E.st;
+  const SpeciesArgs& G = E.sp[2];
+  const unsigned long long nsurv = st->n_surv, nph0 = st->n_live[2];
+  const unsigned long long id0 = st->next_id + 2ull * st->n_nbw + st->id_add[1u + (species & 1u)];
+  const unsigned long long j = nsurv + rank;
+  if (!G.present || j >= G.cap) {
+    atomicOr(&gst->status, QED_STATUS_CAPACITY);
+    atomicAdd(&st->ev[4], 1ull);
+    return;
+  }
+  if (j < nph0) ph_vacate<R>(G, st, holes, j);
+  G.x[j] = b.x; G.y[j] = b.y; G.z[j] = b.z;
+  stv<R>(G.px, j, b.k.x); stv<R>(G.py, j, b.k.y); stv<R>(G.pz, j, b.k.z);
+  stv<R>(G.s1, j, b.xi.x); stv<R>(G.s2, j, b.xi.y); stv<R>(G.s3, j, b.xi.z);
+  stv<R>(G.theta, j, b.theta);
+  stv<R>(G.w, j, b.w);
+  G.id[j] = id0 + rank;
+}
+
+// a whole emission, once the scan has finished
+template <typename R>
+__device__ __forceinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
+                                          unsigned long long rank, bool births, unsigned int flags, DevState* gst,
+                                          bool learned, float lnu_learned, const unsigned int* holes) {
+  NcsBirth<R> b;
+  ncs_emit<R>(rec, E, tb, step, births, flags, learned, lnu_learned, &b);
+  if (births) ncs_birth<R>(b, E, rec.species, rank, gst, holes);
 }
 
 // ---- sharded steps: one rank's birth counts; the id offsets from every rank's -------------
@@ -2031,23 +2094,62 @@ __device__ __forceinline__ unsigned long long fill_setup(const StepArgs& a, bool
 // k_events: every logged emission, every logged decay and every refill task of the step,
 // one thread each (grid-stride); they touch disjoint data (see the photon-slot rules
 // above), so one launch runs them all.  Its last block closes the step.
+//
+// It is launched as a programmatic dependent of the scan, which is an ordinary launch after
+// both streaming passes: when it starts, the passes have finished and only the scan's
+// results (ranks, holes, counts) may still be missing.  So each thread takes its first
+// emission or decay up to the rank-dependent birth before it waits for the scan, and the
+// sampling and spin arithmetic of the step's events runs beside the scan.
 // ======================================================================================
 template <typename R, bool kB>
 __global__ void __launch_bounds__(kTile) k_events(const __grid_constant__ StepArgs a) {
-  pdl_wait();
   __shared__ unsigned int s_fb[kB ? kMaxEns + 1 : 1];
   DevState* gst = a.st;
   const Tabs<R> tb = tabs_global<R>(a.tables);
+  // the logs, their extents and the tile counts are the passes' (final here)
   const unsigned long long n1 = min(gst->cursor[1], a.rec_cap[1]);
   const unsigned long long n0 = min(gst->cursor[0], a.rec_cap[0]);
   const unsigned int epoch = gst->epoch;
   const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
-  const unsigned long long nfill = fill_setup<kB>(a, births, s_fb);
   const NcsRec<R>* ncslog = reinterpret_cast<const NcsRec<R>*>(a.rec[1]);
   const NbwRec<R>* nbwlog = reinterpret_cast<const NbwRec<R>*>(a.rec[0]);
+  const unsigned long long k0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  // the first task, before the scan: 1 an emission, 2 a decay (NBW), taken up to the birth
+  int early = 0;
+  unsigned int e_tile = 0u, e_rin = 0u, e_tag = 0u;
+  NcsBirth<R> eb;
+  NbwPair<R> ep;
+  if (k0 < n1) {
+    const NcsRec<R> rec = ncslog[k0];
+    if (rec.stamp == epoch && a.tile_cnt[1][rec.tile] != 0 && !(rec.species & kEvMedium)) {
+      const EnsArgs& E = ens_of<kB>(a, kB ? (int)(rec.species >> 1) : 0);
+      ncs_emit<R>(rec, E, tb, time_of<kB>(E).step, births, a.flags, false, 0.0f, &eb);
+      early = 1; e_tile = rec.tile; e_rin = rec.r_in; e_tag = rec.species;
+    }
+  } else if (k0 < n1 + n0) {
+    const NbwRec<R> rec = nbwlog[k0 - n1];
+    if (rec.stamp == epoch && a.tile_cnt[0][rec.tile] != 0 && !(rec.ens & kEvMedium)) {
+      const EnsArgs& E = ens_of<kB>(a, kB ? (int)rec.ens : 0);
+      nbw_pair<R>(rec, E, tb, time_of<kB>(E).step, &ep);
+      early = 2; e_tile = rec.tile; e_rin = rec.r_in; e_tag = rec.ens;
+    }
+  }
+  pdl_wait();
+  const unsigned long long nfill = fill_setup<kB>(a, births, s_fb);
+  if (early == 1) {
+    const int ens = kB ? (int)(e_tag >> 1) : 0;
+    const unsigned long long grank = (unsigned long long)a.tile_pre[1][e_tile] + e_rin;
+    const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
+    if (births) ncs_birth<R>(eb, ens_of<kB>(a, ens), e_tag, rank, gst, holes_of<kB>(a, ens));
+  } else if (early == 2) {
+    const int ens = kB ? (int)e_tag : 0;
+    const unsigned long long grank = (unsigned long long)a.tile_pre[0][e_tile] + e_rin;
+    const unsigned long long rank = kB ? grank - a.map->ev_base[0][ens] : grank;
+    nbw_birth<R>(ep, ens_of<kB>(a, ens), rank, gst);
+  }
   const unsigned long long total = n1 + n0 + nfill;
-  for (unsigned long long kk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; kk < total;
-       kk += (unsigned long long)gridDim.x * blockDim.x) {
+  for (unsigned long long kk = k0; kk < total; kk += (unsigned long long)gridDim.x * blockDim.x) {
+    if (kk == k0 && early != 0) continue;   // taken above
     if (kk < n1) {
       const NcsRec<R> rec = ncslog[kk];
       if (rec.stamp != epoch || a.tile_cnt[1][rec.tile] == 0) continue;
