@@ -1799,58 +1799,66 @@ __device__ __forceinline__ void close_step(const StepArgs& a, bool births) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  const unsigned int epoch = threadIdx.x == 0 ? static_cast<volatile DevState*>(gst)->epoch : 0u;
   const int ne = kB ? a.n_ens : 1;
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const EnsArgs& E = ens_of<kB>(a, e);
     volatile DevState* v = E.st;
+    // every load before the first store: one round trip
     const unsigned long long nbw = v->n_nbw, ncs = births ? v->n_ncs_tot : 0ull, surv = v->n_surv;
-    const unsigned long long processed = (E.sp[0].present ? v->n_live[0] : 0ull) +   // step-start counts
-                                         (E.sp[1].present ? v->n_live[1] : 0ull) +
-                                         (E.sp[2].present ? v->n_live[2] : 0ull);
+    const unsigned long long live[3] = {v->n_live[0], v->n_live[1], v->n_live[2]};
+    const unsigned long long nid = v->next_id, add3 = v->id_add[3];
+    unsigned long long ev[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ev[q] = v->ev[q];
+    const double t0 = kB ? v->t : 0.0;
+    const unsigned int step0 = kB ? v->step : 0u;
+    const unsigned long long processed = (E.sp[0].present ? live[0] : 0ull) +   // step-start counts
+                                         (E.sp[1].present ? live[1] : 0ull) +
+                                         (E.sp[2].present ? live[2] : 0ull);
     for (int s = 0; s < 2; ++s) {
       if (!E.sp[s].present) continue;
-      const unsigned long long nn = v->n_live[s] + nbw;
+      const unsigned long long nn = live[s] + nbw;
       v->n_live[s] = nn > E.sp[s].cap ? E.sp[s].cap : nn;
     }
     if (E.sp[2].present) {
       const unsigned long long nn = surv + ncs;
       v->n_live[2] = nn > E.sp[2].cap ? E.sp[2].cap : nn;
     }
-    v->next_id = v->next_id + 2ull * nbw + ncs + v->id_add[3];
+    v->next_id = nid + 2ull * nbw + ncs + add3;
     atomicAdd(&gst->processed, processed);
     if (E.user_stats) {
       E.user_stats->n_processed += processed;
-      E.user_stats->n_ncs[0] += v->ev[0];
-      E.user_stats->n_ncs[1] += v->ev[1];
-      E.user_stats->n_nbw += nbw - v->ev[7];   // the ranked decays include the Bethe-Heitler pairs
-      E.user_stats->n_brems[0] += v->ev[5];
-      E.user_stats->n_brems[1] += v->ev[6];
-      E.user_stats->n_bh += v->ev[7];
-      E.user_stats->n_range += v->ev[3];
-      E.user_stats->n_drop += v->ev[4];
+      E.user_stats->n_ncs[0] += ev[0];
+      E.user_stats->n_ncs[1] += ev[1];
+      E.user_stats->n_nbw += nbw - ev[7];   // the ranked decays include the Bethe-Heitler pairs
+      E.user_stats->n_brems[0] += ev[5];
+      E.user_stats->n_brems[1] += ev[6];
+      E.user_stats->n_bh += ev[7];
+      E.user_stats->n_range += ev[3];
+      E.user_stats->n_drop += ev[4];
       E.user_stats->n_steps += 1;
-      E.user_stats->n_coarse += v->ev[2];
+      E.user_stats->n_coarse += ev[2];
     }
-    if (v->ev[3]) atomicOr(&gst->status, QED_STATUS_TABLE_RANGE);
+    if (ev[3]) atomicOr(&gst->status, QED_STATUS_TABLE_RANGE);
     for (int q = 0; q < 8; ++q) v->ev[q] = 0;
     v->n_nbw = 0; v->n_surv = 0; v->n_ncs_tot = 0; v->n_hlow = 0; v->n_ncs_e = 0;
     for (int q = 0; q < 4; ++q) v->id_add[q] = 0;
     if constexpr (kB) {
       // the ensemble's clock: the same operations as the host forms of a single step
-      const double t = v->t + a.dt;
+      const double t = t0 + a.dt;
       v->t = t;
-      v->step = v->step + 1;
+      v->step = step0 + 1;
       v->t_rel = (float)(t - E.f.phi0);
       v->t_mod = (float)fma(-kTwoPi, floor(t / kTwoPi), t);
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {   // the kernel's end publishes these to the next step's kernels
     volatile DevState* g = gst;
     g->cursor[0] = 0; g->cursor[1] = 0;
     g->done = 0;
-    g->epoch = g->epoch + 1;
-    __threadfence();
+    g->epoch = epoch + 1;
   }
 }
 
@@ -2135,17 +2143,19 @@ __global__ void __launch_bounds__(kTile) k_events(const __grid_constant__ StepAr
     }
   }
   pdl_wait();
+  // the first task's rank, loaded beside the refill set-up
+  const int e_ens = kB ? (int)(early == 1 ? e_tag >> 1 : e_tag) : 0;
+  unsigned long long e_rank = 0;
+  if (early != 0) {
+    const int w = early == 1 ? 1 : 0;
+    e_rank = (unsigned long long)a.tile_pre[w][e_tile] + e_rin;
+    if constexpr (kB) e_rank -= a.map->ev_base[w][e_ens];
+  }
   const unsigned long long nfill = fill_setup<kB>(a, births, s_fb);
   if (early == 1) {
-    const int ens = kB ? (int)(e_tag >> 1) : 0;
-    const unsigned long long grank = (unsigned long long)a.tile_pre[1][e_tile] + e_rin;
-    const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
-    if (births) ncs_birth<R>(eb, ens_of<kB>(a, ens), e_tag, rank, gst, holes_of<kB>(a, ens));
+    if (births) ncs_birth<R>(eb, ens_of<kB>(a, e_ens), e_tag, e_rank, gst, holes_of<kB>(a, e_ens));
   } else if (early == 2) {
-    const int ens = kB ? (int)e_tag : 0;
-    const unsigned long long grank = (unsigned long long)a.tile_pre[0][e_tile] + e_rin;
-    const unsigned long long rank = kB ? grank - a.map->ev_base[0][ens] : grank;
-    nbw_birth<R>(ep, ens_of<kB>(a, ens), rank, gst);
+    nbw_birth<R>(ep, ens_of<kB>(a, e_ens), e_rank, gst);
   }
   const unsigned long long total = n1 + n0 + nfill;
   for (unsigned long long kk = k0; kk < total; kk += (unsigned long long)gridDim.x * blockDim.x) {
