@@ -1578,10 +1578,12 @@ struct NbwPair {
 // the tables, so it may run before the scan that ranks the events has finished.  Not inlined,
 // so that the single-ensemble and the batched kernels run the same compiled arithmetic
 // (inlined into different kernels, the compiler may fuse multiply-adds differently and
-// results would differ in the last bit).
+// results would differ in the last bit).  tcnt (the photon tile counts, or null): false
+// when the entry's tile count is 0 (its log entries were dropped), loaded beside the work.
 template <typename R>
-__device__ __noinline__ void nbw_pair(const NbwRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
-                                      NbwPair<R>* out) {
+__device__ __noinline__ bool nbw_pair(const NbwRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
+                                      const unsigned int* tcnt, NbwPair<R>* out) {
+  const bool tile_ok = tcnt == nullptr || tcnt[rec.tile] != 0u;
   const V3<R> k = mk<R>(rec.kx, rec.ky, rec.kz);
   const V3<R> xi = mk<R>(rec.x1, rec.x2, rec.x3);
   const R wgt = rec.w;
@@ -1651,12 +1653,14 @@ __device__ __noinline__ void nbw_pair(const NbwRec<R>& rec, const EnsArgs& E, co
   }
   const R sp = (o < 2) ? R(1) : R(-1), sm = (o % 2 == 0) ? R(1) : R(-1);
   const R pp = sqrt(ep * ep - R(1)), pm = sqrt(em * em - R(1));
+  if (!tile_ok) return false;
   out->x = rec.x; out->y = rec.y; out->z = rec.z;
   out->p[0] = mk<R>(pm * nn.x, pm * nn.y, pm * nn.z);
   out->p[1] = mk<R>(pp * nn.x, pp * nn.y, pp * nn.z);
   out->s[0] = sm * Sm;
   out->s[1] = sp * Sp;
   out->w = wgt;
+  return true;
 }
 
 // The pair of the decay of rank `rank` takes slot n_live + rank of each lepton set, with
@@ -1689,7 +1693,7 @@ template <typename R>
 __device__ __forceinline__ void nbw_event(const NbwRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
                                           unsigned long long rank, DevState* gst) {
   NbwPair<R> q;
-  nbw_pair<R>(rec, E, tb, step, &q);
+  nbw_pair<R>(rec, E, tb, step, nullptr, &q);
   nbw_birth<R>(q, E, rank, gst);
 }
 
@@ -1874,10 +1878,14 @@ struct NcsBirth {
 // and the photon's state (written to *out when births are on).  It reads only the lepton,
 // its log entry and the tables, and writes only the lepton, so it may run before the scan
 // that ranks the events has finished.  Not inlined for the same reason as nbw_pair.
+// tcnt (the lepton tile counts, or null): when the entry's tile count is 0 (its log entries
+// were dropped) the emission writes nothing and returns false; the count is loaded with
+// the lepton instead of before it.
 template <typename R>
-__device__ __noinline__ void ncs_emit(const NcsRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
+__device__ __noinline__ bool ncs_emit(const NcsRec<R>& rec, const EnsArgs& E, const Tabs<R>& tb, unsigned int step,
                                       bool births, unsigned int flags, bool learned, float lnu_learned,
-                                      NcsBirth<R>* out) {
+                                      const unsigned int* tcnt, NcsBirth<R>* out) {
+  const bool tile_ok = tcnt == nullptr || tcnt[rec.tile] != 0u;
   const SpeciesArgs& L = E.sp[rec.species & 1u];
   const unsigned long long i = rec.i;
   const V3<R> pn = mk<R>(ld<R>(L.px, i), ld<R>(L.py, i), ld<R>(L.pz, i));
@@ -1941,6 +1949,7 @@ __device__ __noinline__ void ncs_emit(const NcsRec<R>& rec, const EnsArgs& E, co
     const R sg = ((R)us.u1 < R(0.5) * (R(1) + fm / F0)) ? R(1) : R(-1);
     xiph = mk<R>(sg * F1 / fm, sg * F2 / fm, sg * F3 / fm);
   }
+  if (!tile_ok) return false;
   stv<R>(L.s1, i, Sf.x); stv<R>(L.s2, i, Sf.y); stv<R>(L.s3, i, Sf.z);
   if (!(flags & QED_F_NO_RECOIL)) {
     // recoil p_f = p_i - omega n, |p_f| = (1-r) gamma - (gamma - |p|)
@@ -1956,6 +1965,7 @@ __device__ __noinline__ void ncs_emit(const NcsRec<R>& rec, const EnsArgs& E, co
     out->theta = m_atan2(dot(av, e2), dot(av, e1));
     out->w = lw;
   }
+  return true;
 }
 
 // The photon of the emission of rank `rank` (species: its lepton's log tag) takes slot
@@ -1989,7 +1999,7 @@ __device__ __forceinline__ void ncs_event(const NcsRec<R>& rec, const EnsArgs& E
                                           unsigned long long rank, bool births, unsigned int flags, DevState* gst,
                                           bool learned, float lnu_learned, const unsigned int* holes) {
   NcsBirth<R> b;
-  ncs_emit<R>(rec, E, tb, step, births, flags, learned, lnu_learned, &b);
+  ncs_emit<R>(rec, E, tb, step, births, flags, learned, lnu_learned, nullptr, &b);
   if (births) ncs_birth<R>(b, E, rec.species, rank, gst, holes);
 }
 
@@ -2127,36 +2137,40 @@ __global__ void __launch_bounds__(kTile) k_events(const __grid_constant__ StepAr
   unsigned int e_tile = 0u, e_rin = 0u, e_tag = 0u;
   NcsBirth<R> eb;
   NbwPair<R> ep;
-  if (k0 < n1) {
+  if (k0 < a.rec_cap[1]) {
+    // the emission record is read beside the log extents (a stale entry fails the stamp)
     const NcsRec<R> rec = ncslog[k0];
-    if (rec.stamp == epoch && a.tile_cnt[1][rec.tile] != 0 && !(rec.species & kEvMedium)) {
+    if (k0 < n1 && rec.stamp == epoch && !(rec.species & kEvMedium)) {
       const EnsArgs& E = ens_of<kB>(a, kB ? (int)(rec.species >> 1) : 0);
-      ncs_emit<R>(rec, E, tb, time_of<kB>(E).step, births, a.flags, false, 0.0f, &eb);
-      early = 1; e_tile = rec.tile; e_rin = rec.r_in; e_tag = rec.species;
+      if (ncs_emit<R>(rec, E, tb, time_of<kB>(E).step, births, a.flags, false, 0.0f, a.tile_cnt[1], &eb)) {
+        early = 1; e_tile = rec.tile; e_rin = rec.r_in; e_tag = rec.species;
+      }
     }
-  } else if (k0 < n1 + n0) {
+  }
+  if (k0 >= n1 && k0 < n1 + n0) {
     const NbwRec<R> rec = nbwlog[k0 - n1];
-    if (rec.stamp == epoch && a.tile_cnt[0][rec.tile] != 0 && !(rec.ens & kEvMedium)) {
+    if (rec.stamp == epoch && !(rec.ens & kEvMedium)) {
       const EnsArgs& E = ens_of<kB>(a, kB ? (int)rec.ens : 0);
-      nbw_pair<R>(rec, E, tb, time_of<kB>(E).step, &ep);
-      early = 2; e_tile = rec.tile; e_rin = rec.r_in; e_tag = rec.ens;
+      if (nbw_pair<R>(rec, E, tb, time_of<kB>(E).step, a.tile_cnt[0], &ep)) {
+        early = 2; e_tile = rec.tile; e_rin = rec.r_in; e_tag = rec.ens;
+      }
     }
   }
   pdl_wait();
-  // the first task's rank, loaded beside the refill set-up
-  const int e_ens = kB ? (int)(early == 1 ? e_tag >> 1 : e_tag) : 0;
-  unsigned long long e_rank = 0;
+  // the first task's birth: its rank and the counts it needs in one round trip (the refill
+  // set-up, which stores to shared memory, comes after it)
   if (early != 0) {
+    const int e_ens = kB ? (int)(early == 1 ? e_tag >> 1 : e_tag) : 0;
     const int w = early == 1 ? 1 : 0;
-    e_rank = (unsigned long long)a.tile_pre[w][e_tile] + e_rin;
+    unsigned long long e_rank = (unsigned long long)a.tile_pre[w][e_tile] + e_rin;
     if constexpr (kB) e_rank -= a.map->ev_base[w][e_ens];
+    if (early == 1) {
+      if (births) ncs_birth<R>(eb, ens_of<kB>(a, e_ens), e_tag, e_rank, gst, holes_of<kB>(a, e_ens));
+    } else {
+      nbw_birth<R>(ep, ens_of<kB>(a, e_ens), e_rank, gst);
+    }
   }
   const unsigned long long nfill = fill_setup<kB>(a, births, s_fb);
-  if (early == 1) {
-    if (births) ncs_birth<R>(eb, ens_of<kB>(a, e_ens), e_tag, e_rank, gst, holes_of<kB>(a, e_ens));
-  } else if (early == 2) {
-    nbw_birth<R>(ep, ens_of<kB>(a, e_ens), e_rank, gst);
-  }
   const unsigned long long total = n1 + n0 + nfill;
   for (unsigned long long kk = k0; kk < total; kk += (unsigned long long)gridDim.x * blockDim.x) {
     if (kk == k0 && early != 0) continue;   // taken above
