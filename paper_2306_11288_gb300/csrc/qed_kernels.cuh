@@ -2203,15 +2203,32 @@ __global__ void __launch_bounds__(kTile) k_events(const __grid_constant__ StepAr
 // ======================================================================================
 template <bool kB>
 __global__ void __launch_bounds__(kMlpRows) k_events_mlp(const __grid_constant__ StepArgs a) {
-  pdl_wait();
   __shared__ MlpSmem sm;
   __shared__ unsigned int s_fb[kB ? kMaxEns + 1 : 1];
   DevState* gst = a.st;
   const Tabs<float> tb = tabs_global<float>(a.tables);
+  // as in k_events: the logs, their extents and the tile counts are final at the start;
+  // the sampling runs before the wait for the scan, the births after it
   const unsigned long long nrec = min(gst->cursor[1], a.rec_cap[1]);
+  const unsigned long long n0 = min(gst->cursor[0], a.rec_cap[0]);
   const unsigned int epoch = gst->epoch;
   const NcsRec<float>* evlog = reinterpret_cast<const NcsRec<float>*>(a.rec[1]);
+  const NbwRec<float>* nbwlog = reinterpret_cast<const NbwRec<float>*>(a.rec[0]);
   const bool births = !(a.flags & (QED_F_NO_RECOIL | QED_F_DROP_PHOTONS));
+  // the thread's first decay, up to its pair's birth
+  const unsigned long long k0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  bool early = false;
+  unsigned int d_tile = 0u, d_rin = 0u, d_ens = 0u;
+  NbwPair<float> ep;
+  if (k0 < n0) {
+    const NbwRec<float> rec = nbwlog[k0];
+    if (rec.stamp == epoch && !(rec.ens & kEvMedium)) {
+      const EnsArgs& E = ens_of<kB>(a, kB ? (int)rec.ens : 0);
+      if (nbw_pair<float>(rec, E, tb, time_of<kB>(E).step, a.tile_cnt[0], &ep)) {
+        early = true; d_tile = rec.tile; d_rin = rec.r_in; d_ens = rec.ens;
+      }
+    }
+  }
   const unsigned long long nchunk = (nrec + kMlpRows - 1) / kMlpRows;
   if (blockIdx.x < nchunk) {   // blocks without events skip the tensor-core set-up
   mlp_setup(sm, static_cast<const MlpParams*>(a.mlp));
@@ -2251,25 +2268,37 @@ __global__ void __launch_bounds__(kMlpRows) k_events_mlp(const __grid_constant__
       if (threadIdx.x == 0) atomicOr(&gst->status, QED_STATUS_TIMEOUT);
       break;
     }
+    // the emission up to its photon's birth (a bremsstrahlung emission waits whole)
+    NcsBirth<float> b;
+    bool emitted = false;
+    if (valid && !(rec.species & kEvMedium)) {
+      // outside the trained chi_e range the table sampler (the fallback) draws the energy
+      const bool learned = rec.chi >= kMlpChiLo && rec.chi <= kMlpChiHi;
+      emitted = ncs_emit<float>(rec, E, tb, tm.step, births, a.flags, learned, mlp_base(lnchi, t) + 8.0f * y, nullptr,
+                                &b);
+    }
+    pdl_wait();   // returns at once after the first time
     if (valid) {
       const unsigned long long grank = (unsigned long long)a.tile_pre[1][rec.tile] + rec.r_in;
       const unsigned long long rank = kB ? grank - a.map->ev_base[1][ens] : grank;
-      // outside the trained chi_e range the table sampler (the fallback) draws the energy
-      const bool learned = rec.chi >= kMlpChiLo && rec.chi <= kMlpChiHi;
       const unsigned int* h = holes_of<kB>(a, ens);
       if (rec.species & kEvMedium) brems_event<float>(a, rec, E, tm.step, rank, births, a.flags, gst, h);
-      else ncs_event<float>(rec, E, tb, tm.step, rank, births, a.flags, gst, learned, mlp_base(lnchi, t) + 8.0f * y,
-                            h);
+      else if (emitted && births) ncs_birth<float>(b, E, rec.species, rank, gst, h);
     }
   }
   mlp_teardown(sm);
   }
-  // the decays and the refill tasks, as in k_events
-  const unsigned long long n0 = min(gst->cursor[0], a.rec_cap[0]);
+  pdl_wait();
+  if (early) {
+    const int ens = kB ? (int)d_ens : 0;
+    unsigned long long rank = (unsigned long long)a.tile_pre[0][d_tile] + d_rin;
+    if constexpr (kB) rank -= a.map->ev_base[0][ens];
+    nbw_birth<float>(ep, ens_of<kB>(a, ens), rank, gst);
+  }
+  // the other decays and the refill tasks, as in k_events
   const unsigned long long nfill = fill_setup<kB>(a, births, s_fb);
-  const NbwRec<float>* nbwlog = reinterpret_cast<const NbwRec<float>*>(a.rec[0]);
-  for (unsigned long long kk = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; kk < n0 + nfill;
-       kk += (unsigned long long)gridDim.x * blockDim.x) {
+  for (unsigned long long kk = k0; kk < n0 + nfill; kk += (unsigned long long)gridDim.x * blockDim.x) {
+    if (kk == k0 && early) continue;   // taken above
     if (kk < n0) nbw_task<float, kB>(a, tb, nbwlog[kk], epoch, gst);
     else fill_task<float, kB>(a, s_fb, kk - n0);
   }
