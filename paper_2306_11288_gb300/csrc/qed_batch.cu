@@ -75,10 +75,12 @@ static void launch_batch_t(const StepArgs& a, const int* nb, cudaStream_t s, cud
   k_bmap<<<1, kMapThreads, 0, s>>>(a);
   cudaEventRecord(fork, s);
   cudaStreamWaitEvent(side, fork, 0);
+  // the photon pass first: it takes the SMs first and the lepton pass fills in as its blocks
+  // retire (lepton first left the photon pass alone at the end: 2.5% slower on 64 ensembles)
+  k_photon<R, true, kSm><<<nb[0], kTile, 0, s>>>(a);
   if (a.flags & (QED_F_LL | QED_F_MLL | QED_F_MBMT)) k_lepton<R, true, kSm, true><<<nb[1], kTile, 0, side>>>(a);
   else k_lepton<R, true, kSm><<<nb[1], kTile, 0, side>>>(a);
   cudaEventRecord(join, side);
-  k_photon<R, true, kSm><<<nb[0], kTile, 0, s>>>(a);
   cudaStreamWaitEvent(s, join, 0);
   k_scan<R, true><<<2, kScanThreads, 0, s>>>(a, -1);   // both scans, after both passes
   if constexpr (sizeof(R) == 4) {
