@@ -158,3 +158,73 @@ def test_batch_validation(parent):
         s.close()
     q.qed_destroy(c1)
     q.qed_destroy(c2)
+
+
+def _event_heavy(n_e, n_ph, orc):
+    """Photons (omega = 4000, chi_gamma = 1) of which ~30% decay in one step and electrons
+    (gamma = 4000, chi_e = 1) that all emit, in a uniform crossed field: the one-step NBW
+    geometry of the oracle's statistics, with a lepton beam added."""
+    xil, alpha = 2.42631023867e-6, 7.2973525693e-3
+    om, chig = 4000.0, 1.0
+    E0 = chig / (xil * om * 2)
+    xi = np.array([0.3, -0.4, 0.5])
+    rng = np.random.default_rng(61)
+
+    def beam(n, px, stokes):
+        d = {"x": rng.uniform(-1, 1, n), "y": rng.uniform(-1, 1, n), "z": rng.uniform(-1, 1, n),
+             "px": np.full(n, px), "py": np.zeros(n), "pz": np.zeros(n), "w": np.ones(n)}
+        if stokes is None:   # spins: random directions, |S| uniform in [0, 1)
+            s = rng.normal(size=(n, 3))
+            s *= rng.uniform(0.0, 1.0, (n, 1)) / np.linalg.norm(s, axis=1, keepdims=True)
+        else:
+            s = np.tile(stokes, (n, 1))
+        d["s1"], d["s2"], d["s3"] = s[:, 0], s[:, 1], s[:, 2]
+        return d
+
+    e = beam(n_e, math.sqrt(om * om - 1.0), None)
+    e["id"] = np.arange(n_e, dtype=np.uint64)
+    ph = beam(n_ph, om, xi)
+    ph["theta"] = np.zeros(n_ph)
+    ph["id"] = np.arange(n_e, n_e + n_ph, dtype=np.uint64)
+    empty = {k: np.zeros(0) for k in ("x", "y", "z", "px", "py", "pz", "s1", "s2", "s3", "w")}
+    empty["id"] = np.zeros(0, dtype=np.uint64)
+    T = orc.nbw_rates(chig)
+    rate = alpha / (math.sqrt(3) * math.pi * xil * om) * (T[0] + xi[2] * T[1])
+    return {"e": e, "pos": empty, "ph": ph, "dt": 0.3 / rate, "seed": 23, "next_id": n_e + n_ph,
+            "field": {"kind": "uniform", "E": (0, E0, 0), "B": (0, 0, -E0)}}
+
+
+@pytest.mark.parametrize("prec", [q.QED_PREC_MIXED, q.QED_PREC_F64])
+def test_more_events_than_event_threads_equal_alone(parent, orc, prec):
+    """A step with more emissions and more decays than the event kernel has threads (one
+    event block of 256 threads per SM): a thread samples its first event before the scan has
+    finished and takes the rest after it, and here every decay is such a later task.  The
+    batch ends exactly where the ensemble ends when stepped alone by qed_step (whose wider
+    event grid gives most events a thread of their own), and on FP64 where the oracle ends."""
+    threads = torch.cuda.get_device_properties(0).multi_processor_count * 256
+    n_e, n_ph = int(1.3 * threads), 4 * threads
+    wl = _event_heavy(n_e, n_ph, orc)
+    caps = {"cap_e": n_e + n_ph, "cap_p": n_ph, "cap_ph": n_ph + 3 * n_e}
+    steps = 2
+    b = q.Batch([wl], prec=prec, ctx=parent, caps=[caps])
+    q.qed_batch_set_config(b.b, 4, 1, 0)
+    b.step(1)
+    c1 = b.sims[0].counters()
+    assert c1["n_ncs_e"] > threads and c1["n_nbw"] > threads   # later tasks of both kinds
+    b.step(steps - 1)
+    assert q.qed_read_status(parent) == 0
+    _same(b.sims[0], _alone(parent, wl, prec, steps), b.clocks()[0])
+    if prec == q.QED_PREC_F64:
+        osim = oracle.Sim(orc, wl, **caps)
+        ost = osim.run(steps, ALL)
+        c = b.sims[0].counters()
+        assert (c["n_ncs_e"], c["n_nbw"]) == (ost["n_ncs_e"], ost["n_nbw"])
+        g, o = b.sims[0].state(), osim.state()
+        assert g["next_id"] == o["next_id"]
+        for sp in ("e", "pos", "ph"):
+            og, oo = np.argsort(g[sp]["id"]), np.argsort(o[sp]["id"])
+            assert np.array_equal(g[sp]["id"][og], o[sp]["id"][oo])
+            for key in ("px", "py", "pz", "s1", "s2", "s3", "x", "y", "z"):
+                a, r = g[sp][key][og], o[sp][key][oo]
+                assert np.all(np.abs(a - r) <= 1e-10 * np.maximum(np.abs(r), 1.0)), (sp, key)
+    b.close()
