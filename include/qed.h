@@ -519,7 +519,10 @@ qed_status qed_batch_set_config(qed_batch *b, const qed_batch_config *cfg);
  * qed_batch_run runs them (a captured graph, replayed), times them with CUDA events, and
  * keeps the one with the most particle-steps per second.  The
  * population grows while the candidates run, so every candidate is timed twice, in a
- * forward and in a backward sweep, and ranked by the mean of its two rates.  The steps
+ * forward and in a backward sweep, and ranked by the mean of its two rates; rates within
+ * 2% of the best count as equal, and among those the shape with the most streaming blocks
+ * per SM is kept (the population keeps growing, and larger populations favour the wider
+ * grid).  The steps
  * (2 x (steps_per_candidate + 1) per candidate) advance the simulation; the results do not
  * depend on the launch shape.  Syncs.  *rate (optional) receives the chosen shape's mean
  * particle-steps per second.  Errors: QED_ERR_INVALID_ARG, QED_ERR_CUDA. */
