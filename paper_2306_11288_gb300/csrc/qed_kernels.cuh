@@ -221,6 +221,20 @@ __device__ __forceinline__ int find_ens(const unsigned int* off, int n, unsigned
   return lo;
 }
 
+// The same for a g common to the whole warp (a streaming pass's tile), with two ballots
+// instead of a search: the candidates 32 apart, then the 32 from there (off[0] = 0, so both
+// ballots have a bit set; off is non-decreasing, so the highest set bit is the last index
+// with off <= g).  n <= 1024; every lane of the warp calls it.
+__device__ __forceinline__ int find_ens_warp(const unsigned int* off, int n, unsigned int g) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const int ci = lane * 32;
+  const unsigned int cb = __ballot_sync(0xffffffffu, ci < n && off[ci] <= g);
+  const int c = (31 - __clz((int)cb)) * 32;
+  const int fi = c + lane;
+  const unsigned int fb = __ballot_sync(0xffffffffu, fi < n && off[fi] <= g);
+  return c + (31 - __clz((int)fb));
+}
+
 // block-wide bounds over the threads with on = true, into shared b[]: b[0..3] = imin, imax,
 // jmin, jmax of (i, j); b[4 + k] = the largest of the non-negative values m[k], k < kM (as
 // int bits, which order non-negative floats); b[4 + kM] = the smallest positive of the
@@ -815,7 +829,7 @@ template <bool kB>
 __device__ __forceinline__ PhTile ph_tile(const StepArgs& a, const unsigned int* s_off, unsigned long long n_one,
                                           unsigned int tile) {
   PhTile t;
-  t.ens = kB ? find_ens(s_off, a.n_ens, tile) : 0;
+  t.ens = kB ? find_ens_warp(s_off, a.n_ens, tile) : 0;
   const EnsArgs& E = ens_of<kB>(a, t.ens);
   const SpeciesArgs& P = E.sp[2];
   const unsigned long long n = kB ? (P.present ? E.st->n_live[2] : 0ull) : n_one;
@@ -1207,7 +1221,7 @@ __global__ void __launch_bounds__(kTile, (kRad || kDep) ? OccPh<R>::v : Occ<R>::
   const R dt = sizeof(R) == 8 ? (R)a.dt : (R)a.fdt;
   NcsRec<R>* evlog = reinterpret_cast<NcsRec<R>*>(a.rec[1]);
   for (unsigned int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int ens = kB ? find_ens(s_off, a.n_ens, tile) : 0;
+    const int ens = kB ? find_ens_warp(s_off, a.n_ens, tile) : 0;
     const EnsArgs& E = ens_of<kB>(a, ens);
     const EnsTime tm = time_of<kB>(E);
     DevState* st = E.st;
