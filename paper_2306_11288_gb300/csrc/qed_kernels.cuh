@@ -5,7 +5,8 @@
 // One step = four launches.  Caller's stream: k_photon, then (after joining the side
 // stream) k_scan (two blocks: photon tiles, lepton tiles) and k_events; the context's side
 // stream runs k_lepton concurrently with the photon pass.  The event kernel is a
-// programmatic dependent of the scans.
+// programmatic dependent of the scans: it samples each thread's first event while they run
+// and waits for their ranks only before the births.
 //   k_photon   : streaming pass over photons -- gather, Stokes frame rotation (Eq. rotation),
 //                VB phase (Eq. rotation2), NBW decision (Sec. III D); photons are updated in
 //                place and every decay is logged (tile, rank inside the tile) in an event log.
